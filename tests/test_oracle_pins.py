@@ -1,0 +1,374 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: brute-force DFT sums,
+closed-form solutions (free Gaussian spreading, the 1D NLS sech soliton, plane waves, Poisson
+on a sinusoid, the linear Jeans dispersion relation), exact invariants of the kick-drift-kick
+scheme (unitarity, time reversibility, O(dt^2) energy error) and exact CIC identities.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def coords(n, L):
+    return -0.5 * L + (L / n) * np.arange(n)
+
+
+def mesh(nx, ny, nz, L):
+    Lx, Ly, Lz = L
+    z, y, x = np.meshgrid(coords(nz, Lz), coords(ny, Ly), coords(nx, Lx), indexing="ij")
+    return x, y, z
+
+
+def brute_dft(x, sign=-1):
+    n = x.size
+    j = np.arange(n)
+    M = np.exp(sign * 2j * np.pi * np.outer(j, j) / n)
+    return M @ x
+
+
+# --------------------------------------------------------------------------- FFT
+
+
+@pytest.mark.parametrize("n", [2, 3, 6, 8, 12, 24, 32, 96, 5, 7])
+def test_fft1_matches_brute_force_sum(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ref = brute_dft(x, -1)
+    got = oracle.fft1(x, -1)
+    assert np.abs(got - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+    inv = oracle.fft1(x, +1)
+    assert np.abs(inv - brute_dft(x, +1) / n).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+
+
+def test_fft3_matches_brute_force_on_8_cubed():
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((8, 8, 8)) + 1j * rng.standard_normal((8, 8, 8))
+    j = np.arange(8)
+    F = np.exp(-2j * np.pi * np.outer(j, j) / 8)
+    # dense 512 x 512 DFT matrix = kron(Fz, Fy, Fx) acting on the x-fastest flattening
+    M = np.kron(np.kron(F, F), F)
+    ref = (M @ a.reshape(-1)).reshape(8, 8, 8)
+    got = oracle.fft3(a, -1)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_fft3_matches_library_fft_on_mixed_radix_box():
+    rng = np.random.default_rng(4)
+    a = rng.standard_normal((12, 8, 6)) + 1j * rng.standard_normal((12, 8, 6))
+    assert np.allclose(oracle.fft3(a, -1), np.fft.fftn(a), rtol=0, atol=1e-12)
+    assert np.allclose(oracle.fft3(a, +1), np.fft.ifftn(a), rtol=0, atol=1e-14)
+
+
+def test_fft_parseval_and_roundtrip():
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((16, 12, 24)) + 1j * rng.standard_normal((16, 12, 24))
+    A = oracle.fft3(a, -1)
+    assert abs(np.sum(np.abs(A) ** 2) / a.size - np.sum(np.abs(a) ** 2)) <= 1e-12 * np.sum(np.abs(a) ** 2)
+    back = oracle.fft3(A, +1)
+    assert np.abs(back - a).max() <= 1e-13
+
+
+# --------------------------------------------------------------------------- drift
+
+
+def _free_gaussian_1d(x, t, c, k0, s0, eta, L, images=3):
+    """Exact free evolution (i psi_t = -(eta/2) psi_xx) of the 1D Gaussian
+    (2 pi s0^2)^{-1/4} exp(-(x-c)^2/(4 s0^2) + i k0 x), summed over periodic images.
+    From the Fourier integral with a = s0^2, b = eta t / 2:
+    psi = N0 sqrt(a/(a+ib)) e^{i k0 c} exp((2 a k0 + i (x-c))^2 / (4 (a+ib)) - a k0^2)."""
+    a, b = s0 * s0, eta * t / 2.0
+    out = np.zeros_like(x, dtype=complex)
+    for m in range(-images, images + 1):
+        xm = x + m * L
+        out += np.sqrt(a / (a + 1j * b)) * np.exp(1j * k0 * c) * np.exp(
+            (2 * a * k0 + 1j * (xm - c)) ** 2 / (4 * (a + 1j * b)) - a * k0 * k0)
+    return (2 * np.pi * s0 * s0) ** -0.25 * out
+
+
+def test_free_gaussian_spreads_and_moves_as_closed_form():
+    """G = 0, kappa = 0: the split step is the exact free propagator, so a Gaussian packet must
+    follow the closed-form solution (spreading s(t) = s0 sqrt(1 + (eta t/(2 s0^2))^2), centre
+    moving at eta k0, and the phase).  This fixes the k^2/2 factor, the sign of the drift
+    phase, hbar/m and the per-axis k indexing."""
+    n, L, s0, eta = 64, 1.0, 0.05, 0.7
+    x, y, z = mesh(n, n, n, (L, L, L))
+    c = np.array([-0.1, 0.05, 0.0])
+    k0 = 2 * np.pi * np.array([2.0, -1.0, 3.0]) / L
+    sol = lambda t: (_free_gaussian_1d(x, t, c[0], k0[0], s0, eta, L)
+                     * _free_gaussian_1d(y, t, c[1], k0[1], s0, eta, L)
+                     * _free_gaussian_1d(z, t, c[2], k0[2], s0, eta, L))
+    o = Oracle(n, n, n, L, hbar_over_m=eta, G=0.0, kappa=0.0)
+    psi0 = sol(0.0)
+    o.set_ic(psi0)
+    t, steps = 0.012, 6
+    o.step(steps, t / steps)
+    ref = sol(t)
+    err = np.abs(o.get_psi() - ref).max() / np.abs(ref).max()
+    assert err < 1e-12, err
+    # the closed form itself spreads as stated (guards the reference formula)
+    rho = np.abs(ref) ** 2
+    s = s0 * math.sqrt(1 + (eta * t / (2 * s0 ** 2)) ** 2)
+    d = (x - c[0] - eta * k0[0] * t + 0.5) % 1.0 - 0.5
+    var = np.sum(rho * d * d) / np.sum(rho)
+    assert var == pytest.approx(s * s, rel=1e-6)
+
+
+def test_plane_wave_with_self_interaction_is_exact():
+    """Uniform-amplitude plane wave exp(i k0 x): Phi = 0 (zero mode removed), so
+    psi(t) = psi0 exp(-i (eta k0^2 / 2 + kappa rho0 / eta) t) exactly, for any dt."""
+    nx, ny, nz, L = 16, 8, 4, (2.0, 1.0, 1.0)
+    x, y, z = mesh(nx, ny, nz, L)
+    eta, kappa, rho0 = 0.5, 3.0, 2.0
+    k0 = 2 * np.pi * 3 / L[0]
+    psi = math.sqrt(rho0) * np.exp(1j * k0 * x)
+    o = Oracle(nx, ny, nz, L, hbar_over_m=eta, G=1.3, kappa=kappa)
+    o.set_ic(psi)
+    dt, steps = 0.0137, 11
+    o.step(steps, dt)
+    t = dt * steps
+    ref = psi * np.exp(-1j * (eta * k0 ** 2 / 2 + kappa * rho0 / eta) * t)
+    assert np.abs(o.get_psi() - ref).max() < 1e-12
+
+
+# --------------------------------------------------------------------------- Poisson
+
+
+def test_poisson_on_sinusoid_is_exact():
+    """rho = rho0 + A cos(k.r)  =>  Phi = -4 pi G A cos(k.r) / |k|^2, mean zero
+    (Sec. 3.1 step (c), Sec. 3.2.1).  Non-cubic box and grid pin the per-axis k tables."""
+    nx, ny, nz, L = 24, 16, 8, (1.5, 1.0, 0.5)
+    x, y, z = mesh(nx, ny, nz, L)
+    G, rho0, A = 2.5, 3.0, 0.7
+    m = np.array([2, -1, 1])
+    kv = 2 * np.pi * m / np.array(L)
+    ph = kv[0] * x + kv[1] * y + kv[2] * z
+    psi = np.sqrt(rho0 + A * np.cos(ph)).astype(complex)
+    o = Oracle(nx, ny, nz, L, G=G)
+    o.set_ic(psi)
+    phi = o.potential()
+    ref = -4 * np.pi * G * A * np.cos(ph) / np.dot(kv, kv)
+    assert np.abs(phi - ref).max() < 1e-12 * np.abs(ref).max() + 1e-14
+    assert abs(phi.mean()) < 1e-13
+
+
+def test_linear_jeans_dispersion_relation():
+    """Small perturbation psi = sqrt(rho0) (1 + eps cos kx) of a uniform background: the density
+    mode oscillates as cos(omega t) with omega^2 = eta^2 k^4 / 4 - 4 pi G rho0.  This fixes the
+    sign and size of the gravitational coupling in the kick (the wrong sign gives
+    omega^2 = eta^2 k^4/4 + 4 pi G rho0)."""
+    nx, L, eta, G, rho0, eps = 32, 1.0, 1.0, 1.0, 10.0, 1e-4
+    x, _, _ = mesh(nx, 4, 4, (L, L, L))
+    k = 2 * np.pi / L
+    psi = (math.sqrt(rho0) * (1 + eps * np.cos(k * x))).astype(complex)
+    o = Oracle(nx, 4, 4, L, hbar_over_m=eta, G=G)
+    o.set_ic(psi)
+    omega = math.sqrt(eta ** 2 * k ** 4 / 4 - 4 * math.pi * G * rho0)
+    dt = 2.5e-4
+    t = 0.0
+    for _ in range(8):
+        o.step(100, dt)
+        t += 100 * dt
+        rho = np.abs(o.get_psi()) ** 2
+        amp = 2.0 / nx * np.sum((rho[0, 0, :] / rho0 - 1.0) * np.cos(k * x[0, 0, :]))  # 2 eps cos(wt)
+        assert abs(amp / (2 * eps) - math.cos(omega * t)) < 5e-3, (t, amp / (2 * eps), math.cos(omega * t))
+
+
+# --------------------------------------------------------------------------- nonlinear splitting
+
+
+def _sech_soliton_error(dt, T=1.0, n=512, L=40.0, a=1.0, v=1.0):
+    x = coords(n, L)
+    exact = lambda t: a / np.cosh(a * (x - v * t)) * np.exp(1j * (v * x + (a * a - v * v) * t / 2))
+    o = Oracle(n, 1, 1, (L, 1.0, 1.0), hbar_over_m=1.0, G=0.0, kappa=-1.0)
+    o.set_ic(exact(0.0).reshape(1, 1, n))
+    steps = int(round(T / dt))
+    o.step(steps, dt)
+    return np.abs(o.get_psi().reshape(-1) - exact(T)).max()
+
+
+def test_nls_sech_soliton_second_order():
+    """Focusing cubic NLS i psi_t = -psi_xx / 2 - |psi|^2 psi (kappa = -1, G = 0, grid n x 1 x 1)
+    has the exact soliton a sech(a (x - v t)) exp(i (v x + (a^2 - v^2) t / 2)).  The KDK error
+    must fall 4x per halving of dt (second order, Sec. 3.1)."""
+    errs = [_sech_soliton_error(dt) for dt in (0.02, 0.01, 0.005)]
+    assert errs[0] < 5e-3
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.5 < r1 < 4.5 and 3.5 < r2 < 4.5, errs
+
+
+# --------------------------------------------------------------------------- invariants
+
+
+def _packets(n, seed=7, n_packets=4):
+    from paper_2606_25026_gb300 import inputs
+    return inputs.gaussian_packets(n, n_packets=n_packets, sigma=0.08, max_mode=3, seed=seed)
+
+
+def test_mass_is_conserved_to_roundoff():
+    n = 16
+    o = Oracle(n, n, n, 1.0, G=1.0, kappa=0.5)
+    psi = _packets(n)
+    o.set_ic(psi)
+    m0 = o.energy()["mass"]
+    o.step(50, 5e-4)
+    assert abs(o.energy()["mass"] - m0) < 1e-13 * m0
+
+
+def test_time_reversibility_with_particles():
+    """KDK with Phi recomputed from the current psi and particles is exactly reversible:
+    n steps with +dt then n steps with -dt return the initial state (to roundoff)."""
+    n = 16
+    o = Oracle(n, n, n, 1.0, G=1.0, kappa=0.3)
+    psi = _packets(n, seed=8)
+    rng = np.random.default_rng(9)
+    pos = (rng.random((20, 3)) - 0.5)
+    vel = rng.standard_normal((20, 3)) * 0.3
+    mass = np.full(20, 0.01)
+    o.set_ic(psi)
+    o.set_particles(pos, vel, mass)
+    o.step(30, 4e-4)
+    p_mid, _ = o.get_particles()
+    assert np.abs(p_mid - pos).max() > 1e-4  # it moved
+    o.step(30, -4e-4)
+    p1, v1 = o.get_particles()
+    assert np.abs(o.get_psi() - psi).max() < 1e-11
+    d = (p1 - pos + 0.5) % 1.0 - 0.5
+    assert np.abs(d).max() < 1e-11 and np.abs(v1 - vel).max() < 1e-10
+
+
+def test_energy_error_is_second_order_in_dt():
+    n = 16
+    psi = _packets(n, seed=10)
+    T = 0.02
+    drifts = []
+    for dt in (1e-3, 5e-4, 2.5e-4):
+        o = Oracle(n, n, n, 1.0, G=4.0, kappa=0.0)
+        o.set_ic(psi)
+        e0 = o.energy()["total"]
+        o.step(int(round(T / dt)), dt)
+        drifts.append(abs(o.energy()["total"] - e0))
+    r1, r2 = drifts[0] / drifts[1], drifts[1] / drifts[2]
+    assert 3.3 < r1 < 4.7 and 3.3 < r2 < 4.7, drifts
+
+
+def test_energy_components_of_plane_wave():
+    """Plane wave sqrt(rho0) e^{i k0 x}: kinetic = eta^2 k0^2 rho0 V / 2, interaction =
+    kappa rho0^2 V / 2, potential = 0, mass = rho0 V."""
+    nx, ny, nz, L = 16, 8, 8, (1.0, 1.0, 1.0)
+    x, y, z = mesh(nx, ny, nz, L)
+    eta, kappa, rho0 = 0.8, 2.0, 1.5
+    k0 = 2 * np.pi * 2
+    o = Oracle(nx, ny, nz, L, hbar_over_m=eta, G=1.0, kappa=kappa)
+    o.set_ic(math.sqrt(rho0) * np.exp(1j * k0 * x))
+    e = o.energy()
+    assert abs(e["mass"] - rho0) < 1e-13
+    assert abs(e["kinetic"] - eta ** 2 * k0 ** 2 * rho0 / 2) < 1e-10
+    assert abs(e["interaction"] - kappa * rho0 ** 2 / 2) < 1e-12
+    assert abs(e["potential"]) < 1e-13
+
+
+# --------------------------------------------------------------------------- particles / CIC
+
+
+def test_cic_deposit_conserves_mass_and_hits_single_node():
+    n, L = 8, 1.0
+    o = Oracle(n, n, n, L)
+    rng = np.random.default_rng(11)
+    pos = rng.random((50, 3)) - 0.5
+    mass = rng.random(50)
+    o.set_particles(pos, np.zeros((50, 3)), mass)
+    rho = o.deposit()
+    dv = (L / n) ** 3
+    assert abs(rho.sum() * dv - mass.sum()) < 1e-13 * mass.sum()
+    # a particle exactly on node (i, j, k) = (3, 5, 0) deposits only there
+    node = np.array([-0.5 + 3 / n, -0.5 + 5 / n, -0.5 + 0 / n])
+    o.set_particles(node[None, :], np.zeros((1, 3)), np.array([2.0]))
+    rho = o.deposit()
+    assert rho[0, 5, 3] == pytest.approx(2.0 / dv, rel=1e-14)
+    assert np.count_nonzero(rho) == 1
+
+
+def test_cic_force_of_sinusoidal_potential_closed_form():
+    """Phi = cos(k x): the central difference at node i is -(Phi_{i+1} - Phi_{i-1}) / (2 dx) =
+    sin(k x_i) sin(k dx) / dx; the CIC interpolation between nodes is linear in f."""
+    n, L = 16, 1.0
+    x, y, z = mesh(n, n, n, (L, L, L))
+    k = 2 * np.pi * 2 / L
+    dx = L / n
+    o = Oracle(n, n, n, L)
+    o.set_phi(np.cos(k * x))
+    xi = coords(n, L)
+    f = 0.3
+    px = xi[5] + f * dx
+    o.set_particles(np.array([[xi[5], 0.1, -0.2], [px, 0.0, 0.0]]), np.zeros((2, 3)), np.ones(2))
+    g = o.accel()
+    node_g = lambda i: math.sin(k * xi[i % n]) * math.sin(k * dx) / dx
+    assert g[0, 0] == pytest.approx(node_g(5), rel=1e-12)
+    assert g[1, 0] == pytest.approx((1 - f) * node_g(5) + f * node_g(6), rel=1e-12)
+    assert abs(g[0, 1]) < 1e-12 and abs(g[0, 2]) < 1e-12
+
+
+def test_particle_momentum_conserved_by_pm_forces():
+    """Stars only (psi = 0): CIC deposit + central-difference gradient + CIC interpolation give
+    pairwise antisymmetric forces, so sum m_p g_p = 0."""
+    n = 16
+    o = Oracle(n, n, n, 1.0, G=1.0)
+    o.set_ic(np.zeros((n, n, n), complex))
+    rng = np.random.default_rng(12)
+    pos = (rng.random((40, 3)) - 0.5) * 0.6
+    mass = rng.random(40)
+    o.set_particles(pos, np.zeros((40, 3)), mass)
+    o.potential()
+    g = o.accel()
+    tot = (mass[:, None] * g).sum(0)
+    assert np.abs(tot).max() < 1e-12 * (mass[:, None] * np.abs(g)).sum()
+
+
+def test_free_streaming_particles():
+    n = 8
+    o = Oracle(n, n, n, 1.0, G=0.0)
+    rng = np.random.default_rng(13)
+    pos = rng.random((10, 3)) - 0.5
+    vel = rng.standard_normal((10, 3))
+    o.set_particles(pos, vel, np.ones(10))
+    o.step(7, 0.01)
+    p, v = o.get_particles()
+    ref = pos + vel * 0.07
+    ref -= np.floor(ref + 0.5)
+    assert np.abs(p - ref).max() < 1e-13 and np.abs(v - vel).max() == 0.0
+    assert (p >= -0.5).all() and (p < 0.5).all()
+
+
+# --------------------------------------------------------------------------- CFL
+
+
+def test_suggest_dt_follows_sec_3_5():
+    g = json.load(open(os.path.join(GOLDEN, "cfl_sec3_5.json")))
+    pre, zeta = g["prefactor"], g["default_safety_zeta_t"]
+    kin = g["kinetic_coefficient_numerator"] / (g["kinetic_coefficient_denominator_over_pi"] * math.pi)
+    two_pi = g["phase_limit_over_pi"] * math.pi
+    # kinetic term binds (free field)
+    n, L, eta = 32, 1.0, 0.6
+    o = Oracle(n, n, n, L, hbar_over_m=eta, G=0.0)
+    o.set_ic(np.ones((n, n, n), complex))
+    assert o.suggest_dt(zeta) == pytest.approx(zeta * pre * kin * (L / n) ** 2 / eta, rel=1e-14)
+    # self-interaction term binds
+    o = Oracle(8, 8, 8, 1.0, hbar_over_m=eta, G=0.0, kappa=500.0)
+    o.set_ic(np.full((8, 8, 8), 2.0, complex))
+    assert o.suggest_dt(zeta) == pytest.approx(zeta * pre * two_pi * eta / (500.0 * 4.0), rel=1e-14)
+    # potential term binds: rho = 1 + A cos(2 pi x) => max|Phi| = 4 pi G A / (2 pi)^2
+    x, _, _ = mesh(8, 8, 8, (1.0, 1.0, 1.0))
+    Gv, A = 20000.0, 0.5
+    o = Oracle(8, 8, 8, 1.0, hbar_over_m=eta, G=Gv)
+    o.set_ic(np.sqrt(1 + A * np.cos(2 * np.pi * x)).astype(complex))
+    maxphi = 4 * math.pi * Gv * A / (2 * math.pi) ** 2
+    assert o.suggest_dt(zeta) == pytest.approx(zeta * pre * two_pi * eta / maxphi, rel=1e-12)
