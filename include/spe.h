@@ -1,0 +1,174 @@
+/*
+ * libspe -- GB300-native pseudo-spectral split-step solver for the
+ * Schroedinger-Poisson equation coupled to star particles.
+ *
+ * The method (Meng & Dong 2026, "WaveDM.jl"):
+ *   i eta psi_t = -(eta^2/2) lap psi + (Phi + kappa|psi|^2) psi,
+ *   lap Phi = 4 pi G (|psi|^2 + rho_*),
+ * advanced per step of size dt as
+ *   (a) psi <- exp(-i (Phi + kappa|psi|^2) dt/2 / eta) psi        Sec. 3.1 Eq. (SPE_solver_KDK) (a)
+ *   (b) psi <- F^-1{ exp(-i eta k^2 dt / 2) F{psi} }                 step (b), Algorithm 1
+ *   (c) Phi <- F^-1{ -4 pi G F{|psi|^2 + rho_*} / k^2 }, k=0 -> 0   step (c), Sec. 3.2.1
+ *   (d) psi <- exp(-i (Phi + kappa|psi|^2) dt/2 / eta) psi        step (d)
+ * with eta = hbar/m (Sec. 2.2, Eqs. (GPE), (Poisson), (SPE_dimensionless)),
+ * kappa the local self-interaction of Sec. 2.2 / Sec. 2.4, and rho_* the
+ * cloud-in-cell deposit of star particles that move by a kick-drift-kick
+ * leapfrog in the same potential (Sec. 3.2.2, dynamic particle mode), their
+ * acceleration the CIC interpolation of the second-order central-difference
+ * gradient of Phi (Sec. 3.1, finite differences).
+ *
+ * Grid: periodic, nx x ny x nz nodes, node (i,j,k) at
+ * (-Lx/2 + i Lx/nx, -Ly/2 + j Ly/ny, -Lz/2 + k Lz/nz).  Field arrays are
+ * [z][y][x] with x fastest.  Complex values are complex64: interleaved
+ * (re, im) float pairs, 8 bytes per node.  Particle arrays are n x 3 floats
+ * (x, y, z per particle) plus n floats of mass.
+ *
+ * Every entry point returns SPE_OK (0) or a negative status; nothing aborts
+ * the process and no C++ exception crosses this interface.  "where" selects
+ * whether a caller buffer is host memory (SPE_HOST, pageable or pinned) or
+ * device memory on the grid's device (SPE_DEVICE).  Caller buffers are only
+ * borrowed for the duration of the call.
+ *
+ * Streams: all device work of a grid is ordered on cfg.cuda_stream (NULL =
+ * the legacy default stream).  Calls that return data to the host, or that
+ * report device-side status, synchronise that stream first.
+ */
+#ifndef SPE_H
+#define SPE_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define SPE_API __attribute__((visibility("default")))
+#else
+#define SPE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SPE_OK            0
+#define SPE_EINVAL       -1   /* bad argument (size, pointer, unsupported shape) */
+#define SPE_ENOMEM       -2   /* workspace too small or device allocation failed */
+#define SPE_ECUDA        -3   /* a CUDA runtime call failed */
+#define SPE_ECFL         -4   /* |dt| above the Sec. 3.5 CFL bound (unless SPE_NO_CFL_CHECK) */
+#define SPE_ENONFINITE   -5   /* the field's mass became NaN or infinite */
+#define SPE_ETIMEOUT     -6   /* a bounded device-side wait gave up */
+#define SPE_ESTATE       -7   /* call out of order (e.g. no initial condition set) */
+
+/* ---- where a caller buffer lives ---- */
+#define SPE_HOST   0
+#define SPE_DEVICE 1
+
+/* ---- spe_config.flags ---- */
+#define SPE_GRAVITY_OFF   (1 << 0)  /* G treated as 0: no Poisson solve */
+#define SPE_NO_CFL_CHECK  (1 << 1)  /* spe_step does not reject dt above the kinetic CFL bound */
+#define SPE_ASYNC         (1 << 2)  /* spe_step returns after enqueueing; no status check */
+#define SPE_PROFILE       (1 << 3)  /* time every kernel launch with CUDA events (spe_profile_read) */
+#define SPE_NO_GRAPH      (1 << 4)  /* launch the per-step kernels directly, never through a CUDA graph */
+
+typedef struct spe_grid spe_grid;   /* opaque */
+
+typedef struct {
+    int nx, ny, nz;          /* nodes per axis: each in {4,6,8,12,16,24,32,48,64,96,128,192,256,384,512,768,1024} */
+    double Lx, Ly, Lz;       /* box side lengths */
+    double hbar_over_m;      /* eta > 0 */
+    double G;                /* gravitational constant in code units */
+    double kappa;            /* local self-interaction strength (0 = none) */
+    size_t max_particles;    /* particle capacity (0 = field only) */
+    int flags;               /* SPE_* flags above */
+    void *cuda_stream;       /* cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = default */
+} spe_config;
+
+typedef struct {
+    double mass;          /* sum |psi|^2 dV */
+    double kinetic;       /* (eta^2/2) sum_k k^2 |F{psi}_k|^2 dV / Ncells (spectral) */
+    double potential;     /* 1/2 sum (|psi|^2 + rho_*) Phi dV */
+    double interaction;   /* kappa/2 sum |psi|^4 dV */
+    double star_kinetic;  /* 1/2 sum m_p |v_p|^2 */
+    double total;         /* kinetic + potential + interaction + star_kinetic */
+    double max_abs_phi;   /* max |Phi| over the nodes */
+} spe_energy_t;
+
+/* Device bytes a grid with this configuration needs (field buffers, the
+ * half-spectrum potential buffer, particle arrays, tables and reduction
+ * scratch).  Returns SPE_EINVAL for an unsupported configuration. */
+SPE_API int spe_workspace_bytes(const spe_config *cfg, size_t *bytes);
+
+/* Create a grid.  workspace: a device buffer of at least
+ * spe_workspace_bytes() bytes, 256-byte aligned, owned by the caller and
+ * kept alive until spe_destroy (e.g. a torch uint8 tensor); or NULL, in
+ * which case the library allocates it with cudaMalloc and frees it in
+ * spe_destroy.  The configuration is copied.  psi starts at zero. */
+SPE_API int spe_create_grid(const spe_config *cfg, void *workspace, size_t workspace_bytes, spe_grid **out);
+
+/* Release the grid (and its workspace if the library allocated it). */
+SPE_API int spe_destroy(spe_grid *g);
+
+/* Copy the initial field in: n must equal nx*ny*nz complex64 values. */
+SPE_API int spe_set_ic(spe_grid *g, const void *psi_c64, size_t n, int where);
+
+/* Append n star particles (pos3, vel3: n x 3 floats; mass: n floats).
+ * Positions are wrapped into the box.  Fails with SPE_ENOMEM if the total
+ * exceeds cfg.max_particles. */
+SPE_API int spe_add_particles(spe_grid *g, size_t n, const float *pos3, const float *vel3, const float *mass, int where);
+
+/* Remove all particles. */
+SPE_API int spe_clear_particles(spe_grid *g);
+
+/* Advance nsteps kick-drift-kick steps of size dt (dt may be negative).
+ * The half kicks of consecutive steps inside one call are applied as one
+ * full kick; the call starts and ends with a half kick so that psi and the
+ * particles are synchronised at return.  Unless SPE_ASYNC is set, the call
+ * waits for the work and returns SPE_ENONFINITE if the field's mass stopped
+ * being finite. */
+SPE_API int spe_step(spe_grid *g, int nsteps, double dt);
+
+/* Sec. 3.5: dt = safety * 0.5 * min{4/(3 pi) dx^2/eta, 2 pi eta/max|Phi|,
+ * 2 pi eta/(|kappa| max|psi|^2)}, dx the smallest cell edge. */
+SPE_API int spe_suggest_dt(spe_grid *g, double safety, double *dt_out);
+
+/* rho_psi + rho_* on the nodes: nx*ny*nz floats. */
+SPE_API int spe_density(spe_grid *g, float *out, int where);
+
+/* Phi on the nodes (zero mode removed): nx*ny*nz floats. */
+SPE_API int spe_potential(spe_grid *g, float *out, int where);
+
+/* Mass and energy terms (FP64 accumulation on the device). */
+SPE_API int spe_energy(spe_grid *g, spe_energy_t *out);
+
+/* Mass of the field as computed inside the last step (no extra pass). */
+SPE_API int spe_last_mass(spe_grid *g, double *mass_out);
+
+/* Copy psi out: nx*ny*nz complex64 values. */
+SPE_API int spe_get_psi(spe_grid *g, void *out, int where);
+
+/* Copy the particles out in the order they were added (pos3, vel3: n x 3
+ * floats; either may be NULL). */
+SPE_API int spe_get_particles(spe_grid *g, float *pos3, float *vel3, int where);
+
+/* Number of particles currently held. */
+SPE_API int spe_particle_count(spe_grid *g, size_t *n_out);
+
+/* Wait for all work queued on the grid's stream. */
+SPE_API int spe_sync(spe_grid *g);
+
+/* Kernel launches issued by this grid since creation (or the last reset). */
+SPE_API int spe_launch_count(spe_grid *g, unsigned long long *count_out, int reset);
+
+/* With SPE_PROFILE: per kernel kind, the launches and the summed device
+ * time (ms) measured by CUDA events on the grid's stream since the last
+ * read; resets the record.  names[i] points at static strings.  Returns the
+ * number of kinds written (at most cap) or a negative status. */
+SPE_API int spe_profile_read(spe_grid *g, const char **names, unsigned long long *launches, double *ms, int cap);
+
+/* Human-readable text for a status code (static storage). */
+SPE_API const char *spe_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPE_H */

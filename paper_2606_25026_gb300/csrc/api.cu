@@ -1,0 +1,854 @@
+// libspe C ABI: grid state, workspace layout and the per-step schedule.
+//
+// Per kick-drift-kick step (Sec. 3.1 Eq. (SPE_solver_KDK), Algorithm 1) the
+// device runs, on the grid's stream:
+//   1. x pass  : Phi rows from the x half spectrum, kick psi by (Phi +
+//                kappa|psi|^2) dt_k / eta, forward x transform of psi  [(a)/(d), (b)]
+//   2. stars   : v += g dt_k, x += v dt, CIC deposit                  [Sec. 3.2.2]
+//   3. y pass  : forward y transform of psi                           [(b)]
+//   4. z pass  : forward z, drift exp(-i eta k^2 dt / 2) / N^3, inverse z  [(b)]
+//   5. y pass  : inverse y transform of psi                           [(b)]
+//   6. x pass  : inverse x transform, rho = |psi|^2 + rho_*, mass, forward
+//                real x transform of rho                               [(b), (c)]
+//   7. y pass  : forward y transform of rho_hat                       [(c)]
+//   8. z pass  : forward z, * -4 pi G / (k^2 N^3) (k = 0 -> 0), inverse z   [(c)]
+//   9. y pass  : inverse y transform                                  [(c)]
+// leaving Phi as an x half spectrum that the next step's pass 1 turns into
+// real-space Phi.  Within one spe_step call the second half kick of a step
+// and the first of the next are one full kick (dt_k = dt); the call starts
+// and ends with a half kick (dt_k = dt/2).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "spe.h"
+#include "spe_internal.cuh"
+
+namespace spe {
+cudaError_t setup_xpass_attributes();
+cudaError_t setup_spass_attributes();
+
+bool supported_n(int n)
+{
+    switch (n) {
+#define X(v) case v:
+        SPE_FOR_EACH_N(X)
+#undef X
+        return true;
+    default: return false;
+    }
+}
+
+cudaError_t setup_kernel_attributes()
+{
+    cudaError_t e = setup_xpass_attributes();
+    if (e == cudaSuccess) e = setup_spass_attributes();
+    return e;
+}
+}  // namespace spe
+
+using namespace spe;
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+enum Kind {
+    KIND_X_KICK_FFT = 0,
+    KIND_X_IFFT_DENSITY,
+    KIND_Y_PSI,
+    KIND_Z_DRIFT,
+    KIND_Y_RHO,
+    KIND_Z_POISSON,
+    KIND_PARTICLES,
+    KIND_X_KICK_FINAL,
+    KIND_X_POTENTIAL,
+    KIND_DIAG,
+    KIND_COPY,
+    KIND_COUNT
+};
+
+const char *kKindNames[KIND_COUNT] = {
+    "x_kick_fwd", "x_inv_density_r2c", "y_fft_psi", "z_fft_drift", "y_fft_rho", "z_fft_poisson",
+    "particles_kdk_deposit", "x_kick_final", "x_potential", "diagnostics", "layout_copy",
+};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t e0, e1;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t psi, phik, phi, dep, part, tw, k2, drift, partials, counter, diag, total;
+};
+
+int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
+{
+    if (!c) return SPE_EINVAL;
+    if (!supported_n(c->nx) || !supported_n(c->ny) || !supported_n(c->nz)) return SPE_EINVAL;
+    if (!(c->Lx > 0) || !(c->Ly > 0) || !(c->Lz > 0) || !(c->hbar_over_m > 0)) return SPE_EINVAL;
+    if (!isfinite(c->G) || !isfinite(c->kappa)) return SPE_EINVAL;
+    if (c->max_particles > (size_t)0x7fffffff) return SPE_EINVAL;
+    const size_t ncells = (size_t)c->nx * c->ny * c->nz;
+    const int w = c->nx / 2 + 1;
+    const int p = (w + 3) & ~3;
+    size_t off = 0;
+    L->psi = off;      off = align256(off + ncells * sizeof(float2));
+    L->phik = off;     off = align256(off + (size_t)c->ny * c->nz * p * sizeof(float2));
+    L->phi = off;      off = align256(off + ncells * sizeof(float));
+    L->dep = off;      off = align256(off + (c->max_particles ? ncells * sizeof(long long) : 0));
+    L->part = off;     off = align256(off + 7 * align256(c->max_particles * sizeof(float)));
+    L->tw = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float2));
+    L->k2 = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float));
+    L->drift = off;    off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float2));
+    L->partials = off; off = align256(off + (size_t)kMaxPartials * 5 * sizeof(double));
+    L->counter = off;  off = align256(off + 256);
+    L->diag = off;     off = align256(off + 64 * sizeof(double));
+    L->total = off;
+    *W = w;
+    *P = p;
+    return SPE_OK;
+}
+
+}  // namespace
+
+struct spe_grid {
+    spe_config cfg;
+    int device;
+    int n[3];
+    double L[3], dx[3], dv;
+    size_t ncells;
+    int W, P;
+    cudaStream_t st;
+    bool gravity;
+    unsigned char *ws;
+    bool owns_ws;
+    float2 *psi, *phik;
+    float *phi;
+    long long *dep;
+    float *px, *py, *pz, *vx, *vy, *vz, *pm;
+    float2 *tw[3];
+    float *k2[3];
+    float2 *drift[3];
+    double *partials;
+    unsigned int *counter;
+    double *diag;
+    float2 *h_stage;  // pinned staging for the drift tables
+    size_t np;
+    double mstar;
+    double quantum;
+    bool phi_valid;
+    bool tables_valid;
+    double table_dt;
+    unsigned long long launches;
+    bool profile;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> evfree;
+};
+
+namespace {
+
+int cuerr(cudaError_t e) { return e == cudaSuccess ? SPE_OK : SPE_ECUDA; }
+
+cudaEvent_t take_event(spe_grid *g)
+{
+    if (!g->evfree.empty()) {
+        cudaEvent_t e = g->evfree.back();
+        g->evfree.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Issue one kernel launch, counting it and (with SPE_PROFILE) timing it.
+template <class F>
+int launch(spe_grid *g, int kind, F &&f)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (g->profile) {
+        e0 = take_event(g);
+        cudaEventRecord(e0, g->st);
+    }
+    cudaError_t e = f();
+    g->launches++;
+    if (g->profile) {
+        e1 = take_event(g);
+        cudaEventRecord(e1, g->st);
+        g->prof.push_back(ProfRec{kind, e0, e1});
+    }
+    return cuerr(e);
+}
+
+double wavenumber(int j, int n, double L)
+{
+    const int s = (2 * j < n) ? j : j - n;
+    return 2.0 * kPi * (double)s / L;
+}
+
+XParams base_x(spe_grid *g)
+{
+    XParams p;
+    memset(&p, 0, sizeof(p));
+    p.psi = g->psi;
+    p.phik = g->phik;
+    p.phi_out = g->phi;
+    p.dep = g->dep;
+    p.tw = g->tw[0];
+    p.k2 = g->k2[0];
+    p.rows = g->n[1] * g->n[2];
+    p.P = g->P;
+    p.kappa = (float)g->cfg.kappa;
+    p.dep_scale = (float)(g->quantum / g->dv);
+    p.partials = g->partials;
+    p.counter = g->counter;
+    p.result = g->diag;
+    return p;
+}
+
+// Transform along y of a field with W live columns at row pitch P.
+SParams base_y(spe_grid *g, float2 *data, int W, int P)
+{
+    SParams p;
+    memset(&p, 0, sizeof(p));
+    p.data = data;
+    p.S = P;
+    p.bstride = (long long)P * g->n[1];
+    p.W = W;
+    p.batches = g->n[2];
+    p.tw = g->tw[1];
+    p.linek2 = g->k2[1];
+    p.partials = g->partials;
+    p.counter = g->counter;
+    p.result = g->diag;
+    return p;
+}
+
+// Transform along z.
+SParams base_z(spe_grid *g, float2 *data, int W, int P)
+{
+    SParams p;
+    memset(&p, 0, sizeof(p));
+    p.data = data;
+    p.S = (long long)P * g->n[1];
+    p.bstride = P;
+    p.W = W;
+    p.batches = g->n[1];
+    p.tw = g->tw[2];
+    p.colf = g->drift[0];
+    p.batchf = g->drift[1];
+    p.linef = g->drift[2];
+    p.colk2 = g->k2[0];
+    p.batchk2 = g->k2[1];
+    p.linek2 = g->k2[2];
+    p.norm = (float)(1.0 / (double)g->ncells);
+    p.poisson = (float)(-4.0 * kPi * g->cfg.G);
+    p.partials = g->partials;
+    p.counter = g->counter;
+    p.result = g->diag;
+    return p;
+}
+
+PParams base_p(spe_grid *g)
+{
+    PParams p;
+    memset(&p, 0, sizeof(p));
+    p.x = g->px; p.y = g->py; p.z = g->pz;
+    p.vx = g->vx; p.vy = g->vy; p.vz = g->vz;
+    p.m = g->pm;
+    p.phi = g->phi;
+    p.dep = g->dep;
+    p.n = (int)g->np;
+    p.nx = g->n[0]; p.ny = g->n[1]; p.nz = g->n[2];
+    p.Lx = (float)g->L[0]; p.Ly = (float)g->L[1]; p.Lz = (float)g->L[2];
+    p.inv_dx = (float)(1.0 / g->dx[0]);
+    p.inv_dy = (float)(1.0 / g->dx[1]);
+    p.inv_dz = (float)(1.0 / g->dx[2]);
+    p.gx_scale = (float)(0.5 / g->dx[0]);
+    p.gy_scale = (float)(0.5 / g->dx[1]);
+    p.gz_scale = (float)(0.5 / g->dx[2]);
+    p.inv_quantum = (float)(1.0 / g->quantum);
+    return p;
+}
+
+int run_x(spe_grid *g, int kind, XParams p)
+{
+    return launch(g, kind, [&] { return launch_xpass(g->n[0], p, g->st, nullptr); });
+}
+
+int run_s(spe_grid *g, int kind, int n, SParams p)
+{
+    return launch(g, kind, [&] { return launch_spass(n, p, g->st, nullptr); });
+}
+
+// exp(-i eta k^2 dt / 2) per axis, phase reduced modulo 2 pi in FP64.
+int ensure_drift_tables(spe_grid *g, double dt)
+{
+    if (g->tables_valid && g->table_dt == dt) return SPE_OK;
+    cudaError_t e = cudaStreamSynchronize(g->st);  // the staging buffer may still be in flight
+    if (e != cudaSuccess) return SPE_ECUDA;
+    size_t off = 0;
+    for (int a = 0; a < 3; ++a) {
+        for (int j = 0; j < g->n[a]; ++j) {
+            const double k = wavenumber(j, g->n[a], g->L[a]);
+            double ph = fmod(g->cfg.hbar_over_m * k * k * dt * 0.5, 2.0 * kPi);
+            g->h_stage[off + j] = make_float2((float)cos(ph), (float)-sin(ph));
+        }
+        off += g->n[a];
+    }
+    e = cudaMemcpyAsync(g->drift[0], g->h_stage, off * sizeof(float2), cudaMemcpyHostToDevice, g->st);
+    if (e != cudaSuccess) return SPE_ECUDA;
+    g->tables_valid = true;
+    g->table_dt = dt;
+    return SPE_OK;
+}
+
+bool has_kick(spe_grid *g) { return g->gravity || g->cfg.kappa != 0.0; }
+
+// Phi from the current psi and particles (the state at n = 0 of Algorithm 1,
+// or after set_ic / add_particles).
+int compute_phi(spe_grid *g)
+{
+    int rc = SPE_OK;
+    if (!g->gravity) {
+        g->phi_valid = true;
+        return SPE_OK;
+    }
+    const bool parts = g->np > 0;
+    if (parts) {
+        PParams pp = base_p(g);
+        pp.flags = PK_DEPOSIT;
+        rc = launch(g, KIND_PARTICLES, [&] { return launch_particles(pp, g->st); });
+        if (rc) return rc;
+    }
+    XParams xp = base_x(g);
+    xp.flags = X_MASS | X_R2C | (parts ? X_DEP : 0);
+    if ((rc = run_x(g, KIND_X_IFFT_DENSITY, xp))) return rc;
+    SParams y = base_y(g, g->phik, g->W, g->P);
+    y.flags = S_FWD;
+    if ((rc = run_s(g, KIND_Y_RHO, g->n[1], y))) return rc;
+    SParams z = base_z(g, g->phik, g->W, g->P);
+    z.flags = S_FWD | S_POISSON | S_INV;
+    if ((rc = run_s(g, KIND_Z_POISSON, g->n[2], z))) return rc;
+    y.flags = S_INV;
+    if ((rc = run_s(g, KIND_Y_RHO, g->n[1], y))) return rc;
+    g->phi_valid = true;
+    return SPE_OK;
+}
+
+// One KDK step whose leading kick has size dtk (dt/2 for the first step of
+// a call, dt afterwards).
+int step_body(spe_grid *g, double dtk, double dt)
+{
+    int rc;
+    const bool grav = g->gravity;
+    const bool parts = g->np > 0;
+    XParams xp = base_x(g);
+    xp.flags = X_FFT | (has_kick(g) ? X_KICK : 0) | (grav ? X_HAS_PHI : 0) | ((parts && grav) ? X_WRITE_PHI : 0);
+    xp.kick_scale = (float)(dtk / g->cfg.hbar_over_m);
+    if ((rc = run_x(g, KIND_X_KICK_FFT, xp))) return rc;
+    if (parts) {
+        PParams pp = base_p(g);
+        pp.flags = PK_DRIFT | (grav ? (PK_KICK | PK_DEPOSIT) : 0);
+        pp.kick = (float)dtk;
+        pp.drift = (float)dt;
+        if ((rc = launch(g, KIND_PARTICLES, [&] { return launch_particles(pp, g->st); }))) return rc;
+    }
+    SParams y = base_y(g, g->psi, g->n[0], g->n[0]);
+    y.flags = S_FWD;
+    if ((rc = run_s(g, KIND_Y_PSI, g->n[1], y))) return rc;
+    SParams z = base_z(g, g->psi, g->n[0], g->n[0]);
+    z.flags = S_FWD | S_DRIFT | S_INV;
+    if ((rc = run_s(g, KIND_Z_DRIFT, g->n[2], z))) return rc;
+    y.flags = S_INV;
+    if ((rc = run_s(g, KIND_Y_PSI, g->n[1], y))) return rc;
+    xp.flags = X_IFFT | X_MASS | (grav ? X_R2C : 0) | ((parts && grav) ? X_DEP : 0);
+    if ((rc = run_x(g, KIND_X_IFFT_DENSITY, xp))) return rc;
+    if (grav) {
+        SParams yr = base_y(g, g->phik, g->W, g->P);
+        yr.flags = S_FWD;
+        if ((rc = run_s(g, KIND_Y_RHO, g->n[1], yr))) return rc;
+        SParams zr = base_z(g, g->phik, g->W, g->P);
+        zr.flags = S_FWD | S_POISSON | S_INV;
+        if ((rc = run_s(g, KIND_Z_POISSON, g->n[2], zr))) return rc;
+        yr.flags = S_INV;
+        if ((rc = run_s(g, KIND_Y_RHO, g->n[1], yr))) return rc;
+    }
+    return SPE_OK;
+}
+
+int final_half_kick(spe_grid *g, double h)
+{
+    int rc;
+    const bool grav = g->gravity;
+    const bool parts = g->np > 0;
+    if (has_kick(g)) {
+        XParams xp = base_x(g);
+        xp.flags = X_KICK | (grav ? X_HAS_PHI : 0) | ((parts && grav) ? X_WRITE_PHI : 0);
+        xp.kick_scale = (float)(h / g->cfg.hbar_over_m);
+        if ((rc = run_x(g, KIND_X_KICK_FINAL, xp))) return rc;
+    }
+    if (parts && grav) {
+        PParams pp = base_p(g);
+        pp.flags = PK_KICK;
+        pp.kick = (float)h;
+        if ((rc = launch(g, KIND_PARTICLES, [&] { return launch_particles(pp, g->st); }))) return rc;
+    }
+    return SPE_OK;
+}
+
+// Real-space Phi into g->phi.
+int potential_to_phi(spe_grid *g)
+{
+    int rc;
+    if (!g->phi_valid && (rc = compute_phi(g))) return rc;
+    if (!g->gravity) return cuerr(cudaMemsetAsync(g->phi, 0, g->ncells * sizeof(float), g->st));
+    XParams xp = base_x(g);
+    xp.flags = X_HAS_PHI | X_WRITE_PHI;
+    return run_x(g, KIND_X_POTENTIAL, xp);
+}
+
+int deposit_only(spe_grid *g)
+{
+    if (!g->np) return SPE_OK;
+    PParams pp = base_p(g);
+    pp.flags = PK_DEPOSIT;
+    return launch(g, KIND_PARTICLES, [&] { return launch_particles(pp, g->st); });
+}
+
+int copy_out(spe_grid *g, void *dst, const void *src, size_t bytes, int where)
+{
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, where == SPE_HOST ? cudaMemcpyDeviceToHost
+                                                                       : cudaMemcpyDeviceToDevice, g->st);
+    if (e != cudaSuccess) return SPE_ECUDA;
+    return cuerr(cudaStreamSynchronize(g->st));
+}
+
+void update_quantum(spe_grid *g)
+{
+    g->quantum = (g->mstar > 0.0) ? g->mstar * ldexp(1.0, -50) : 1.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *spe_strerror(int s)
+{
+    switch (s) {
+    case SPE_OK: return "ok";
+    case SPE_EINVAL: return "invalid argument or unsupported configuration";
+    case SPE_ENOMEM: return "out of memory or workspace too small";
+    case SPE_ECUDA: return "CUDA runtime error";
+    case SPE_ECFL: return "time step above the CFL bound";
+    case SPE_ENONFINITE: return "field mass is not finite";
+    case SPE_ETIMEOUT: return "bounded device wait timed out";
+    case SPE_ESTATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+int spe_workspace_bytes(const spe_config *cfg, size_t *bytes)
+{
+    if (!bytes) return SPE_EINVAL;
+    Layout L;
+    int W, P;
+    int rc = compute_layout(cfg, &L, &W, &P);
+    if (rc) return rc;
+    *bytes = L.total;
+    return SPE_OK;
+}
+
+int spe_create_grid(const spe_config *cfg, void *workspace, size_t workspace_bytes, spe_grid **out)
+{
+    if (!out) return SPE_EINVAL;
+    *out = nullptr;
+    Layout L;
+    int W, P;
+    int rc = compute_layout(cfg, &L, &W, &P);
+    if (rc) return rc;
+    if (workspace && (workspace_bytes < L.total || ((uintptr_t)workspace & 255))) return SPE_ENOMEM;
+    static bool attrs_done = false;
+    if (!attrs_done) {
+        if (setup_kernel_attributes() != cudaSuccess) return SPE_ECUDA;
+        attrs_done = true;
+    }
+    spe_grid *g = new (std::nothrow) spe_grid();
+    if (!g) return SPE_ENOMEM;
+    g->cfg = *cfg;
+    cudaGetDevice(&g->device);
+    g->n[0] = cfg->nx; g->n[1] = cfg->ny; g->n[2] = cfg->nz;
+    g->L[0] = cfg->Lx; g->L[1] = cfg->Ly; g->L[2] = cfg->Lz;
+    for (int a = 0; a < 3; ++a) g->dx[a] = g->L[a] / g->n[a];
+    g->dv = g->dx[0] * g->dx[1] * g->dx[2];
+    g->ncells = (size_t)cfg->nx * cfg->ny * cfg->nz;
+    g->W = W;
+    g->P = P;
+    g->st = (cudaStream_t)cfg->cuda_stream;
+    g->gravity = !(cfg->flags & SPE_GRAVITY_OFF) && cfg->G != 0.0;
+    g->profile = (cfg->flags & SPE_PROFILE) != 0;
+    if (workspace) {
+        g->ws = (unsigned char *)workspace;
+        g->owns_ws = false;
+    } else {
+        if (cudaMalloc(&g->ws, L.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete g;
+            return SPE_ENOMEM;
+        }
+        g->owns_ws = true;
+    }
+    if (cudaMallocHost(&g->h_stage, (size_t)(cfg->nx + cfg->ny + cfg->nz) * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        if (g->owns_ws) cudaFree(g->ws);
+        delete g;
+        return SPE_ENOMEM;
+    }
+    unsigned char *b = g->ws;
+    g->psi = (float2 *)(b + L.psi);
+    g->phik = (float2 *)(b + L.phik);
+    g->phi = (float *)(b + L.phi);
+    g->dep = cfg->max_particles ? (long long *)(b + L.dep) : nullptr;
+    const size_t pstride = align256(cfg->max_particles * sizeof(float));
+    float **parr[7] = {&g->px, &g->py, &g->pz, &g->vx, &g->vy, &g->vz, &g->pm};
+    for (int i = 0; i < 7; ++i) *parr[i] = (float *)(b + L.part + i * pstride);
+    g->tw[0] = (float2 *)(b + L.tw);
+    g->tw[1] = g->tw[0] + cfg->nx;
+    g->tw[2] = g->tw[1] + cfg->ny;
+    g->k2[0] = (float *)(b + L.k2);
+    g->k2[1] = g->k2[0] + cfg->nx;
+    g->k2[2] = g->k2[1] + cfg->ny;
+    g->drift[0] = (float2 *)(b + L.drift);
+    g->drift[1] = g->drift[0] + cfg->nx;
+    g->drift[2] = g->drift[1] + cfg->ny;
+    g->partials = (double *)(b + L.partials);
+    g->counter = (unsigned int *)(b + L.counter);
+    g->diag = (double *)(b + L.diag);
+    update_quantum(g);
+
+    cudaError_t e = cudaMemsetAsync(g->ws, 0, L.total, g->st);
+    // FP64-built tables: twiddles exp(-2 pi i e / N) and k^2 per axis
+    const int ntot = cfg->nx + cfg->ny + cfg->nz;
+    std::vector<float2> tw(ntot);
+    std::vector<float> k2(ntot);
+    int off = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int n = g->n[a];
+        for (int j = 0; j < n; ++j) {
+            const double ang = -2.0 * kPi * (double)j / (double)n;
+            tw[off + j] = make_float2((float)cos(ang), (float)sin(ang));
+            const double k = wavenumber(j, n, g->L[a]);
+            k2[off + j] = (float)(k * k);
+        }
+        off += n;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->tw[0], tw.data(), ntot * sizeof(float2), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->k2[0], k2.data(), ntot * sizeof(float), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) {
+        spe_destroy(g);
+        return SPE_ECUDA;
+    }
+    *out = g;
+    return SPE_OK;
+}
+
+int spe_destroy(spe_grid *g)
+{
+    if (!g) return SPE_EINVAL;
+    cudaStreamSynchronize(g->st);
+    for (auto &r : g->prof) {
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+    }
+    for (auto e : g->evfree) cudaEventDestroy(e);
+    if (g->h_stage) cudaFreeHost(g->h_stage);
+    if (g->owns_ws) cudaFree(g->ws);
+    delete g;
+    return SPE_OK;
+}
+
+int spe_set_ic(spe_grid *g, const void *psi, size_t n, int where)
+{
+    if (!g || !psi || n != g->ncells || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(g->psi, psi, n * sizeof(float2),
+                                    where == SPE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->st);
+    if (e == cudaSuccess && where == SPE_HOST) e = cudaStreamSynchronize(g->st);
+    g->phi_valid = false;
+    return cuerr(e);
+}
+
+int spe_add_particles(spe_grid *g, size_t n, const float *pos3, const float *vel3, const float *mass, int where)
+{
+    if (!g || (n && (!pos3 || !vel3 || !mass)) || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
+    if (n == 0) return SPE_OK;
+    if (g->np + n > g->cfg.max_particles) return SPE_ENOMEM;
+    const size_t o = g->np;
+    cudaError_t e = cudaSuccess;
+    double msum = 0.0;
+    if (where == SPE_HOST) {
+        std::vector<float> soa(7 * n);
+        for (size_t i = 0; i < n; ++i) {
+            for (int a = 0; a < 3; ++a) {
+                float x = pos3[3 * i + a];
+                const float Lf = (float)g->L[a];
+                soa[a * n + i] = x - Lf * floorf((x + 0.5f * Lf) / Lf);
+                soa[(3 + a) * n + i] = vel3[3 * i + a];
+            }
+            soa[6 * n + i] = mass[i];
+            msum += mass[i];
+        }
+        float *dst[7] = {g->px, g->py, g->pz, g->vx, g->vy, g->vz, g->pm};
+        for (int k = 0; k < 7 && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(dst[k] + o, soa.data() + k * n, n * sizeof(float), cudaMemcpyHostToDevice, g->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    } else {
+        std::vector<float> hm(n);
+        e = cudaMemcpyAsync(hm.data(), mass, n * sizeof(float), cudaMemcpyDeviceToHost, g->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+        for (size_t i = 0; i < n; ++i) msum += hm[i];
+        if (e == cudaSuccess)
+            e = launch_particles_to_soa(pos3, vel3, mass, (int)n, g->px + o, g->py + o, g->pz + o, g->vx + o,
+                                        g->vy + o, g->vz + o, g->pm + o, (float)g->L[0], (float)g->L[1],
+                                        (float)g->L[2], g->st);
+        g->launches++;
+    }
+    if (e != cudaSuccess) return SPE_ECUDA;
+    g->np += n;
+    g->mstar += msum;
+    update_quantum(g);
+    g->phi_valid = false;
+    return SPE_OK;
+}
+
+int spe_clear_particles(spe_grid *g)
+{
+    if (!g) return SPE_EINVAL;
+    g->np = 0;
+    g->mstar = 0.0;
+    update_quantum(g);
+    g->phi_valid = false;
+    return SPE_OK;
+}
+
+int spe_step(spe_grid *g, int nsteps, double dt)
+{
+    if (!g || nsteps < 0 || !isfinite(dt)) return SPE_EINVAL;
+    if (nsteps == 0) return SPE_OK;
+    if (!(g->cfg.flags & SPE_NO_CFL_CHECK)) {
+        double dx = g->dx[0];
+        if (g->dx[1] < dx) dx = g->dx[1];
+        if (g->dx[2] < dx) dx = g->dx[2];
+        const double bound = 0.5 * 4.0 / (3.0 * kPi) * dx * dx / g->cfg.hbar_over_m;
+        if (fabs(dt) > bound * (1.0 + 1e-12)) return SPE_ECFL;
+    }
+    int rc;
+    if ((rc = ensure_drift_tables(g, dt))) return rc;
+    if (!g->phi_valid && (rc = compute_phi(g))) return rc;
+    for (int s = 0; s < nsteps; ++s)
+        if ((rc = step_body(g, s == 0 ? 0.5 * dt : dt, dt))) return rc;
+    if ((rc = final_half_kick(g, 0.5 * dt))) return rc;
+    if (g->cfg.flags & SPE_ASYNC) return SPE_OK;
+    double mass = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&mass, g->diag, sizeof(double), cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) return SPE_ECUDA;
+    if (!isfinite(mass)) return SPE_ENONFINITE;
+    return SPE_OK;
+}
+
+int spe_last_mass(spe_grid *g, double *mass_out)
+{
+    if (!g || !mass_out) return SPE_EINVAL;
+    double m = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&m, g->diag, sizeof(double), cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) return SPE_ECUDA;
+    *mass_out = m * g->dv;
+    return SPE_OK;
+}
+
+int spe_suggest_dt(spe_grid *g, double safety, double *dt_out)
+{
+    if (!g || !dt_out || !(safety > 0)) return SPE_EINVAL;
+    int rc;
+    if ((rc = potential_to_phi(g))) return rc;
+    if ((rc = launch(g, KIND_DIAG, [&] {
+             return launch_grid_diag(g->psi, g->phi, nullptr, 0.f, (float)g->cfg.kappa, g->dv, g->ncells,
+                                     g->partials, g->counter, g->diag + 8, g->st);
+         })))
+        return rc;
+    double raw[5];
+    if ((rc = copy_out(g, raw, g->diag + 8, sizeof(raw), SPE_HOST))) return rc;
+    double dx = g->dx[0];
+    if (g->dx[1] < dx) dx = g->dx[1];
+    if (g->dx[2] < dx) dx = g->dx[2];
+    const double eta = g->cfg.hbar_over_m;
+    double t = 4.0 / (3.0 * kPi) * dx * dx / eta;
+    const double maxphi = g->gravity ? raw[3] : 0.0, maxrho = raw[4];
+    if (maxphi > 0.0 && 2.0 * kPi * eta / maxphi < t) t = 2.0 * kPi * eta / maxphi;
+    if (g->cfg.kappa != 0.0 && maxrho > 0.0) {
+        const double ti = 2.0 * kPi * eta / (fabs(g->cfg.kappa) * maxrho);
+        if (ti < t) t = ti;
+    }
+    *dt_out = safety * 0.5 * t;
+    return SPE_OK;
+}
+
+int spe_density(spe_grid *g, float *out, int where)
+{
+    if (!g || !out || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
+    int rc;
+    if ((rc = deposit_only(g))) return rc;
+    float *dst = (where == SPE_DEVICE) ? out : g->phi;
+    if ((rc = launch(g, KIND_DIAG, [&] {
+             return launch_density(g->psi, g->np ? g->dep : nullptr, (float)(g->quantum / g->dv), dst, g->ncells,
+                                   g->st);
+         })))
+        return rc;
+    if (where == SPE_HOST) return copy_out(g, out, g->phi, g->ncells * sizeof(float), SPE_HOST);
+    return cuerr(cudaStreamSynchronize(g->st));
+}
+
+int spe_potential(spe_grid *g, float *out, int where)
+{
+    if (!g || !out || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
+    int rc;
+    if ((rc = potential_to_phi(g))) return rc;
+    return copy_out(g, out, g->phi, g->ncells * sizeof(float), where);
+}
+
+int spe_energy(spe_grid *g, spe_energy_t *out)
+{
+    if (!g || !out) return SPE_EINVAL;
+    int rc;
+    if ((rc = potential_to_phi(g))) return rc;
+    if ((rc = deposit_only(g))) return rc;
+    if ((rc = launch(g, KIND_DIAG, [&] {
+             return launch_grid_diag(g->psi, g->phi, g->np ? g->dep : nullptr, (float)(g->quantum / g->dv),
+                                     (float)g->cfg.kappa, g->dv, g->ncells, g->partials, g->counter, g->diag + 8,
+                                     g->st);
+         })))
+        return rc;
+    // kinetic: sum over axes of (1/N_a) sum_lines sum_k k_a^2 |F_a line|^2
+    XParams xp = base_x(g);
+    xp.flags = X_KIN;
+    xp.result = g->diag + 16;
+    if ((rc = run_x(g, KIND_DIAG, xp))) return rc;
+    SParams y = base_y(g, g->psi, g->n[0], g->n[0]);
+    y.flags = S_KIN;
+    y.result = g->diag + 17;
+    if ((rc = run_s(g, KIND_DIAG, g->n[1], y))) return rc;
+    SParams z = base_z(g, g->psi, g->n[0], g->n[0]);
+    z.flags = S_KIN;
+    z.result = g->diag + 18;
+    if ((rc = run_s(g, KIND_DIAG, g->n[2], z))) return rc;
+    double skin = 0.0;
+    if (g->np) {
+        if ((rc = launch(g, KIND_DIAG, [&] {
+                 return launch_particle_ke(g->vx, g->vy, g->vz, g->pm, (int)g->np, g->partials, g->counter,
+                                           g->diag + 19, g->st);
+             })))
+            return rc;
+    }
+    double raw[12];
+    if ((rc = copy_out(g, raw, g->diag + 8, sizeof(raw), SPE_HOST))) return rc;
+    if (g->np) skin = raw[11];
+    const double eta = g->cfg.hbar_over_m;
+    out->mass = raw[0] * g->dv;
+    out->potential = g->gravity ? 0.5 * raw[1] * g->dv : 0.0;
+    out->interaction = 0.5 * g->cfg.kappa * raw[2] * g->dv;
+    out->max_abs_phi = g->gravity ? raw[3] : 0.0;
+    out->kinetic = 0.5 * eta * eta * g->dv * (raw[8] / g->n[0] + raw[9] / g->n[1] + raw[10] / g->n[2]);
+    out->star_kinetic = skin;
+    out->total = out->kinetic + out->potential + out->interaction + out->star_kinetic;
+    return SPE_OK;
+}
+
+int spe_get_psi(spe_grid *g, void *out, int where)
+{
+    if (!g || !out || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
+    return copy_out(g, out, g->psi, g->ncells * sizeof(float2), where);
+}
+
+int spe_get_particles(spe_grid *g, float *pos3, float *vel3, int where)
+{
+    if (!g || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
+    const size_t n = g->np;
+    if (!n) return SPE_OK;
+    if (where == SPE_DEVICE) {
+        int rc = launch(g, KIND_COPY, [&] {
+            return launch_particles_from_soa(g->px, g->py, g->pz, g->vx, g->vy, g->vz, (int)n, pos3, vel3, g->st);
+        });
+        if (rc) return rc;
+        return cuerr(cudaStreamSynchronize(g->st));
+    }
+    std::vector<float> soa(6 * n);
+    const float *src[6] = {g->px, g->py, g->pz, g->vx, g->vy, g->vz};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 6 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(soa.data() + k * n, src[k], n * sizeof(float), cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) return SPE_ECUDA;
+    for (size_t i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (pos3) pos3[3 * i + a] = soa[a * n + i];
+            if (vel3) vel3[3 * i + a] = soa[(3 + a) * n + i];
+        }
+    return SPE_OK;
+}
+
+int spe_particle_count(spe_grid *g, size_t *n_out)
+{
+    if (!g || !n_out) return SPE_EINVAL;
+    *n_out = g->np;
+    return SPE_OK;
+}
+
+int spe_sync(spe_grid *g)
+{
+    if (!g) return SPE_EINVAL;
+    return cuerr(cudaStreamSynchronize(g->st));
+}
+
+int spe_launch_count(spe_grid *g, unsigned long long *count_out, int reset)
+{
+    if (!g || !count_out) return SPE_EINVAL;
+    *count_out = g->launches;
+    if (reset) g->launches = 0;
+    return SPE_OK;
+}
+
+int spe_profile_read(spe_grid *g, const char **names, unsigned long long *launches, double *ms, int cap)
+{
+    if (!g || cap < 0) return SPE_EINVAL;
+    if (cudaStreamSynchronize(g->st) != cudaSuccess) return SPE_ECUDA;
+    unsigned long long cnt[KIND_COUNT] = {0};
+    double tot[KIND_COUNT] = {0};
+    for (auto &r : g->prof) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.e0, r.e1) == cudaSuccess) tot[r.kind] += t;
+        cnt[r.kind]++;
+        g->evfree.push_back(r.e0);
+        g->evfree.push_back(r.e1);
+    }
+    g->prof.clear();
+    int w = 0;
+    for (int k = 0; k < KIND_COUNT && w < cap; ++k) {
+        if (names) names[w] = kKindNames[k];
+        if (launches) launches[w] = cnt[k];
+        if (ms) ms[w] = tot[k];
+        ++w;
+    }
+    return w;
+}
+
+}  // extern "C"

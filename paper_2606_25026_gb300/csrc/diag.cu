@@ -1,0 +1,94 @@
+// Diagnostics off the per-step path: mass / potential / interaction energy
+// and the maxima the CFL bound needs (Sec. 3.5), the stars' kinetic energy,
+// and the density field.  FP32 data, FP64 accumulation, fixed-order
+// (deterministic) grid reductions.
+#include "reduce.cuh"
+#include "spe_internal.cuh"
+
+namespace spe {
+
+constexpr int kDiagNT = 256;
+
+// Raw sums: out[0] = sum |psi|^2, out[1] = sum (|psi|^2 + rho_*) Phi, out[2] = sum |psi|^4,
+// out[3] = max |Phi|, out[4] = max |psi|^2 (the caller scales by dV, 1/2, kappa/2).
+__global__ void __launch_bounds__(kDiagNT) grid_diag_kernel(const float2 *__restrict__ psi,
+                                                            const float *__restrict__ phi, long long *dep,
+                                                            float dep_scale, float kappa, double dv, size_t n,
+                                                            double *partials, unsigned int *counter, double *out)
+{
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (size_t i = blockIdx.x * (size_t)kDiagNT + threadIdx.x; i < n; i += (size_t)gridDim.x * kDiagNT) {
+        const float2 v = psi[i];
+        const double a2 = (double)v.x * v.x + (double)v.y * v.y;
+        double rs = 0.0;
+        if (dep) {
+            rs = (double)dep[i] * dep_scale;
+            dep[i] = 0;
+        }
+        const double f = phi ? (double)phi[i] : 0.0;
+        acc[0] += a2;
+        acc[1] += (a2 + rs) * f;
+        acc[2] += a2 * a2;
+        acc[3] = fmax(acc[3], fabs(f));
+        acc[4] = fmax(acc[4], a2);
+    }
+    grid_reduce<5, kDiagNT>(acc, (1 << 3) | (1 << 4), partials, counter, out);
+}
+
+cudaError_t launch_grid_diag(const float2 *psi, const float *phi, long long *dep, float dep_scale, float kappa,
+                             double dv, size_t ncells, double *partials, unsigned int *counter, double *out,
+                             cudaStream_t st)
+{
+    size_t blocks = (ncells + kDiagNT - 1) / kDiagNT;
+    if (blocks > (size_t)kReduceBlocks) blocks = kReduceBlocks;
+    grid_diag_kernel<<<(unsigned)blocks, kDiagNT, 0, st>>>(psi, phi, dep, dep_scale, kappa, dv, ncells, partials,
+                                                           counter, out);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kDiagNT) particle_ke_kernel(const float *vx, const float *vy, const float *vz,
+                                                              const float *m, int n, double *partials,
+                                                              unsigned int *counter, double *out)
+{
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * kDiagNT + threadIdx.x; i < n; i += gridDim.x * kDiagNT) {
+        const double v2 = (double)vx[i] * vx[i] + (double)vy[i] * vy[i] + (double)vz[i] * vz[i];
+        acc[0] += 0.5 * (double)m[i] * v2;
+    }
+    grid_reduce<1, kDiagNT>(acc, 0, partials, counter, out);
+}
+
+cudaError_t launch_particle_ke(const float *vx, const float *vy, const float *vz, const float *m, int n,
+                               double *partials, unsigned int *counter, double *out, cudaStream_t st)
+{
+    int blocks = (n + kDiagNT - 1) / kDiagNT;
+    if (blocks < 1) blocks = 1;
+    if (blocks > kReduceBlocks) blocks = kReduceBlocks;
+    particle_ke_kernel<<<blocks, kDiagNT, 0, st>>>(vx, vy, vz, m, n, partials, counter, out);
+    return cudaGetLastError();
+}
+
+__global__ void density_kernel(const float2 *__restrict__ psi, long long *dep, float dep_scale, float *dens,
+                               size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = psi[i];
+        float r = v.x * v.x + v.y * v.y;
+        if (dep) {
+            r += (float)dep[i] * dep_scale;
+            dep[i] = 0;
+        }
+        dens[i] = r;
+    }
+}
+
+cudaError_t launch_density(const float2 *psi, long long *dep, float dep_scale, float *dens, size_t ncells,
+                           cudaStream_t st)
+{
+    size_t blocks = (ncells + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    density_kernel<<<(unsigned)blocks, 256, 0, st>>>(psi, dep, dep_scale, dens, ncells);
+    return cudaGetLastError();
+}
+
+}  // namespace spe

@@ -1,0 +1,135 @@
+// Strided passes: transforms along y or z, where consecutive points of a
+// line are S complex values apart and neighbouring lines (columns) are
+// adjacent in memory.
+//
+// One CTA owns a tile of T adjacent columns x N points (T = 32 for N <= 256,
+// 16 above), so every row of the tile is one coalesced 128/256-byte segment,
+// loaded and stored as float4 (two columns per thread).  The tile lives in
+// shared memory element-major (tile[n * T + t]) with lanes over t: the FFT
+// stages are then bank-conflict free without padding.
+//
+// Flags select forward transform, a pointwise multiply in k space, and the
+// inverse transform, all on the same tile:
+//   drift   (S_FWD | S_DRIFT | S_INV on the z axis of psi):
+//       psi_hat *= exp(-i eta k^2 dt / 2) / (nx ny nz), the separable product
+//       of three per-axis factors built in FP64 on the host
+//       [Sec. 3.1 step (b), Algorithm 1 "kinetic drift in Fourier space"];
+//   Poisson (S_FWD | S_POISSON | S_INV on the z axis of the half spectrum):
+//       rho_hat *= -4 pi G / (k^2 nx ny nz), zero at k = 0
+//       [Sec. 3.1 step (c), Sec. 3.2.1: zero mode removed].
+#include "fft_tile.cuh"
+#include "reduce.cuh"
+#include "spe_internal.cuh"
+
+namespace spe {
+
+template <int N> struct SCfg {
+    static constexpr int T = (N >= 384) ? 16 : 32;
+    static constexpr int TP = T;
+    static constexpr int NT = (N * T / 8 >= 256) ? 256 : ((N * T / 8 >= 128) ? 128 : 64);
+    static constexpr size_t smem = sizeof(float2) * N * TP;
+};
+
+template <int N>
+__global__ void __launch_bounds__(SCfg<N>::NT) spass_kernel(SParams p)
+{
+    constexpr int T = SCfg<N>::T, TP = SCfg<N>::TP, NT = SCfg<N>::NT, HT = T / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+    __shared__ float2 colfac[T];
+    __shared__ float colk2[T];
+    const int c0 = blockIdx.x * T;
+    const int b = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int flags = p.flags;
+    float2 *base = p.data + (size_t)b * p.bstride + c0;
+
+    if (tid < T) {
+        const int c = c0 + tid;
+        if (flags & S_DRIFT) {
+            colfac[tid] = (c < p.W) ? cscale(cmul(__ldg(&p.colf[c]), __ldg(&p.batchf[b])), p.norm)
+                                    : make_float2(0.f, 0.f);
+        }
+        if (flags & S_POISSON) colk2[tid] = (c < p.W) ? __ldg(&p.colk2[c]) + __ldg(&p.batchk2[b]) : 0.f;
+    }
+
+    for (int idx = tid; idx < N * HT; idx += NT) {
+        const int n = idx / HT, q = idx % HT;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c0 + 2 * q < p.W) v = *reinterpret_cast<const float4 *>(base + (size_t)n * p.S + 2 * q);
+        *reinterpret_cast<float4 *>(&tile[n * TP + 2 * q]) = v;
+    }
+    __syncthreads();
+    if (flags & S_FWD) tile_fft<N, T, TP, NT, -1>(tile, p.tw);
+
+    if (flags & (S_DRIFT | S_POISSON)) {
+        for (int idx = tid; idx < N * T; idx += NT) {
+            const int n = idx / T, t = idx % T;
+            float2 v = tile[n * TP + t];
+            if (flags & S_DRIFT) {
+                v = cmul(v, cmul(colfac[t], __ldg(&p.linef[n])));
+            } else {
+                const float k2 = colk2[t] + __ldg(&p.linek2[n]);
+                const float f = (k2 > 0.f) ? p.poisson * p.norm / k2 : 0.f;
+                v = cscale(v, f);
+            }
+            tile[n * TP + t] = v;
+        }
+        __syncthreads();
+    }
+    if (flags & S_INV) tile_fft<N, T, TP, NT, +1>(tile, p.tw);
+
+    if (flags & S_KIN) {
+        double acc = 0.0;
+        for (int idx = tid; idx < N * T; idx += NT) {
+            const int n = idx / T, t = idx % T;
+            if (c0 + t < p.W) {
+                const float2 v = tile[n * TP + t];
+                acc += (double)(__ldg(&p.linek2[n]) * (v.x * v.x + v.y * v.y));
+            }
+        }
+        double r[1] = {acc};
+        grid_reduce<1, NT>(r, 0, p.partials, p.counter, p.result);
+        return;
+    }
+
+    for (int idx = tid; idx < N * HT; idx += NT) {
+        const int n = idx / HT, q = idx % HT;
+        if (c0 + 2 * q < p.W)
+            *reinterpret_cast<float4 *>(base + (size_t)n * p.S + 2 * q) =
+                *reinterpret_cast<const float4 *>(&tile[n * TP + 2 * q]);
+    }
+}
+
+template <int N>
+static cudaError_t launch_s_n(const SParams &p, cudaStream_t st, int *blocks_out)
+{
+    dim3 grid((p.W + SCfg<N>::T - 1) / SCfg<N>::T, p.batches);
+    if (blocks_out) *blocks_out = grid.x * grid.y;
+    spass_kernel<N><<<grid, SCfg<N>::NT, SCfg<N>::smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spass(int n, const SParams &p, cudaStream_t st, int *blocks_out)
+{
+    switch (n) {
+#define X(n) \
+    case n: return launch_s_n<n>(p, st, blocks_out);
+        SPE_FOR_EACH_N(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t setup_spass_attributes()
+{
+    cudaError_t e = cudaSuccess;
+#define X(n)                                                                                                    \
+    if (e == cudaSuccess)                                                                                        \
+        e = cudaFuncSetAttribute(spass_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCfg<n>::smem);
+    SPE_FOR_EACH_N(X)
+#undef X
+    return e;
+}
+
+}  // namespace spe

@@ -1,0 +1,137 @@
+// Internal declarations shared by the libspe translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spe {
+
+// Supported axis lengths (each instantiates its own FFT kernels).
+#define SPE_FOR_EACH_N(X) \
+    X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
+
+bool supported_n(int n);
+
+// ---------------------------------------------------------------- x passes
+// Lines along x are contiguous rows of nx complex values; rows = ny * nz.
+// The half-spectrum buffer holds W = nx/2 + 1 complex values per row at a
+// row pitch of P (P = W rounded up to a multiple of 4 complex = 32 bytes).
+
+enum XFlags : int {
+    X_HAS_PHI = 1 << 0,    // rebuild Phi on the row from the half spectrum (C2R)
+    X_WRITE_PHI = 1 << 1,  // store Phi (real) to phi_out
+    X_KICK = 1 << 2,       // psi *= exp(-i (Phi + kappa|psi|^2) kick_scale)
+    X_FFT = 1 << 3,        // forward x transform of psi after the kick
+    X_IFFT = 1 << 4,       // inverse x transform of psi before the density
+    X_DEP = 1 << 5,        // add the fixed-point star deposit to rho and clear it
+    X_MASS = 1 << 6,       // reduce sum |psi|^2 into diag[0] (deterministic)
+    X_R2C = 1 << 7,        // forward real-to-complex x transform of rho into the half spectrum
+    X_KIN = 1 << 8,        // reduce sum_k kx^2 |psi_hat|^2 (energy diagnostic), no store
+};
+
+struct XParams {
+    float2 *psi;              // rows of nx complex
+    float2 *phik;             // rows of P complex (half spectrum)
+    float *phi_out;           // rows of nx floats (X_WRITE_PHI)
+    long long *dep;           // fixed-point star mass per node (X_DEP)
+    const float2 *tw;         // nx twiddles
+    const float *k2;          // nx values of kx^2 (X_KIN)
+    int rows;                 // ny * nz
+    int P;                    // half-spectrum row pitch (complex)
+    float kick_scale;         // dt_kick / eta
+    float kappa;
+    float dep_scale;          // mass quantum / cell volume
+    double *partials;         // per-block partial sums
+    unsigned int *counter;    // last-block ticket (returns to 0 after use)
+    double *result;           // where the final reduction goes
+    int *status;              // device status word (bit 0: non-finite mass)
+    int flags;
+};
+
+// ---------------------------------------------------------------- strided passes
+// Lines along y or z: point n of column c in batch b sits at
+//   data[b * bstride + c + n * S]     (complex units), c < W.
+
+enum SFlags : int {
+    S_FWD = 1 << 0,
+    S_INV = 1 << 1,
+    S_DRIFT = 1 << 2,     // multiply by colf[c] * batchf[b] * linef[n] * norm (complex tables)
+    S_POISSON = 1 << 3,   // multiply by -4 pi G norm / (colk2[c] + batchk2[b] + linek2[n]), 0 at k = 0
+    S_KIN = 1 << 4,       // reduce sum_k linek2[n] |X|^2 after the forward transform, no store
+};
+
+struct SParams {
+    float2 *data;
+    long long S;          // element stride along the line
+    long long bstride;    // batch stride
+    int W;                // live columns
+    int batches;
+    const float2 *tw;     // N twiddles
+    const float2 *colf, *batchf, *linef;   // drift factors
+    const float *colk2, *batchk2, *linek2; // k^2 tables
+    float norm;           // 1 / (nx ny nz) folded into the multiply
+    float poisson;        // -4 pi G
+    double *partials;
+    unsigned int *counter;
+    double *result;
+    int flags;
+};
+
+// ---------------------------------------------------------------- particles
+
+struct PParams {
+    float *x, *y, *z, *vx, *vy, *vz;
+    const float *m;
+    const float *phi;        // nodes, x fastest
+    long long *dep;          // fixed-point deposit (PK_DEPOSIT)
+    int n;
+    int nx, ny, nz;
+    float Lx, Ly, Lz;
+    float inv_dx, inv_dy, inv_dz;      // 1/dx
+    float gx_scale, gy_scale, gz_scale; // 1/(2 dx)
+    float kick;              // dt for the velocity update (0 = none)
+    float drift;             // dt for the position update (0 = none)
+    float inv_quantum;       // 1 / mass quantum of the deposit
+    int flags;
+};
+
+enum PFlags : int {
+    PK_KICK = 1 << 0,
+    PK_DRIFT = 1 << 1,
+    PK_DEPOSIT = 1 << 2,
+};
+
+// ---------------------------------------------------------------- launchers
+// Each returns cudaGetLastError() after the launch.  blocks_out (if given)
+// receives the grid size, for the reductions' partial counts.
+
+cudaError_t launch_xpass(int nx, const XParams &p, cudaStream_t st, int *blocks_out);
+cudaError_t launch_spass(int n, const SParams &p, cudaStream_t st, int *blocks_out);
+size_t xpass_rows_per_block(int nx);
+cudaError_t setup_kernel_attributes();
+
+cudaError_t launch_particles(const PParams &p, cudaStream_t st);
+cudaError_t launch_particles_to_soa(const float *pos3, const float *vel3, const float *mass, int n,
+                                    float *x, float *y, float *z, float *vx, float *vy, float *vz, float *m,
+                                    float Lx, float Ly, float Lz, cudaStream_t st);
+cudaError_t launch_particles_from_soa(const float *x, const float *y, const float *z, const float *vx,
+                                      const float *vy, const float *vz, int n, float *pos3, float *vel3,
+                                      cudaStream_t st);
+
+// Grid diagnostics (raw sums): out[0] = sum |psi|^2, out[1] = sum (|psi|^2 + rho_*) phi,
+// out[2] = sum |psi|^4, out[3] = max |phi|, out[4] = max |psi|^2; clears dep if given.
+// Deterministic (fixed-order) FP64 accumulation.
+cudaError_t launch_grid_diag(const float2 *psi, const float *phi, long long *dep, float dep_scale, float kappa,
+                             double dv, size_t ncells, double *partials, unsigned int *counter, double *out,
+                             cudaStream_t st);
+// out[0] = 1/2 sum m v^2
+cudaError_t launch_particle_ke(const float *vx, const float *vy, const float *vz, const float *m, int n,
+                               double *partials, unsigned int *counter, double *out, cudaStream_t st);
+// dens[i] = |psi_i|^2 + dep_i * dep_scale; clears dep if given.
+cudaError_t launch_density(const float2 *psi, long long *dep, float dep_scale, float *dens, size_t ncells,
+                           cudaStream_t st);
+
+// Maximum number of partial-sum slots any reduction uses.
+constexpr int kMaxPartials = 1 << 17;
+constexpr int kReduceBlocks = 1024;
+
+}  // namespace spe

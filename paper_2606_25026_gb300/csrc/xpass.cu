@@ -1,0 +1,215 @@
+// x-axis passes: lines along x are contiguous rows of the field.
+//
+// One CTA owns T = 16 consecutive rows.  Rows are staged in shared memory
+// element-major (tile[n * (T+1) + t], the +1 pad keeps both the row-wise
+// global<->shared copies and the FFT stages free of bank conflicts).  What a
+// launch does is selected by XParams::flags; the step uses two combinations:
+//
+//   kick pass     (X_HAS_PHI | X_KICK | X_FFT [| X_WRITE_PHI]):
+//       Phi rows rebuilt from the x half spectrum (inverse real transform,
+//       two rows packed as one complex line), psi *= exp(-i (Phi +
+//       kappa|psi|^2) dt_k / eta)  [Sec. 3.1 steps (a)/(d), Algorithm 1],
+//       then the forward x transform of psi  [step (b), first axis].
+//   density pass  (X_IFFT | X_MASS | X_R2C [| X_DEP]):
+//       inverse x transform of psi  [step (b), last axis], rho = |psi|^2 +
+//       rho_*  [step (c)], the mass reduced on the fly, and the forward real
+//       x transform of rho into the half spectrum  [step (c), first axis].
+#include "fft_tile.cuh"
+#include "reduce.cuh"
+#include "spe_internal.cuh"
+
+namespace spe {
+
+template <int N> struct XCfg {
+    static constexpr int T = 16;
+    static constexpr int TP = T + 1;
+    static constexpr int NT = (N * T / 8 >= 256) ? 256 : ((N * T / 8 >= 128) ? 128 : 64);
+    static constexpr size_t smem = sizeof(float2) * N * TP + sizeof(float) * N * T;
+};
+
+template <int N>
+__global__ void __launch_bounds__(XCfg<N>::NT) xpass_kernel(XParams p)
+{
+    constexpr int T = XCfg<N>::T, TP = XCfg<N>::TP, NT = XCfg<N>::NT, H = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+    float *aux = reinterpret_cast<float *>(tile + N * TP);  // aux[t * N + n]: real row t
+    const int row0 = blockIdx.x * T;
+    const int tid = threadIdx.x;
+    const int flags = p.flags;
+
+    // ---- Phi rows from the half spectrum: rows (2m, 2m+1) as one complex line
+    if (flags & X_HAS_PHI) {
+        for (int idx = tid; idx < (T / 2) * N; idx += NT) {
+            const int n = idx % N, m = idx / N;
+            const int ra = row0 + 2 * m;
+            float2 A = make_float2(0.f, 0.f), B = A;
+            if (ra + 1 < p.rows) {
+                const int kk = (n <= H) ? n : N - n;
+                A = p.phik[(size_t)ra * p.P + kk];
+                B = p.phik[(size_t)(ra + 1) * p.P + kk];
+                if (n > H) { A.y = -A.y; B.y = -B.y; }
+                if (n == 0 || n == H) { A.y = 0.f; B.y = 0.f; }
+            }
+            tile[n * TP + m] = make_float2(A.x - B.y, A.y + B.x);
+        }
+        __syncthreads();
+        tile_fft<N, T / 2, TP, NT, +1>(tile, p.tw);
+        for (int idx = tid; idx < (T / 2) * N; idx += NT) {
+            const int n = idx % N, m = idx / N;
+            const float2 z = tile[n * TP + m];
+            aux[(2 * m) * N + n] = z.x;
+            aux[(2 * m + 1) * N + n] = z.y;
+            const int ra = row0 + 2 * m;
+            if ((flags & X_WRITE_PHI) && ra + 1 < p.rows) {
+                p.phi_out[(size_t)ra * N + n] = z.x;
+                p.phi_out[(size_t)(ra + 1) * N + n] = z.y;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- kick and forward x transform of psi
+    if (flags & (X_KICK | X_FFT)) {
+        const bool fft = flags & X_FFT;
+        for (int idx = tid; idx < T * N; idx += NT) {
+            const int n = idx % N, t = idx / N;
+            const int row = row0 + t;
+            float2 v = make_float2(0.f, 0.f);
+            if (row < p.rows) v = p.psi[(size_t)row * N + n];
+            if (flags & X_KICK) {
+                const float a2 = v.x * v.x + v.y * v.y;
+                const float phi = (flags & X_HAS_PHI) ? aux[t * N + n] : 0.f;
+                float s, c;
+                sincosf((phi + p.kappa * a2) * p.kick_scale, &s, &c);
+                v = make_float2(v.x * c + v.y * s, v.y * c - v.x * s);  // v * exp(-i phase)
+            }
+            if (fft) tile[n * TP + t] = v;
+            else if (row < p.rows) p.psi[(size_t)row * N + n] = v;
+        }
+        if (fft) {
+            __syncthreads();
+            tile_fft<N, T, TP, NT, -1>(tile, p.tw);
+            for (int idx = tid; idx < T * N; idx += NT) {
+                const int n = idx % N, t = idx / N;
+                const int row = row0 + t;
+                if (row < p.rows) p.psi[(size_t)row * N + n] = tile[n * TP + t];
+            }
+        }
+    }
+
+    // ---- inverse x transform, density, mass, real-to-complex x transform of rho
+    if (flags & (X_R2C | X_MASS | X_IFFT)) {
+        const bool ifft = flags & X_IFFT;
+        if (ifft) {
+            for (int idx = tid; idx < T * N; idx += NT) {
+                const int n = idx % N, t = idx / N;
+                const int row = row0 + t;
+                tile[n * TP + t] = (row < p.rows) ? p.psi[(size_t)row * N + n] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            tile_fft<N, T, TP, NT, +1>(tile, p.tw);
+        }
+        float msum = 0.f;
+        for (int idx = tid; idx < T * N; idx += NT) {
+            const int n = idx % N, t = idx / N;
+            const int row = row0 + t;
+            float2 v;
+            if (ifft) {
+                v = tile[n * TP + t];
+                if (row < p.rows) p.psi[(size_t)row * N + n] = v;
+            } else {
+                v = (row < p.rows) ? p.psi[(size_t)row * N + n] : make_float2(0.f, 0.f);
+            }
+            float r = v.x * v.x + v.y * v.y;
+            msum += r;
+            if ((flags & X_DEP) && row < p.rows) {
+                long long *d = p.dep + (size_t)row * N + n;
+                r += (float)(*d) * p.dep_scale;
+                *d = 0;
+            }
+            aux[t * N + n] = r;
+        }
+        __syncthreads();
+        if (flags & X_R2C) {
+            for (int idx = tid; idx < (T / 2) * N; idx += NT) {
+                const int n = idx % N, m = idx / N;
+                tile[n * TP + m] = make_float2(aux[(2 * m) * N + n], aux[(2 * m + 1) * N + n]);
+            }
+            __syncthreads();
+            tile_fft<N, T / 2, TP, NT, -1>(tile, p.tw);
+            // separate the two real rows: A_k = (Z_k + conj Z_{N-k}) / 2, B_k = (Z_k - conj Z_{N-k}) / (2i)
+            for (int idx = tid; idx < (T / 2) * (H + 1); idx += NT) {
+                const int k = idx % (H + 1), m = idx / (H + 1);
+                const int ra = row0 + 2 * m;
+                const float2 Z = tile[k * TP + m];
+                const float2 Zc = cconj(tile[((N - k) % N) * TP + m]);
+                const float2 A = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
+                const float2 D = csub(Z, Zc);
+                const float2 B = make_float2(0.5f * D.y, -0.5f * D.x);
+                if (ra + 1 < p.rows) {
+                    p.phik[(size_t)ra * p.P + k] = A;
+                    p.phik[(size_t)(ra + 1) * p.P + k] = B;
+                }
+            }
+        }
+        if (flags & X_MASS) {
+            double v[1] = {(double)msum};
+            grid_reduce<1, NT>(v, 0, p.partials, p.counter, p.result);
+        }
+    }
+
+    // ---- kinetic-energy diagnostic along x: sum_k kx^2 |F_x psi|^2 (no store)
+    if (flags & X_KIN) {
+        for (int idx = tid; idx < T * N; idx += NT) {
+            const int n = idx % N, t = idx / N;
+            const int row = row0 + t;
+            tile[n * TP + t] = (row < p.rows) ? p.psi[(size_t)row * N + n] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        tile_fft<N, T, TP, NT, -1>(tile, p.tw);
+        double acc = 0.0;
+        for (int idx = tid; idx < T * N; idx += NT) {
+            const int n = idx % N, t = idx / N;
+            const float2 v = tile[n * TP + t];
+            acc += (double)(__ldg(&p.k2[n]) * (v.x * v.x + v.y * v.y));
+        }
+        double v[1] = {acc};
+        grid_reduce<1, NT>(v, 0, p.partials, p.counter, p.result);
+    }
+}
+
+template <int N>
+static cudaError_t launch_x_n(const XParams &p, cudaStream_t st, int *blocks_out)
+{
+    const int blocks = (p.rows + XCfg<N>::T - 1) / XCfg<N>::T;
+    if (blocks_out) *blocks_out = blocks;
+    xpass_kernel<N><<<blocks, XCfg<N>::NT, XCfg<N>::smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xpass(int nx, const XParams &p, cudaStream_t st, int *blocks_out)
+{
+    switch (nx) {
+#define X(n) \
+    case n: return launch_x_n<n>(p, st, blocks_out);
+        SPE_FOR_EACH_N(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t xpass_rows_per_block(int) { return 16; }
+
+cudaError_t setup_xpass_attributes()
+{
+    cudaError_t e = cudaSuccess;
+#define X(n)                                                                                                    \
+    if (e == cudaSuccess)                                                                                        \
+        e = cudaFuncSetAttribute(xpass_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XCfg<n>::smem);
+    SPE_FOR_EACH_N(X)
+#undef X
+    return e;
+}
+
+}  // namespace spe

@@ -1,0 +1,279 @@
+"""Thin ctypes binding over the libspe C ABI (include/spe.h).
+
+Argument marshalling only: every step of the solver runs in libspe's CUDA kernels.  PyTorch
+supplies device memory (the grid's workspace is a torch uint8 tensor) and the CUDA stream.
+There is no fallback: if libspe.so is missing or no GPU is present, creating a grid raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspe.so")
+
+# status codes and flags (mirror include/spe.h)
+SPE_OK, SPE_EINVAL, SPE_ENOMEM, SPE_ECUDA, SPE_ECFL, SPE_ENONFINITE, SPE_ETIMEOUT, SPE_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+SPE_HOST, SPE_DEVICE = 0, 1
+SPE_GRAVITY_OFF = 1 << 0
+SPE_NO_CFL_CHECK = 1 << 1
+SPE_ASYNC = 1 << 2
+SPE_PROFILE = 1 << 3
+SPE_NO_GRAPH = 1 << 4
+
+SUPPORTED_N = (4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024)
+
+# every entry point include/spe.h declares
+EXPORTED = (
+    "spe_workspace_bytes", "spe_create_grid", "spe_destroy", "spe_set_ic", "spe_add_particles",
+    "spe_clear_particles", "spe_step", "spe_suggest_dt", "spe_density", "spe_potential", "spe_energy",
+    "spe_last_mass", "spe_get_psi", "spe_get_particles", "spe_particle_count", "spe_sync",
+    "spe_launch_count", "spe_profile_read", "spe_strerror",
+)
+
+
+class SpeError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{what}: {strerror(status)} (status {status})")
+        self.status = status
+
+
+class spe_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+        ("hbar_over_m", ctypes.c_double), ("G", ctypes.c_double), ("kappa", ctypes.c_double),
+        ("max_particles", ctypes.c_size_t), ("flags", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class spe_energy_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("mass", "kinetic", "potential", "interaction", "star_kinetic", "total", "max_abs_phi")]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libspe.so (built by __graft_entry__.build() / paper_2606_25026_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libspe.so not built at {path}; run paper_2606_25026_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, S, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_double
+    fp = ctypes.c_void_p
+    sig = {
+        "spe_workspace_bytes": (I, [ctypes.POINTER(spe_config), ctypes.POINTER(S)]),
+        "spe_create_grid": (I, [ctypes.POINTER(spe_config), P, S, ctypes.POINTER(P)]),
+        "spe_destroy": (I, [P]),
+        "spe_set_ic": (I, [P, P, S, I]),
+        "spe_add_particles": (I, [P, S, fp, fp, fp, I]),
+        "spe_clear_particles": (I, [P]),
+        "spe_step": (I, [P, I, D]),
+        "spe_suggest_dt": (I, [P, D, ctypes.POINTER(D)]),
+        "spe_density": (I, [P, fp, I]),
+        "spe_potential": (I, [P, fp, I]),
+        "spe_energy": (I, [P, ctypes.POINTER(spe_energy_t)]),
+        "spe_last_mass": (I, [P, ctypes.POINTER(D)]),
+        "spe_get_psi": (I, [P, P, I]),
+        "spe_get_particles": (I, [P, fp, fp, I]),
+        "spe_particle_count": (I, [P, ctypes.POINTER(S)]),
+        "spe_sync": (I, [P]),
+        "spe_launch_count": (I, [P, ctypes.POINTER(ctypes.c_ulonglong), I]),
+        "spe_profile_read": (I, [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_ulonglong),
+                                 ctypes.POINTER(D), I]),
+        "spe_strerror": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return load_library().spe_strerror(int(status)).decode()
+    except ImportError:
+        return f"status {status}"
+
+
+def _check(status, what):
+    if status != SPE_OK:
+        raise SpeError(status, what)
+
+
+def _ptr_where(a):
+    """(pointer, where, keepalive) for a numpy array or a torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return a.data_ptr(), (SPE_DEVICE if a.is_cuda else SPE_HOST), a
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(a)
+    return a.ctypes.data, SPE_HOST, a
+
+
+class Grid:
+    """One periodic grid on the current CUDA device.  Methods map one to one onto the C ABI:
+    create_grid (the constructor), set_ic, add_particles, clear_particles, step, suggest_dt,
+    density, potential, energy, last_mass, get_psi, get_particles, particle_count, sync,
+    launch_count, profile_read, destroy."""
+
+    def __init__(self, nx, ny=None, nz=None, L=1.0, hbar_over_m=1.0, G=1.0, kappa=0.0, max_particles=0,
+                 flags=0, stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libspe needs a CUDA device; there is no CPU fallback")
+        self._lib = load_library()
+        ny = nx if ny is None else ny
+        nz = nx if nz is None else nz
+        if np.isscalar(L):
+            L = (float(L),) * 3
+        self.shape = (nz, ny, nx)
+        self.ncells = nx * ny * nz
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.cfg = spe_config(nx, ny, nz, *(float(v) for v in L), float(hbar_over_m), float(G), float(kappa),
+                              int(max_particles), int(flags), ctypes.c_void_p(self.stream.cuda_stream))
+        nbytes = ctypes.c_size_t()
+        _check(self._lib.spe_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)), "spe_workspace_bytes")
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        _check(self._lib.spe_create_grid(ctypes.byref(self.cfg), ctypes.c_void_p(self.workspace.data_ptr()),
+                                         nbytes.value, ctypes.byref(h)), "spe_create_grid")
+        self._h = h
+
+    # -- lifetime
+    def destroy(self):
+        if getattr(self, "_h", None):
+            self._lib.spe_destroy(self._h)
+            self._h = None
+            self.workspace = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    # -- state in
+    def set_ic(self, psi):
+        """psi: complex64 (nz, ny, nx) numpy array (host) or torch tensor (host or device)."""
+        import torch
+        if isinstance(psi, torch.Tensor):
+            if psi.dtype != torch.complex64:
+                raise TypeError("psi must be complex64")
+            ptr, where, keep = _ptr_where(psi.contiguous())
+        else:
+            ptr, where, keep = _ptr_where(np.ascontiguousarray(psi, dtype=np.complex64))
+        _check(self._lib.spe_set_ic(self._h, ctypes.c_void_p(ptr), self.ncells, where), "spe_set_ic")
+
+    def add_particles(self, pos, vel, mass):
+        import torch
+        if isinstance(pos, torch.Tensor):
+            pos, vel, mass = (t.contiguous().float() for t in (pos, vel, mass))
+        else:
+            pos = np.ascontiguousarray(pos, dtype=np.float32).reshape(-1, 3)
+            vel = np.ascontiguousarray(vel, dtype=np.float32).reshape(-1, 3)
+            mass = np.ascontiguousarray(mass, dtype=np.float32).reshape(-1)
+        n = int(mass.shape[0])
+        pp, where, k1 = _ptr_where(pos)
+        vp, w2, k2 = _ptr_where(vel)
+        mp, w3, k3 = _ptr_where(mass)
+        if not (where == w2 == w3):
+            raise ValueError("pos, vel and mass must live in the same memory")
+        _check(self._lib.spe_add_particles(self._h, n, ctypes.c_void_p(pp), ctypes.c_void_p(vp),
+                                           ctypes.c_void_p(mp), where), "spe_add_particles")
+
+    def clear_particles(self):
+        _check(self._lib.spe_clear_particles(self._h), "spe_clear_particles")
+
+    # -- stepping
+    def step(self, nsteps, dt):
+        _check(self._lib.spe_step(self._h, int(nsteps), float(dt)), "spe_step")
+
+    def suggest_dt(self, safety=0.9):
+        out = ctypes.c_double()
+        _check(self._lib.spe_suggest_dt(self._h, float(safety), ctypes.byref(out)), "spe_suggest_dt")
+        return out.value
+
+    def sync(self):
+        _check(self._lib.spe_sync(self._h), "spe_sync")
+
+    # -- state out
+    def _field_out(self, fn, what, out, dtype_np, dtype_t):
+        import torch
+        if out is None:
+            out = np.empty(self.shape, dtype=dtype_np)
+        if isinstance(out, torch.Tensor):
+            if out.dtype != dtype_t or not out.is_contiguous() or out.numel() != self.ncells:
+                raise ValueError(f"{what}: output tensor must be contiguous {dtype_t} of {self.ncells} elements")
+        ptr, where, keep = _ptr_where(out)
+        _check(fn(self._h, ctypes.c_void_p(ptr), where), what)
+        return out
+
+    def get_psi(self, out=None):
+        import torch
+        return self._field_out(self._lib.spe_get_psi, "spe_get_psi", out, np.complex64, torch.complex64)
+
+    def density(self, out=None):
+        import torch
+        return self._field_out(self._lib.spe_density, "spe_density", out, np.float32, torch.float32)
+
+    def potential(self, out=None):
+        import torch
+        return self._field_out(self._lib.spe_potential, "spe_potential", out, np.float32, torch.float32)
+
+    def energy(self) -> dict:
+        e = spe_energy_t()
+        _check(self._lib.spe_energy(self._h, ctypes.byref(e)), "spe_energy")
+        return {n: getattr(e, n) for n, _ in spe_energy_t._fields_}
+
+    def last_mass(self) -> float:
+        out = ctypes.c_double()
+        _check(self._lib.spe_last_mass(self._h, ctypes.byref(out)), "spe_last_mass")
+        return out.value
+
+    def particle_count(self) -> int:
+        out = ctypes.c_size_t()
+        _check(self._lib.spe_particle_count(self._h, ctypes.byref(out)), "spe_particle_count")
+        return out.value
+
+    def get_particles(self):
+        n = self.particle_count()
+        pos = np.empty((n, 3), np.float32)
+        vel = np.empty((n, 3), np.float32)
+        if n:
+            _check(self._lib.spe_get_particles(self._h, pos.ctypes.data, vel.ctypes.data, SPE_HOST),
+                   "spe_get_particles")
+        return pos, vel
+
+    # -- accounting
+    def launch_count(self, reset=False) -> int:
+        out = ctypes.c_ulonglong()
+        _check(self._lib.spe_launch_count(self._h, ctypes.byref(out), int(bool(reset))), "spe_launch_count")
+        return out.value
+
+    def profile_read(self) -> dict:
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        launches = (ctypes.c_ulonglong * cap)()
+        ms = (ctypes.c_double * cap)()
+        k = self._lib.spe_profile_read(self._h, names, launches, ms, cap)
+        if k < 0:
+            raise SpeError(k, "spe_profile_read")
+        return {names[i].decode(): (launches[i], ms[i]) for i in range(k)}
+
+
+def create_grid(*args, **kwargs) -> Grid:
+    return Grid(*args, **kwargs)
