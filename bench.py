@@ -1,0 +1,382 @@
+"""Benchmark: split-step Schroedinger-Poisson grid-cell-steps/s on GB300.
+
+Workload (default): 256^3 complex64 grid, central soliton + granular halo, 1e6 Plummer stars
+(5% of the mass), CIC coupling, dt from the Sec. 3.5 kinetic CFL term.  One "step" is one full
+kick-drift-kick step of the field and the stars (every kernel of the hot path).
+
+Prints one JSON line (rank 0).  ``value`` is device-resident throughput (inputs already in HBM,
+CUDA events on the grid's stream, K steps in one spe_step call).  ``e2e`` is the same metric through
+the C ABI with host buffers: pinned-host upload of the initial field and stars, K single-step calls
+each followed by a device->host read of the step's mass, and the final download of psi and the
+stars, all inside the timed region.  ``roofline`` is the dominant kernel's algorithmic bytes over
+its CUDA-event duration, against the measured HBM copy bandwidth.  ``cpu_baseline`` is the FP64
+oracle on the host cores on one step of the same workload.
+
+Multi-GPU: the grid does not shard here; N ranks run N independent replicas (weak scaling).
+``--impl reference`` times the FP64 CPU oracle as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Algorithmic HBM bytes per grid cell for one launch of each kernel kind, with stars (the
+# fused axis-pass schedule): reads + writes that the step cannot avoid at that pass.
+#   x_kick_fwd        : R psi 8 + R Phi_hat 4 + W psi 8 + W Phi 4           = 24
+#   y_fft_psi         : R 8 + W 8                                           = 16
+#   z_fft_drift       : R 8 + W 8                                           = 16
+#   x_inv_density_r2c : R psi_hat 8 + R deposit 8 + W deposit 8 (clear) + W psi 8 + W rho_hat 4 = 36
+#   y_fft_rho, z_fft_poisson : R 4 + W 4 (half spectrum)                    = 8
+#   x_kick_final      : R psi 8 + R Phi_hat 4 + W psi 8 + W Phi 4           = 24
+BYTES_PER_CELL = {
+    "x_kick_fwd": 24.0, "y_fft_psi": 16.0, "z_fft_drift": 16.0, "x_inv_density_r2c": 36.0,
+    "y_fft_rho": 8.0, "z_fft_poisson": 8.0, "x_kick_final": 24.0,
+}
+BYTES_PER_CELL_NO_STARS = dict(BYTES_PER_CELL, x_kick_fwd=20.0, x_inv_density_r2c=20.0, x_kick_final=20.0)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="halo256_stars1e6",
+                    choices=["halo256_stars1e6", "halo512", "packets32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_25026_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """dram bytes per launch from the committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = source_hash()
+    for line in open(path):
+        if line.startswith("#") or "=" not in line:
+            continue
+        kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source_hash") == want:
+            return float(kv["bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"spe_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.remove(self.path)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def make_inputs(workload):
+    from paper_2606_25026_gb300 import inputs
+    psi, pos, vel, mass, dt, _ = inputs.make_workload(workload)
+    return (psi.astype(np.complex64), pos.astype(np.float32), vel.astype(np.float32), mass.astype(np.float32),
+            float(dt))
+
+
+def cpu_baseline(psi, pos, vel, mass, dt):
+    """The FP64 oracle on the host cores: one KDK step of the same workload (the Phi(0) solve
+    before it is not timed).  Returns (cell-steps/s, threads, seconds, oracle psi after 1 step)."""
+    import oracle
+    oracle.build()
+    nz, ny, nx = psi.shape
+    o = oracle.Oracle(nx, ny, nz, 1.0, G=1.0)
+    o.set_ic(psi.astype(np.complex128))
+    if len(mass):
+        o.set_particles(pos.astype(np.float64), vel.astype(np.float64), mass.astype(np.float64))
+    o.potential()
+    t0 = time.perf_counter()
+    o.step(1, dt)
+    sec = time.perf_counter() - t0
+    return psi.size / sec, oracle.threads(), sec, o
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    psi, pos, vel, mass, dt = make_inputs(args.workload)
+    import oracle
+    oracle.build()
+    nz, ny, nx = psi.shape
+    o = oracle.Oracle(nx, ny, nz, 1.0, G=1.0)
+    o.set_ic(psi.astype(np.complex128))
+    if len(mass):
+        o.set_particles(pos.astype(np.float64), vel.astype(np.float64), mass.astype(np.float64))
+    budget = 150.0
+    t_start = time.perf_counter()
+    for _ in range(min(args.warmup, 1)):
+        o.step(1, dt)
+    done, t_tot = 0, 0.0
+    while done < args.steps and (time.perf_counter() - t_start) < budget:
+        t0 = time.perf_counter()
+        o.step(1, dt)
+        t_tot += time.perf_counter() - t0
+        done += 1
+    value = psi.size * done / t_tot
+    line = {
+        "impl": "reference", "metric": "grid_cell_steps_per_s", "value": value, "unit": "cell-steps/s",
+        "n_gpus": world, "steps": done, "steps_requested": args.steps, "warmup": min(args.warmup, 1),
+        "ms_per_step": 1e3 * t_tot / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": list(psi.shape[::-1]), "n_star": int(len(mass)), "dt": dt},
+        "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": oracle.threads(), "kind": "oracle",
+                         "sample": f"{done} oracle KDK steps of the workload (time-bounded at {budget:.0f} s)"},
+        "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2606_25026_gb300 import build as spe_build
+    if rank == 0 or world == 1:
+        spe_build.build()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        spe_build.build()
+    torch.cuda.set_device(local)
+    from paper_2606_25026_gb300 import spe
+
+    psi, pos, vel, mass, dt = make_inputs(args.workload)
+    nz, ny, nx = psi.shape
+    ncells = psi.size
+    nstar = len(mass)
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region
+    g = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, flags=spe.SPE_ASYNC | spe.SPE_PROFILE,
+                 stream=stream)
+    g.set_ic(torch.from_numpy(psi).cuda())
+    if nstar:
+        g.add_particles(torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda(), torch.from_numpy(mass).cuda())
+    g.step(args.warmup, dt)
+    g.sync()
+    g.profile_read()
+    g.launch_count(reset=True)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    g.step(args.steps, dt)
+    ev1.record(stream)
+    ev1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = g.launch_count()
+    prof = g.profile_read()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ncells * args.steps / (ms * 1e-3)
+
+    # roofline of the dominant kernel
+    bpc = BYTES_PER_CELL if nstar else BYTES_PER_CELL_NO_STARS
+    dom = max((k for k in prof if k in bpc), key=lambda k: prof[k][1])
+    n_launch, dom_ms = prof[dom]
+    per_launch_s = dom_ms * 1e-3 / max(n_launch, 1)
+    alg_bytes = bpc[dom] * ncells
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = recorded_traffic(dom, args.workload)
+    step_bytes = sum(bpc[k] for k in ("x_kick_fwd", "y_fft_psi", "z_fft_drift", "x_inv_density_r2c")) + \
+        2 * bpc["y_fft_psi"] + (3 * 8.0)
+    kernel_split = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / max(1e-9, sum(
+        x[1] for x in prof.values())), 4)} for k, v in prof.items() if v[0]}
+
+    line = {
+        "metric": "grid_cell_steps_per_s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": [nx, ny, nz], "n_star": nstar, "dt": dt,
+                   "l2": f"working set {g.workspace.numel() / 2**20:.0f} MiB > 129 MB L2 (no flush needed)",
+                   "parallelism": f"{world} independent replica(s)"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                     else "fallback 6800 GB/s", "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "bytes_per_cell": bpc[dom], "launches": n_launch,
+                     "avg_launch_ms": per_launch_s * 1e3},
+        "step_roofline": {"bytes_per_cell_step": step_bytes,
+                          "achieved_GBs": step_bytes * ncells * args.steps / (ms * 1e-3) / 1e9,
+                          "frac": step_bytes * ncells * args.steps / (ms * 1e-3) / 1e9 / peak},
+        "kernels": kernel_split,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    g.destroy()
+    del g
+    torch.cuda.empty_cache()
+
+    # ---------------- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        h_psi = torch.from_numpy(psi).pin_memory()
+        h_pos = torch.from_numpy(pos).pin_memory()
+        h_vel = torch.from_numpy(vel).pin_memory()
+        h_mass = torch.from_numpy(mass).pin_memory()
+        o_psi = torch.empty(psi.shape, dtype=torch.complex64).pin_memory()
+        o_pos = np.empty((nstar, 3), np.float32)
+        ge = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, stream=stream)
+        ke = max(1, min(args.steps, 200))
+        # warm the path once
+        ge.set_ic(h_psi)
+        if nstar:
+            ge.add_particles(h_pos, h_vel, h_mass)
+        ge.step(2, dt)
+        ge.last_mass()
+        barrier()
+        t0 = time.perf_counter()
+        ge.set_ic(h_psi)
+        ge.clear_particles()
+        if nstar:
+            ge.add_particles(h_pos, h_vel, h_mass)
+        for _ in range(ke):
+            ge.step(1, dt)
+            ge.last_mass()
+        ge.get_psi(o_psi)
+        if nstar:
+            ge.get_particles()
+        barrier()
+        sec = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([sec], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            sec = float(t.item())
+        h2d = psi.nbytes + pos.nbytes + vel.nbytes + mass.nbytes
+        d2h = ke * 8 + psi.nbytes + pos.nbytes + vel.nbytes
+        line["e2e"] = {"value": world * ncells * ke / sec, "unit": "cell-steps/s", "steps": ke,
+                       "h2d_bytes_per_step": h2d / ke, "d2h_bytes_per_step": d2h / ke,
+                       "what": "pinned-host upload of psi and stars, single-step spe_step calls each followed "
+                               "by a device->host read of the step's mass, final download of psi and stars"}
+        ge.destroy()
+        del ge
+
+    # ---------------- CPU oracle baseline and the stated psi error vs FP64 (rank 0, N = 1)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sec, o = cpu_baseline(psi, pos, vel, mass, dt)
+        line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"1 KDK step of the {args.workload} workload ({sec:.1f} s), "
+                                          "Phi(0) solve untimed"}
+        gc = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, stream=stream)
+        gc.set_ic(psi)
+        if nstar:
+            gc.add_particles(pos, vel, mass)
+        gc.step(1, dt)
+        ref = o.get_psi()
+        got = gc.get_psi()
+        line["psi_rel_l2_vs_fp64_1step"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        if nstar:
+            gp, _ = gc.get_particles()
+            op, _ = o.get_particles()
+            d = (gp - op + 0.5) % 1.0 - 0.5
+            line["pos_err_vs_fp64_1step_box"] = float(np.abs(d).max())
+        gc.destroy()
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -103,9 +103,9 @@ int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
     L->phi = off;      off = align256(off + ncells * sizeof(float));
     L->dep = off;      off = align256(off + (c->max_particles ? ncells * sizeof(long long) : 0));
     L->part = off;     off = align256(off + 7 * align256(c->max_particles * sizeof(float)));
-    L->tw = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float2));
+    L->tw = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float4));
     L->k2 = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float));
-    L->drift = off;    off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float2));
+    L->drift = off;    off = align256(off + ((size_t)c->nx * c->ny + c->nz) * sizeof(float4));
     L->partials = off; off = align256(off + (size_t)kMaxPartials * 5 * sizeof(double));
     L->counter = off;  off = align256(off + 256);
     L->diag = off;     off = align256(off + 64 * sizeof(double));
@@ -132,13 +132,14 @@ struct spe_grid {
     float *phi;
     long long *dep;
     float *px, *py, *pz, *vx, *vy, *vz, *pm;
-    float2 *tw[3];
+    float4 *tw[3];
     float *k2[3];
-    float2 *drift[3];
+    float4 *dxy;      // exp(-i eta (kx^2 + ky^2) dt / 2) / (nx ny nz), (hi, lo)
+    float4 *ez;       // exp(-i eta kz^2 dt / 2), (hi, lo)
     double *partials;
     unsigned int *counter;
     double *diag;
-    float2 *h_stage;  // pinned staging for the drift tables
+    float4 *h_stage;  // pinned staging for the drift tables
     size_t np;
     double mstar;
     double quantum;
@@ -241,9 +242,9 @@ SParams base_z(spe_grid *g, float2 *data, int W, int P)
     p.W = W;
     p.batches = g->n[1];
     p.tw = g->tw[2];
-    p.colf = g->drift[0];
-    p.batchf = g->drift[1];
-    p.linef = g->drift[2];
+    p.dxy = g->dxy;
+    p.ez = g->ez;
+    p.dxy_pitch = g->n[0];
     p.colk2 = g->k2[0];
     p.batchk2 = g->k2[1];
     p.linek2 = g->k2[2];
@@ -287,22 +288,45 @@ int run_s(spe_grid *g, int kind, int n, SParams p)
     return launch(g, kind, [&] { return launch_spass(n, p, g->st, nullptr); });
 }
 
-// exp(-i eta k^2 dt / 2) per axis, phase reduced modulo 2 pi in FP64.
+float4 split_c(double re, double im)
+{
+    const float hr = (float)re, hi = (float)im;
+    return make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+}
+
+// Drift factors for step size dt, built in FP64: D_xy = exp(-i eta (kx^2 +
+// ky^2) dt / 2) / (nx ny nz) per (kx, ky) and E_z = exp(-i eta kz^2 dt / 2),
+// phases reduced modulo 2 pi in FP64, each stored as a (hi, lo) float pair.
 int ensure_drift_tables(spe_grid *g, double dt)
 {
     if (g->tables_valid && g->table_dt == dt) return SPE_OK;
     cudaError_t e = cudaStreamSynchronize(g->st);  // the staging buffer may still be in flight
     if (e != cudaSuccess) return SPE_ECUDA;
-    size_t off = 0;
-    for (int a = 0; a < 3; ++a) {
-        for (int j = 0; j < g->n[a]; ++j) {
-            const double k = wavenumber(j, g->n[a], g->L[a]);
-            double ph = fmod(g->cfg.hbar_over_m * k * k * dt * 0.5, 2.0 * kPi);
-            g->h_stage[off + j] = make_float2((float)cos(ph), (float)-sin(ph));
-        }
-        off += g->n[a];
+    const double eta = g->cfg.hbar_over_m, twopi = 2.0 * kPi;
+    const double norm = 1.0 / (double)g->ncells;
+    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+    std::vector<double> px(nx), py(ny);
+    for (int i = 0; i < nx; ++i) {
+        const double k = wavenumber(i, nx, g->L[0]);
+        px[i] = fmod(eta * k * k * dt * 0.5, twopi);
     }
-    e = cudaMemcpyAsync(g->drift[0], g->h_stage, off * sizeof(float2), cudaMemcpyHostToDevice, g->st);
+    for (int j = 0; j < ny; ++j) {
+        const double k = wavenumber(j, ny, g->L[1]);
+        py[j] = fmod(eta * k * k * dt * 0.5, twopi);
+    }
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const double ph = px[i] + py[j];
+            g->h_stage[(size_t)j * nx + i] = split_c(norm * cos(ph), -norm * sin(ph));
+        }
+    float4 *ezh = g->h_stage + (size_t)nx * ny;
+    for (int k = 0; k < nz; ++k) {
+        const double kk = wavenumber(k, nz, g->L[2]);
+        const double ph = fmod(eta * kk * kk * dt * 0.5, twopi);
+        ezh[k] = split_c(cos(ph), -sin(ph));
+    }
+    e = cudaMemcpyAsync(g->dxy, g->h_stage, ((size_t)nx * ny + nz) * sizeof(float4), cudaMemcpyHostToDevice,
+                        g->st);
     if (e != cudaSuccess) return SPE_ECUDA;
     g->tables_valid = true;
     g->table_dt = dt;
@@ -504,7 +528,7 @@ int spe_create_grid(const spe_config *cfg, void *workspace, size_t workspace_byt
         }
         g->owns_ws = true;
     }
-    if (cudaMallocHost(&g->h_stage, (size_t)(cfg->nx + cfg->ny + cfg->nz) * sizeof(float2)) != cudaSuccess) {
+    if (cudaMallocHost(&g->h_stage, ((size_t)cfg->nx * cfg->ny + cfg->nz) * sizeof(float4)) != cudaSuccess) {
         cudaGetLastError();
         if (g->owns_ws) cudaFree(g->ws);
         delete g;
@@ -518,38 +542,37 @@ int spe_create_grid(const spe_config *cfg, void *workspace, size_t workspace_byt
     const size_t pstride = align256(cfg->max_particles * sizeof(float));
     float **parr[7] = {&g->px, &g->py, &g->pz, &g->vx, &g->vy, &g->vz, &g->pm};
     for (int i = 0; i < 7; ++i) *parr[i] = (float *)(b + L.part + i * pstride);
-    g->tw[0] = (float2 *)(b + L.tw);
+    g->tw[0] = (float4 *)(b + L.tw);
     g->tw[1] = g->tw[0] + cfg->nx;
     g->tw[2] = g->tw[1] + cfg->ny;
     g->k2[0] = (float *)(b + L.k2);
     g->k2[1] = g->k2[0] + cfg->nx;
     g->k2[2] = g->k2[1] + cfg->ny;
-    g->drift[0] = (float2 *)(b + L.drift);
-    g->drift[1] = g->drift[0] + cfg->nx;
-    g->drift[2] = g->drift[1] + cfg->ny;
+    g->dxy = (float4 *)(b + L.drift);
+    g->ez = g->dxy + (size_t)cfg->nx * cfg->ny;
     g->partials = (double *)(b + L.partials);
     g->counter = (unsigned int *)(b + L.counter);
     g->diag = (double *)(b + L.diag);
     update_quantum(g);
 
     cudaError_t e = cudaMemsetAsync(g->ws, 0, L.total, g->st);
-    // FP64-built tables: twiddles exp(-2 pi i e / N) and k^2 per axis
+    // FP64-built tables: twiddles exp(-2 pi i e / N) as (hi, lo) float pairs and k^2 per axis
     const int ntot = cfg->nx + cfg->ny + cfg->nz;
-    std::vector<float2> tw(ntot);
+    std::vector<float4> tw(ntot);
     std::vector<float> k2(ntot);
     int off = 0;
     for (int a = 0; a < 3; ++a) {
         const int n = g->n[a];
         for (int j = 0; j < n; ++j) {
             const double ang = -2.0 * kPi * (double)j / (double)n;
-            tw[off + j] = make_float2((float)cos(ang), (float)sin(ang));
+            tw[off + j] = split_c(cos(ang), sin(ang));
             const double k = wavenumber(j, n, g->L[a]);
             k2[off + j] = (float)(k * k);
         }
         off += n;
     }
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(g->tw[0], tw.data(), ntot * sizeof(float2), cudaMemcpyHostToDevice, g->st);
+        e = cudaMemcpyAsync(g->tw[0], tw.data(), ntot * sizeof(float4), cudaMemcpyHostToDevice, g->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->k2[0], k2.data(), ntot * sizeof(float), cudaMemcpyHostToDevice, g->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);

@@ -11,8 +11,10 @@
 // Flags select forward transform, a pointwise multiply in k space, and the
 // inverse transform, all on the same tile:
 //   drift   (S_FWD | S_DRIFT | S_INV on the z axis of psi):
-//       psi_hat *= exp(-i eta k^2 dt / 2) / (nx ny nz), the separable product
-//       of three per-axis factors built in FP64 on the host
+//       psi_hat *= exp(-i eta k^2 dt / 2) / (nx ny nz) = D_xy(kx, ky) E_z(kz),
+//       both factors built in FP64 on the host and applied as (hi + lo) float
+//       pairs with compensated products, so that the per-mode factor carries
+//       no fixed FP32 rounding that would repeat every step
 //       [Sec. 3.1 step (b), Algorithm 1 "kinetic drift in Fourier space"];
 //   Poisson (S_FWD | S_POISSON | S_INV on the z axis of the half spectrum):
 //       rho_hat *= -4 pi G / (k^2 nx ny nz), zero at k = 0
@@ -36,7 +38,7 @@ __global__ void __launch_bounds__(SCfg<N>::NT) spass_kernel(SParams p)
     constexpr int T = SCfg<N>::T, TP = SCfg<N>::TP, NT = SCfg<N>::NT, HT = T / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
-    __shared__ float2 colfac[T];
+    __shared__ float4 colfac[T];
     __shared__ float colk2[T];
     const int c0 = blockIdx.x * T;
     const int b = blockIdx.y;
@@ -46,10 +48,8 @@ __global__ void __launch_bounds__(SCfg<N>::NT) spass_kernel(SParams p)
 
     if (tid < T) {
         const int c = c0 + tid;
-        if (flags & S_DRIFT) {
-            colfac[tid] = (c < p.W) ? cscale(cmul(__ldg(&p.colf[c]), __ldg(&p.batchf[b])), p.norm)
-                                    : make_float2(0.f, 0.f);
-        }
+        if (flags & S_DRIFT)
+            colfac[tid] = (c < p.W) ? __ldg(&p.dxy[(size_t)b * p.dxy_pitch + c]) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (flags & S_POISSON) colk2[tid] = (c < p.W) ? __ldg(&p.colk2[c]) + __ldg(&p.batchk2[b]) : 0.f;
     }
 
@@ -67,7 +67,10 @@ __global__ void __launch_bounds__(SCfg<N>::NT) spass_kernel(SParams p)
             const int n = idx / T, t = idx % T;
             float2 v = tile[n * TP + t];
             if (flags & S_DRIFT) {
-                v = cmul(v, cmul(colfac[t], __ldg(&p.linef[n])));
+                const float4 d = colfac[t];
+                const float4 e = __ldg(&p.ez[n]);
+                v = cmul_comp(v, make_float2(d.x, d.y), make_float2(d.z, d.w));
+                v = cmul_comp(v, make_float2(e.x, e.y), make_float2(e.z, e.w));
             } else {
                 const float k2 = colk2[t] + __ldg(&p.linek2[n]);
                 const float f = (k2 > 0.f) ? p.poisson * p.norm / k2 : 0.f;

@@ -33,7 +33,7 @@ struct XParams {
     float2 *phik;             // rows of P complex (half spectrum)
     float *phi_out;           // rows of nx floats (X_WRITE_PHI)
     long long *dep;           // fixed-point star mass per node (X_DEP)
-    const float2 *tw;         // nx twiddles
+    const float4 *tw;         // nx twiddles, (hi, lo) float pairs
     const float *k2;          // nx values of kx^2 (X_KIN)
     int rows;                 // ny * nz
     int P;                    // half-spectrum row pitch (complex)
@@ -54,7 +54,7 @@ struct XParams {
 enum SFlags : int {
     S_FWD = 1 << 0,
     S_INV = 1 << 1,
-    S_DRIFT = 1 << 2,     // multiply by colf[c] * batchf[b] * linef[n] * norm (complex tables)
+    S_DRIFT = 1 << 2,     // multiply by dxy[b * dxy_pitch + c] * ez[n] ((hi, lo) complex tables)
     S_POISSON = 1 << 3,   // multiply by -4 pi G norm / (colk2[c] + batchk2[b] + linek2[n]), 0 at k = 0
     S_KIN = 1 << 4,       // reduce sum_k linek2[n] |X|^2 after the forward transform, no store
 };
@@ -65,10 +65,12 @@ struct SParams {
     long long bstride;    // batch stride
     int W;                // live columns
     int batches;
-    const float2 *tw;     // N twiddles
-    const float2 *colf, *batchf, *linef;   // drift factors
+    const float4 *tw;     // N twiddles, (hi, lo) float pairs
+    const float4 *dxy;    // drift factor per (column, batch), normalisation folded in, (hi, lo)
+    const float4 *ez;     // drift factor per line point, (hi, lo)
+    int dxy_pitch;
     const float *colk2, *batchk2, *linek2; // k^2 tables
-    float norm;           // 1 / (nx ny nz) folded into the multiply
+    float norm;           // 1 / (nx ny nz) folded into the Poisson multiply
     float poisson;        // -4 pi G
     double *partials;
     unsigned int *counter;

@@ -78,11 +78,15 @@ __global__ void __launch_bounds__(XCfg<N>::NT) xpass_kernel(XParams p)
             float2 v = make_float2(0.f, 0.f);
             if (row < p.rows) v = p.psi[(size_t)row * N + n];
             if (flags & X_KICK) {
+                // v * exp(-i ph) = v + v * (cos ph - 1 - i sin ph), with cos ph - 1 = -2 sin^2(ph/2):
+                // the factor's modulus error is O(ph^2 eps) instead of the O(eps) of a rounded cos ph,
+                // which would otherwise recur identically step after step while Phi changes slowly.
                 const float a2 = v.x * v.x + v.y * v.y;
                 const float phi = (flags & X_HAS_PHI) ? aux[t * N + n] : 0.f;
-                float s, c;
-                sincosf((phi + p.kappa * a2) * p.kick_scale, &s, &c);
-                v = make_float2(v.x * c + v.y * s, v.y * c - v.x * s);  // v * exp(-i phase)
+                float sh, ch;
+                sincosf(0.5f * ((phi + p.kappa * a2) * p.kick_scale), &sh, &ch);
+                const float cm1 = -2.f * sh * sh, sn = 2.f * sh * ch;
+                v = make_float2(fmaf(v.x, cm1, fmaf(v.y, sn, v.x)), fmaf(v.y, cm1, fmaf(-v.x, sn, v.y)));
             }
             if (fft) tile[n * TP + t] = v;
             else if (row < p.rows) p.psi[(size_t)row * N + n] = v;

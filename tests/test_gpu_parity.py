@@ -133,6 +133,16 @@ def test_packets32_full_run_parity(spe):
         assert abs(eg[k] - eo[k]) <= 1e-5 * abs(eo["kinetic"]), (k, eg[k], eo[k])
 
 
+def test_packets32_thousand_steps(spe):
+    """The same 32^3 packets for 1000 steps (the step count of the 256^3 workload): FP32 rounding
+    must not accumulate coherently from step to step."""
+    psi, _, _, _, dt, _ = inputs.make_workload("packets32")
+    g, o = run_pair(spe, psi.shape, psi, 250, dt, calls=4)
+    err = rel_l2(g.get_psi(), o.get_psi())
+    print(f"packets32 x1000 rel-L2 {err:.3e}")
+    assert err <= PSI_TOL, err
+
+
 SIZES = [4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024]
 
 
