@@ -767,11 +767,11 @@ int spe_energy(spe_grid *g, spe_energy_t *out)
     xp.result = g->diag + 16;
     if ((rc = run_x(g, KIND_DIAG, xp))) return rc;
     SParams y = base_y(g, g->psi, g->n[0], g->n[0]);
-    y.flags = S_KIN;
+    y.flags = S_FWD | S_KIN;
     y.result = g->diag + 17;
     if ((rc = run_s(g, KIND_DIAG, g->n[1], y))) return rc;
     SParams z = base_z(g, g->psi, g->n[0], g->n[0]);
-    z.flags = S_KIN;
+    z.flags = S_FWD | S_KIN;
     z.result = g->diag + 18;
     if ((rc = run_s(g, KIND_DIAG, g->n[2], z))) return rc;
     double skin = 0.0;
