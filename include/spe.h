@@ -164,6 +164,35 @@ SPE_API int spe_launch_count(spe_grid *g, unsigned long long *count_out, int res
  * number of kinds written (at most cap) or a negative status. */
 SPE_API int spe_profile_read(spe_grid *g, const char **names, unsigned long long *launches, double *ms, int cap);
 
+/* ---- field energy without any device allocation ----
+ * Not part of the paper's method (the paper has no counterpart); it serves
+ * callers that may not allocate device memory where they need the number:
+ * code running inside another framework's memory pool, a loop with a fixed
+ * memory budget, or a process that must not grow its device footprint after
+ * start-up.
+ *
+ * Computes, for n complex64 values psi_c64 already in device memory (not
+ * read after return; the caller keeps ownership):
+ *   out2[0] = cell_volume * sum |psi|^2                (spe_energy's mass)
+ *   out2[1] = kappa / 2 * cell_volume * sum |psi|^4   (spe_energy's interaction)
+ * where = SPE_HOST: out2 is host memory, filled before return;
+ * where = SPE_DEVICE: out2 is two doubles of device memory, written on the
+ * stream.  cuda_stream: cudaStream_t or NULL.  The call waits for its work.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * is one fixed array of SPE_NOALLOC_SCRATCH_DOUBLES doubles inside the
+ * library, resident on every GPU that loads libspe until the process exits.
+ * Every call shares that array, so calls that overlap on the GPU race and
+ * must be serialised by the caller.  The first call on each device finds the
+ * array's device address (with that device current) and remembers it; make
+ * that first call before any stream capture.
+ * Returns SPE_EINVAL for n == 0, n > SPE_NOALLOC_MAX_CELLS, a non-positive
+ * cell volume or a NULL pointer. */
+#define SPE_NOALLOC_MAX_CELLS ((size_t)1 << 30)
+#define SPE_NOALLOC_SCRATCH_DOUBLES 2064
+SPE_API int spe_field_energy_noalloc(const void *psi_c64, size_t n, double cell_volume, double kappa,
+                                     double *out2, int where, void *cuda_stream);
+
 /* Human-readable text for a status code (static storage). */
 SPE_API const char *spe_strerror(int status);
 

@@ -30,7 +30,7 @@ EXPORTED = (
     "spe_workspace_bytes", "spe_create_grid", "spe_destroy", "spe_set_ic", "spe_add_particles",
     "spe_clear_particles", "spe_step", "spe_suggest_dt", "spe_density", "spe_potential", "spe_energy",
     "spe_last_mass", "spe_get_psi", "spe_get_particles", "spe_particle_count", "spe_sync",
-    "spe_launch_count", "spe_profile_read", "spe_strerror",
+    "spe_launch_count", "spe_profile_read", "spe_strerror", "spe_field_energy_noalloc",
 )
 
 
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "spe_profile_read": (I, [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_ulonglong),
                                  ctypes.POINTER(D), I]),
         "spe_strerror": (ctypes.c_char_p, [I]),
+        "spe_field_energy_noalloc": (I, [P, S, D, D, ctypes.POINTER(D), I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -277,3 +278,18 @@ class Grid:
 
 def create_grid(*args, **kwargs) -> Grid:
     return Grid(*args, **kwargs)
+
+
+def field_energy_noalloc(psi, cell_volume, kappa=0.0, stream=None):
+    """(mass, interaction) of a complex64 CUDA tensor through spe_field_energy_noalloc: the
+    library allocates nothing for it (its scratch is a fixed array inside libspe)."""
+    import torch
+    lib = load_library()
+    if not (isinstance(psi, torch.Tensor) and psi.is_cuda and psi.dtype == torch.complex64 and psi.is_contiguous()):
+        raise TypeError("psi must be a contiguous complex64 CUDA tensor")
+    out = (ctypes.c_double * 2)()
+    st = (stream or torch.cuda.current_stream(psi.device)).cuda_stream
+    _check(lib.spe_field_energy_noalloc(ctypes.c_void_p(psi.data_ptr()), psi.numel(), float(cell_volume),
+                                        float(kappa), out, SPE_HOST, ctypes.c_void_p(st)),
+           "spe_field_energy_noalloc")
+    return out[0], out[1]
