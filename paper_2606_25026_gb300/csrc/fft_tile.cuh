@@ -54,6 +54,13 @@ constexpr float kRsqrt2Hi = (float)kRsqrt2;
 constexpr float kRsqrt2Lo = (float)(kRsqrt2 - (double)kRsqrt2Hi);
 constexpr float kSqrt3h2Hi = (float)kSqrt3h2;
 constexpr float kSqrt3h2Lo = (float)(kSqrt3h2 - (double)kSqrt3h2Hi);
+// cos(pi/8), sin(pi/8) for the radix-16 butterfly
+constexpr double kCos8 = 0.92387953251128675612818318939678829;
+constexpr double kSin8 = 0.38268343236508977172845998403039887;
+constexpr float kCos8Hi = (float)kCos8;
+constexpr float kCos8Lo = (float)(kCos8 - (double)kCos8Hi);
+constexpr float kSin8Hi = (float)kSin8;
+constexpr float kSin8Lo = (float)(kSin8 - (double)kSin8Hi);
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 // multiply by -i (DIR < 0) or +i (DIR > 0): the R = 4 rotation in direction DIR
 template <int DIR>
@@ -61,6 +68,19 @@ __device__ __forceinline__ float2 rot90(float2 a)
 {
     return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
 }
+
+// ---- asynchronous global -> shared copies (all of a tile's loads in flight at once)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---- small DFTs in registers: v[q] <- sum_r v[r] exp(DIR 2 pi i r q / R) ----
 
@@ -129,6 +149,56 @@ template <int DIR> struct Dft<8, DIR> {
     }
 };
 
+template <int DIR> struct Dft<16, DIR> {
+    // 16 = 4 x 4: with n = 4a + b and k = c + 4d,
+    // X[c + 4d] = sum_b W4^{bd} W16^{bc} sum_a x[4a + b] W4^{ac}.
+    __device__ __forceinline__ static void rot(float2 &v, int e)
+    {
+        // v *= W16^e, W16 = exp(DIR 2 pi i / 16), e in {1, 2, 3, 4, 6, 9}
+        const float2 c8h = make_float2(kCos8Hi, DIR * kSin8Hi), c8l = make_float2(kCos8Lo, DIR * kSin8Lo);
+        const float2 s8h = make_float2(kSin8Hi, DIR * kCos8Hi), s8l = make_float2(kSin8Lo, DIR * kCos8Lo);
+        switch (e) {
+        case 1: v = cmul_comp(v, c8h, c8l); break;                                     // exp(DIR i pi/8)
+        case 2: {                                                                      // exp(DIR i pi/4)
+            const float a = DIR < 0 ? v.x + v.y : v.x - v.y, b = DIR < 0 ? v.y - v.x : v.y + v.x;
+            v = make_float2(mul_comp(a, kRsqrt2Hi, kRsqrt2Lo), mul_comp(b, kRsqrt2Hi, kRsqrt2Lo));
+            break;
+        }
+        case 3: v = cmul_comp(v, s8h, s8l); break;                                     // exp(DIR i 3pi/8)
+        case 4: v = rot90<DIR>(v); break;                                              // exp(DIR i pi/2)
+        case 6: {                                                                      // exp(DIR i 3pi/4)
+            const float a = DIR < 0 ? v.y - v.x : -v.x - v.y, b = DIR < 0 ? -v.x - v.y : v.x - v.y;
+            v = make_float2(mul_comp(a, kRsqrt2Hi, kRsqrt2Lo), mul_comp(b, kRsqrt2Hi, kRsqrt2Lo));
+            break;
+        }
+        case 9: v = cmul_comp(v, make_float2(-c8h.x, -c8h.y), make_float2(-c8l.x, -c8l.y)); break;  // -W16^1
+        default: break;
+        }
+    }
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        float2 u[4][4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float2 t[4] = {v[b], v[4 + b], v[8 + b], v[12 + b]};
+            Dft<4, DIR>::run(t);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) u[b][c] = t[c];
+        }
+#pragma unroll
+        for (int b = 1; b < 4; ++b)
+#pragma unroll
+            for (int c = 1; c < 4; ++c) rot(u[b][c], b * c);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float2 t[4] = {u[0][c], u[1][c], u[2][c], u[3][c]};
+            Dft<4, DIR>::run(t);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) v[c + 4 * d] = t[d];
+        }
+    }
+};
+
 // ---- radix plans per transform length ----
 
 template <int... R> struct RList {};
@@ -138,7 +208,7 @@ template <> struct Plan<4> { using type = RList<4>; };
 template <> struct Plan<6> { using type = RList<3, 2>; };
 template <> struct Plan<8> { using type = RList<8>; };
 template <> struct Plan<12> { using type = RList<3, 4>; };
-template <> struct Plan<16> { using type = RList<4, 4>; };
+template <> struct Plan<16> { using type = RList<16>; };
 template <> struct Plan<24> { using type = RList<3, 8>; };
 template <> struct Plan<32> { using type = RList<8, 4>; };
 template <> struct Plan<48> { using type = RList<3, 4, 4>; };
@@ -146,11 +216,11 @@ template <> struct Plan<64> { using type = RList<8, 8>; };
 template <> struct Plan<96> { using type = RList<3, 4, 8>; };
 template <> struct Plan<128> { using type = RList<8, 4, 4>; };
 template <> struct Plan<192> { using type = RList<3, 8, 8>; };
-template <> struct Plan<256> { using type = RList<4, 8, 8>; };
+template <> struct Plan<256> { using type = RList<16, 16>; };
 template <> struct Plan<384> { using type = RList<3, 4, 4, 8>; };
 template <> struct Plan<512> { using type = RList<8, 8, 8>; };
 template <> struct Plan<768> { using type = RList<3, 4, 8, 8>; };
-template <> struct Plan<1024> { using type = RList<4, 4, 8, 8>; };
+template <> struct Plan<1024> { using type = RList<4, 16, 16>; };
 
 // One Stockham stage over all T lines of the tile, in place through registers.
 template <int N, int T, int TP, int NT, int DIR, int Ns, int R>
@@ -210,6 +280,76 @@ template <int N, int T, int TP, int NT, int DIR>
 __device__ __forceinline__ void tile_fft(float2 *s, const float4 *tw)
 {
     fft_stages<N, T, TP, NT, DIR, 1>(s, tw, typename Plan<N>::type{});
+}
+
+// ---- plan utilities: the last radix, the plan without it, a reversed plan
+template <int R, class L> struct Prepend;
+template <int R, int... Rs> struct Prepend<R, RList<Rs...>> { using type = RList<R, Rs...>; };
+template <class L> struct SplitLast;
+template <int R> struct SplitLast<RList<R>> {
+    static constexpr int last = R;
+    using init = RList<>;
+};
+template <int R0, int R1, int... Rs> struct SplitLast<RList<R0, R1, Rs...>> {
+    static constexpr int last = SplitLast<RList<R1, Rs...>>::last;
+    using init = typename Prepend<R0, typename SplitLast<RList<R1, Rs...>>::init>::type;
+};
+template <class L, class Acc = RList<>> struct Reverse;
+template <class Acc> struct Reverse<RList<>, Acc> { using type = Acc; };
+template <int R, int... Rs, int... As> struct Reverse<RList<R, Rs...>, RList<As...>> {
+    using type = typename Reverse<RList<Rs...>, RList<R, As...>>::type;
+};
+
+// Forward transform, a pointwise op in k space, inverse transform, with the
+// last forward stage, the op and the first inverse stage done in registers.
+// With the plan R_1..R_m the last forward stage (Ns = N / R_m) reads and
+// writes the same index group {j + q N/R_m} of butterfly j, and so does a
+// first inverse stage of radix R_m (Ns = 1, no twiddles); the inverse then
+// continues with R_{m-1}..R_1.  op(v, n, t) gets the value of frequency n of
+// line t and returns it multiplied.
+template <int N, int T, int TP, int NT, class Op>
+__device__ __forceinline__ void tile_fft_fwd_op_inv(float2 *s, const float4 *tw, const Op &op)
+{
+    using Full = typename Plan<N>::type;
+    constexpr int R = SplitLast<Full>::last;
+    using Init = typename SplitLast<Full>::init;
+    constexpr int B = N / R;
+    fft_stages<N, T, TP, NT, -1, 1>(s, tw, Init{});
+    constexpr int TOTAL = B * T;
+    constexpr int PER = (TOTAL + NT - 1) / NT;
+    float2 v[PER][R];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (TOTAL % NT == 0 || idx < TOTAL) {
+            const int t = idx % T, j = idx / T;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[p][r] = s[(j + r * B) * TP + t];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (TOTAL % NT == 0 || idx < TOTAL) {
+            const int t = idx % T, j = idx / T;
+            if (B > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float4 w = __ldg(&tw[j * r]);
+                    v[p][r] = cmul_comp(v[p][r], make_float2(w.x, w.y), make_float2(w.z, w.w));
+                }
+            }
+            Dft<R, -1>::run(v[p]);
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[p][q] = op(v[p][q], j + q * B, t);
+            Dft<R, +1>::run(v[p]);
+#pragma unroll
+            for (int q = 0; q < R; ++q) s[(j * R + q) * TP + t] = v[p][q];
+        }
+    }
+    __syncthreads();
+    fft_stages<N, T, TP, NT, +1, R>(s, tw, typename Reverse<Init>::type{});
 }
 
 }  // namespace spe

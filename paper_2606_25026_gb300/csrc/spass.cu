@@ -2,14 +2,16 @@
 // line are S complex values apart and neighbouring lines (columns) are
 // adjacent in memory.
 //
-// One CTA owns a tile of T adjacent columns x N points (T = 32 for N <= 256,
-// 16 above), so every row of the tile is one coalesced 128/256-byte segment,
-// loaded and stored as float4 (two columns per thread).  The tile lives in
+// One CTA owns a tile of T adjacent columns x N points (T = 32 for N < 256,
+// 16 from 256 up), so every row of the tile is one coalesced 128/256-byte
+// segment.  Loads are asynchronous 16-byte copies straight into shared memory
+// (every load of the tile in flight at once); stores are float4.  The tile lives in
 // shared memory element-major (tile[n * T + t]) with lanes over t: the FFT
 // stages are then bank-conflict free without padding.
 //
 // Flags select forward transform, a pointwise multiply in k space, and the
-// inverse transform, all on the same tile:
+// inverse transform, all on the same tile; with a multiply, the last forward
+// stage, the multiply and the first inverse stage run in registers:
 //   drift   (S_FWD | S_DRIFT | S_INV on the z axis of psi):
 //       psi_hat *= exp(-i eta k^2 dt / 2) / (nx ny nz) = D_xy(kx, ky) E_z(kz),
 //       both factors built in FP64 on the host and applied as (hi + lo) float
@@ -25,11 +27,40 @@
 
 namespace spe {
 
+template <class L> struct MaxRadix;
+template <int R> struct MaxRadix<RList<R>> { static constexpr int value = R; };
+template <int R0, int R1, int... Rs> struct MaxRadix<RList<R0, R1, Rs...>> {
+    static constexpr int rest = MaxRadix<RList<R1, Rs...>>::value;
+    static constexpr int value = R0 > rest ? R0 : rest;
+};
+
 template <int N> struct SCfg {
-    static constexpr int T = (N >= 384) ? 16 : 32;
+    static constexpr int T = (N >= 256) ? 16 : 32;
     static constexpr int TP = T;
-    static constexpr int NT = (N * T / 8 >= 256) ? 256 : ((N * T / 8 >= 128) ? 128 : 64);
+    static constexpr int W = N * T / MaxRadix<typename Plan<N>::type>::value;  // butterflies per stage
+    static constexpr int NT = W >= 512 ? 512 : (W >= 256 ? 256 : (W >= 128 ? 128 : 64));
     static constexpr size_t smem = sizeof(float2) * N * TP;
+};
+
+struct DriftOp {
+    const float4 *colfac, *ez;
+    __device__ __forceinline__ float2 operator()(float2 v, int n, int t) const
+    {
+        const float4 d = colfac[t];
+        const float4 e = __ldg(&ez[n]);
+        v = cmul_comp(v, make_float2(d.x, d.y), make_float2(d.z, d.w));
+        return cmul_comp(v, make_float2(e.x, e.y), make_float2(e.z, e.w));
+    }
+};
+
+struct PoissonOp {
+    const float *colk2, *linek2;
+    float scale;  // -4 pi G / (nx ny nz)
+    __device__ __forceinline__ float2 operator()(float2 v, int n, int t) const
+    {
+        const float k2 = colk2[t] + __ldg(&linek2[n]);
+        return cscale(v, (k2 > 0.f) ? scale / k2 : 0.f);
+    }
 };
 
 template <int N>
@@ -55,32 +86,18 @@ __global__ void __launch_bounds__(SCfg<N>::NT) spass_kernel(SParams p)
 
     for (int idx = tid; idx < N * HT; idx += NT) {
         const int n = idx / HT, q = idx % HT;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c0 + 2 * q < p.W) v = *reinterpret_cast<const float4 *>(base + (size_t)n * p.S + 2 * q);
-        *reinterpret_cast<float4 *>(&tile[n * TP + 2 * q]) = v;
+        if (c0 + 2 * q < p.W) cp_async16(&tile[n * TP + 2 * q], base + (size_t)n * p.S + 2 * q);
+        else *reinterpret_cast<float4 *>(&tile[n * TP + 2 * q]) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    cp_async_wait_all();
     __syncthreads();
-    if (flags & S_FWD) tile_fft<N, T, TP, NT, -1>(tile, p.tw);
-
-    if (flags & (S_DRIFT | S_POISSON)) {
-        for (int idx = tid; idx < N * T; idx += NT) {
-            const int n = idx / T, t = idx % T;
-            float2 v = tile[n * TP + t];
-            if (flags & S_DRIFT) {
-                const float4 d = colfac[t];
-                const float4 e = __ldg(&p.ez[n]);
-                v = cmul_comp(v, make_float2(d.x, d.y), make_float2(d.z, d.w));
-                v = cmul_comp(v, make_float2(e.x, e.y), make_float2(e.z, e.w));
-            } else {
-                const float k2 = colk2[t] + __ldg(&p.linek2[n]);
-                const float f = (k2 > 0.f) ? p.poisson * p.norm / k2 : 0.f;
-                v = cscale(v, f);
-            }
-            tile[n * TP + t] = v;
-        }
-        __syncthreads();
+    if ((flags & (S_FWD | S_INV)) == (S_FWD | S_INV) && (flags & (S_DRIFT | S_POISSON))) {
+        if (flags & S_DRIFT) tile_fft_fwd_op_inv<N, T, TP, NT>(tile, p.tw, DriftOp{colfac, p.ez});
+        else tile_fft_fwd_op_inv<N, T, TP, NT>(tile, p.tw, PoissonOp{colk2, p.linek2, p.poisson * p.norm});
+    } else {
+        if (flags & S_FWD) tile_fft<N, T, TP, NT, -1>(tile, p.tw);
+        if (flags & S_INV) tile_fft<N, T, TP, NT, +1>(tile, p.tw);
     }
-    if (flags & S_INV) tile_fft<N, T, TP, NT, +1>(tile, p.tw);
 
     if (flags & S_KIN) {
         double acc = 0.0;

@@ -75,8 +75,15 @@ __global__ void __launch_bounds__(XCfg<N>::NT) xpass_kernel(XParams p)
         for (int idx = tid; idx < T * N; idx += NT) {
             const int n = idx % N, t = idx / N;
             const int row = row0 + t;
-            float2 v = make_float2(0.f, 0.f);
-            if (row < p.rows) v = p.psi[(size_t)row * N + n];
+            if (row < p.rows) cp_async8(&tile[n * TP + t], &p.psi[(size_t)row * N + n]);
+            else tile[n * TP + t] = make_float2(0.f, 0.f);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (int idx = tid; idx < T * N; idx += NT) {
+            const int n = idx % N, t = idx / N;
+            const int row = row0 + t;
+            float2 v = tile[n * TP + t];
             if (flags & X_KICK) {
                 // v * exp(-i ph) = v + v * (cos ph - 1 - i sin ph), with cos ph - 1 = -2 sin^2(ph/2):
                 // the factor's modulus error is O(ph^2 eps) instead of the O(eps) of a rounded cos ph,
@@ -105,33 +112,42 @@ __global__ void __launch_bounds__(XCfg<N>::NT) xpass_kernel(XParams p)
     // ---- inverse x transform, density, mass, real-to-complex x transform of rho
     if (flags & (X_R2C | X_MASS | X_IFFT)) {
         const bool ifft = flags & X_IFFT;
-        if (ifft) {
-            for (int idx = tid; idx < T * N; idx += NT) {
-                const int n = idx % N, t = idx / N;
-                const int row = row0 + t;
-                tile[n * TP + t] = (row < p.rows) ? p.psi[(size_t)row * N + n] : make_float2(0.f, 0.f);
-            }
-            __syncthreads();
-            tile_fft<N, T, TP, NT, +1>(tile, p.tw);
+        // psi (transformed or not) streams into the tile asynchronously while the star
+        // deposit of the same rows is read, converted and cleared into aux
+        for (int idx = tid; idx < T * N; idx += NT) {
+            const int n = idx % N, t = idx / N;
+            const int row = row0 + t;
+            if (row < p.rows) cp_async8(&tile[n * TP + t], &p.psi[(size_t)row * N + n]);
+            else tile[n * TP + t] = make_float2(0.f, 0.f);
         }
+        if (flags & X_DEP) {
+            // loads only: a zero store to an address whose load is still in flight has to wait
+            // for that load, which serialises the loop on memory latency (measured 4x slower)
+            const long long *__restrict__ dep = p.dep + (size_t)row0 * N;
+#pragma unroll 4
+            for (int idx = tid; idx < T * N; idx += NT) {
+                const int row = row0 + idx / N;
+                aux[idx] = (row < p.rows) ? (float)__ldcs(&dep[idx]) * p.dep_scale : 0.f;
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (flags & X_DEP) {
+            // every deposit value of the tile has been consumed by now: clear for the next step
+            long long *__restrict__ dep = p.dep + (size_t)row0 * N;
+            for (int idx = tid; idx < T * N; idx += NT)
+                if (row0 + idx / N < p.rows) __stcs(&dep[idx], 0ll);
+        }
+        if (ifft) tile_fft<N, T, TP, NT, +1>(tile, p.tw);
         float msum = 0.f;
         for (int idx = tid; idx < T * N; idx += NT) {
             const int n = idx % N, t = idx / N;
             const int row = row0 + t;
-            float2 v;
-            if (ifft) {
-                v = tile[n * TP + t];
-                if (row < p.rows) p.psi[(size_t)row * N + n] = v;
-            } else {
-                v = (row < p.rows) ? p.psi[(size_t)row * N + n] : make_float2(0.f, 0.f);
-            }
+            const float2 v = tile[n * TP + t];
+            if (ifft && row < p.rows) p.psi[(size_t)row * N + n] = v;
             float r = v.x * v.x + v.y * v.y;
             msum += r;
-            if ((flags & X_DEP) && row < p.rows) {
-                long long *d = p.dep + (size_t)row * N + n;
-                r += (float)(*d) * p.dep_scale;
-                *d = 0;
-            }
+            if (flags & X_DEP) r += aux[t * N + n];
             aux[t * N + n] = r;
         }
         __syncthreads();
@@ -168,8 +184,10 @@ __global__ void __launch_bounds__(XCfg<N>::NT) xpass_kernel(XParams p)
         for (int idx = tid; idx < T * N; idx += NT) {
             const int n = idx % N, t = idx / N;
             const int row = row0 + t;
-            tile[n * TP + t] = (row < p.rows) ? p.psi[(size_t)row * N + n] : make_float2(0.f, 0.f);
+            if (row < p.rows) cp_async8(&tile[n * TP + t], &p.psi[(size_t)row * N + n]);
+            else tile[n * TP + t] = make_float2(0.f, 0.f);
         }
+        cp_async_wait_all();
         __syncthreads();
         tile_fft<N, T, TP, NT, -1>(tile, p.tw);
         double acc = 0.0;
