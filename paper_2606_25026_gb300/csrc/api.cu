@@ -68,12 +68,13 @@ enum Kind {
     KIND_X_POTENTIAL,
     KIND_DIAG,
     KIND_COPY,
+    KIND_SORT,
     KIND_COUNT
 };
 
 const char *kKindNames[KIND_COUNT] = {
     "x_kick_fwd", "x_inv_density_r2c", "y_fft_psi", "z_fft_drift", "y_fft_rho", "z_fft_poisson",
-    "particles_kdk_deposit", "x_kick_final", "x_potential", "diagnostics", "layout_copy",
+    "particles_kdk_deposit", "x_kick_final", "x_potential", "diagnostics", "layout_copy", "particles_sort",
 };
 
 struct ProfRec {
@@ -84,7 +85,7 @@ struct ProfRec {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t psi, phik, phi, dep, part, tw, k2, drift, partials, counter, diag, total;
+    size_t psi, phik, phi, dep, part, bins, tw, k2, drift, partials, counter, diag, total;
 };
 
 int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
@@ -102,7 +103,9 @@ int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
     L->phik = off;     off = align256(off + (size_t)c->ny * c->nz * p * sizeof(float2));
     L->phi = off;      off = align256(off + ncells * sizeof(float));
     L->dep = off;      off = align256(off + (c->max_particles ? ncells * sizeof(long long) : 0));
-    L->part = off;     off = align256(off + 7 * align256(c->max_particles * sizeof(float)));
+    // two sets of star arrays (x, y, z, vx, vy, vz, m, id) for reordering, sort keys, block counters
+    L->part = off;     off = align256(off + 17 * align256(c->max_particles * sizeof(float)));
+    L->bins = off;     off = align256(off + sizeof(int) * (size_t)((c->nx + 3) / 4) * ((c->ny + 3) / 4) * ((c->nz + 3) / 4));
     L->tw = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float4));
     L->k2 = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float));
     L->drift = off;    off = align256(off + ((size_t)c->nx * c->ny + c->nz) * sizeof(float4));
@@ -132,6 +135,12 @@ struct spe_grid {
     float *phi;
     long long *dep;
     float *px, *py, *pz, *vx, *vy, *vz, *pm;
+    unsigned int *pid;            // insertion index of the star in each memory slot
+    float *alt[7];                // second set of star arrays (reordering target)
+    unsigned int *alt_id;
+    int *skey, *bins;
+    int nbins, nbx, nby;
+    unsigned long long steps_done;
     float4 *tw[3];
     float *k2[3];
     float4 *dxy;      // exp(-i eta (kx^2 + ky^2) dt / 2) / (nx ny nz), (hi, lo)
@@ -366,6 +375,48 @@ int compute_phi(spe_grid *g)
     return SPE_OK;
 }
 
+// Reorder the star arrays by 4x4x4 cell block every kSortEvery steps so a
+// warp's Phi gathers and deposit atomics hit few L2 lines (stars cross a cell
+// in hundreds of CFL-limited steps, so the order stays useful that long).
+constexpr unsigned long long kSortEvery = 64;
+
+int sort_particles(spe_grid *g)
+{
+    SortParams sp;
+    memset(&sp, 0, sizeof(sp));
+    float *cur[7] = {g->px, g->py, g->pz, g->vx, g->vy, g->vz, g->pm};
+    for (int a = 0; a < 7; ++a) {
+        sp.src[a] = cur[a];
+        sp.dst[a] = g->alt[a];
+    }
+    sp.src_id = g->pid;
+    sp.dst_id = g->alt_id;
+    sp.key = g->skey;
+    sp.count = g->bins;
+    sp.n = (int)g->np;
+    sp.nbins = g->nbins;
+    sp.nx = g->n[0]; sp.ny = g->n[1]; sp.nz = g->n[2];
+    sp.nbx = g->nbx; sp.nby = g->nby;
+    sp.Lx = (float)g->L[0]; sp.Ly = (float)g->L[1]; sp.Lz = (float)g->L[2];
+    sp.inv_dx = (float)(1.0 / g->dx[0]);
+    sp.inv_dy = (float)(1.0 / g->dx[1]);
+    sp.inv_dz = (float)(1.0 / g->dx[2]);
+    int extra = 0;
+    int rc = launch(g, KIND_SORT, [&] { return launch_particle_sort(sp, g->st, &extra); });
+    g->launches += extra > 0 ? extra - 1 : 0;
+    if (rc) return rc;
+    float **mine[7] = {&g->px, &g->py, &g->pz, &g->vx, &g->vy, &g->vz, &g->pm};
+    for (int a = 0; a < 7; ++a) {
+        float *t = *mine[a];
+        *mine[a] = g->alt[a];
+        g->alt[a] = t;
+    }
+    unsigned int *t = g->pid;
+    g->pid = g->alt_id;
+    g->alt_id = t;
+    return SPE_OK;
+}
+
 // One KDK step whose leading kick has size dtk (dt/2 for the first step of
 // a call, dt afterwards).
 int step_body(spe_grid *g, double dtk, double dt)
@@ -378,6 +429,7 @@ int step_body(spe_grid *g, double dtk, double dt)
     xp.kick_scale = (float)(dtk / g->cfg.hbar_over_m);
     if ((rc = run_x(g, KIND_X_KICK_FFT, xp))) return rc;
     if (parts) {
+        if (g->steps_done % kSortEvery == 0 && (rc = sort_particles(g))) return rc;
         PParams pp = base_p(g);
         pp.flags = PK_DRIFT | (grav ? (PK_KICK | PK_DEPOSIT) : 0);
         pp.kick = (float)dtk;
@@ -542,6 +594,14 @@ int spe_create_grid(const spe_config *cfg, void *workspace, size_t workspace_byt
     const size_t pstride = align256(cfg->max_particles * sizeof(float));
     float **parr[7] = {&g->px, &g->py, &g->pz, &g->vx, &g->vy, &g->vz, &g->pm};
     for (int i = 0; i < 7; ++i) *parr[i] = (float *)(b + L.part + i * pstride);
+    g->pid = (unsigned int *)(b + L.part + 7 * pstride);
+    for (int i = 0; i < 7; ++i) g->alt[i] = (float *)(b + L.part + (8 + i) * pstride);
+    g->alt_id = (unsigned int *)(b + L.part + 15 * pstride);
+    g->skey = (int *)(b + L.part + 16 * pstride);
+    g->bins = (int *)(b + L.bins);
+    g->nbx = (cfg->nx + 3) / 4;
+    g->nby = (cfg->ny + 3) / 4;
+    g->nbins = g->nbx * g->nby * ((cfg->nz + 3) / 4);
     g->tw[0] = (float4 *)(b + L.tw);
     g->tw[1] = g->tw[0] + cfg->nx;
     g->tw[2] = g->tw[1] + cfg->ny;
@@ -644,6 +704,10 @@ int spe_add_particles(spe_grid *g, size_t n, const float *pos3, const float *vel
                                         (float)g->L[2], g->st);
         g->launches++;
     }
+    if (e == cudaSuccess) {
+        e = launch_particle_ids(g->pid, (int)o, (int)n, g->st);
+        g->launches++;
+    }
     if (e != cudaSuccess) return SPE_ECUDA;
     g->np += n;
     g->mstar += msum;
@@ -677,7 +741,10 @@ int spe_step(spe_grid *g, int nsteps, double dt)
     if ((rc = ensure_drift_tables(g, dt))) return rc;
     if (!g->phi_valid && (rc = compute_phi(g))) return rc;
     for (int s = 0; s < nsteps; ++s)
+    {
         if ((rc = step_body(g, s == 0 ? 0.5 * dt : dt, dt))) return rc;
+        g->steps_done++;
+    }
     if ((rc = final_half_kick(g, 0.5 * dt))) return rc;
     if (g->cfg.flags & SPE_ASYNC) return SPE_OK;
     double mass = 0.0;
@@ -809,23 +876,30 @@ int spe_get_particles(spe_grid *g, float *pos3, float *vel3, int where)
     if (!n) return SPE_OK;
     if (where == SPE_DEVICE) {
         int rc = launch(g, KIND_COPY, [&] {
-            return launch_particles_from_soa(g->px, g->py, g->pz, g->vx, g->vy, g->vz, (int)n, pos3, vel3, g->st);
+            return launch_particles_from_soa_by_id(g->px, g->py, g->pz, g->vx, g->vy, g->vz, g->pid, (int)n, pos3,
+                                                   vel3, g->st);
         });
         if (rc) return rc;
         return cuerr(cudaStreamSynchronize(g->st));
     }
     std::vector<float> soa(6 * n);
+    std::vector<unsigned int> id(n);
     const float *src[6] = {g->px, g->py, g->pz, g->vx, g->vy, g->vz};
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 6 && e == cudaSuccess; ++k)
         e = cudaMemcpyAsync(soa.data() + k * n, src[k], n * sizeof(float), cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(id.data(), g->pid, n * sizeof(unsigned int), cudaMemcpyDeviceToHost, g->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     if (e != cudaSuccess) return SPE_ECUDA;
-    for (size_t i = 0; i < n; ++i)
+    for (size_t i = 0; i < n; ++i) {
+        const size_t o = id[i];
+        if (o >= n) return SPE_ESTATE;
         for (int a = 0; a < 3; ++a) {
-            if (pos3) pos3[3 * i + a] = soa[a * n + i];
-            if (vel3) vel3[3 * i + a] = soa[(3 + a) * n + i];
+            if (pos3) pos3[3 * o + a] = soa[a * n + i];
+            if (vel3) vel3[3 * o + a] = soa[(3 + a) * n + i];
         }
+    }
     return SPE_OK;
 }
 

@@ -178,3 +178,145 @@ cudaError_t launch_particles_from_soa(const float *x, const float *y, const floa
 }
 
 }  // namespace spe
+
+// ---------------------------------------------------------------- reordering by cell block
+// Stars are kept in memory grouped by coarse cell blocks (4 x 4 x 4 grid
+// cells) so that a warp's Phi gathers and deposit atomics land on few L2
+// lines.  Counting sort: histogram of block keys, exclusive scan, scatter.
+// The order inside a block depends on atomic arrival and is not
+// reproducible, but every per-star update is independent of memory order
+// and the deposit is an integer sum, so the physics stays bitwise
+// reproducible; the id array maps memory slots back to insertion order.
+
+namespace spe {
+
+__device__ __forceinline__ int block_key(float x, float y, float z, const SortParams &s)
+{
+    const Cic cx = cic_axis(x, 0.5f * s.Lx, s.inv_dx, s.nx);
+    const Cic cy = cic_axis(y, 0.5f * s.Ly, s.inv_dy, s.ny);
+    const Cic cz = cic_axis(z, 0.5f * s.Lz, s.inv_dz, s.nz);
+    return ((cz.i0 >> 2) * s.nby + (cy.i0 >> 2)) * s.nbx + (cx.i0 >> 2);
+}
+
+// Lanes of a warp that share a key add to its counter with one atomic (the
+// Plummer core puts most stars in a few blocks, so per-lane atomics would
+// serialise on those counters).  Returns this lane's slot: base + its rank
+// among the lanes with the same key.
+__device__ __forceinline__ int warp_aggregated_add(int *counter, int key, bool active)
+{
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (!active) return 0;
+    const unsigned same = __match_any_sync(act, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(same) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&counter[key], __popc(same));
+    base = __shfl_sync(same, base, leader);
+    return base + __popc(same & ((1u << lane) - 1u));
+}
+
+__global__ void sort_hist_kernel(SortParams s)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < s.n;
+    int k = 0;
+    if (active) {
+        k = block_key(s.src[0][i], s.src[1][i], s.src[2][i], s);
+        s.key[i] = k;
+    }
+    warp_aggregated_add(s.count, k, active);
+}
+
+// Exclusive scan of count[0..nbins) in place, one CTA of 1024 threads:
+// each thread scans a contiguous chunk, a block scan combines the chunks.
+__global__ void __launch_bounds__(1024) sort_scan_kernel(int *count, int nbins)
+{
+    __shared__ int part[1024];
+    const int chunk = (nbins + 1023) / 1024;
+    const int b0 = threadIdx.x * chunk;
+    const int b1 = min(b0 + chunk, nbins);
+    int sum = 0;
+    for (int b = b0; b < b1; ++b) sum += count[b];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - sum;
+    for (int b = b0; b < b1; ++b) {
+        const int c = count[b];
+        count[b] = run;
+        run += c;
+    }
+}
+
+__global__ void sort_scatter_kernel(SortParams s)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < s.n;
+    const int dst = warp_aggregated_add(s.count, active ? s.key[i] : 0, active);
+    if (!active) return;
+#pragma unroll
+    for (int a = 0; a < 7; ++a) s.dst[a][dst] = s.src[a][i];
+    s.dst_id[dst] = s.src_id[i];
+}
+
+cudaError_t launch_particle_sort(const SortParams &s, cudaStream_t st, int *launches)
+{
+    if (s.n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(s.count, 0, sizeof(int) * (size_t)s.nbins, st);
+    if (e != cudaSuccess) return e;
+    const int nb = (s.n + 255) / 256;
+    sort_hist_kernel<<<nb, 256, 0, st>>>(s);
+    sort_scan_kernel<<<1, 1024, 0, st>>>(s.count, s.nbins);
+    sort_scatter_kernel<<<nb, 256, 0, st>>>(s);
+    if (launches) *launches += 3;
+    return cudaGetLastError();
+}
+
+__global__ void ids_kernel(unsigned int *id, int first, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) id[i] = (unsigned int)(first + i);
+}
+
+cudaError_t launch_particle_ids(unsigned int *id, int first, int n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    ids_kernel<<<(n + 255) / 256, 256, 0, st>>>(id + first, first, n);
+    return cudaGetLastError();
+}
+
+// AoS output in insertion order: slot i holds the star with id[i].
+__global__ void from_soa_by_id_kernel(const float *x, const float *y, const float *z, const float *vx,
+                                      const float *vy, const float *vz, const unsigned int *id, int n,
+                                      float *pos3, float *vel3)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned int o = id[i];
+    if (pos3) {
+        pos3[3 * o + 0] = x[i];
+        pos3[3 * o + 1] = y[i];
+        pos3[3 * o + 2] = z[i];
+    }
+    if (vel3) {
+        vel3[3 * o + 0] = vx[i];
+        vel3[3 * o + 1] = vy[i];
+        vel3[3 * o + 2] = vz[i];
+    }
+}
+
+cudaError_t launch_particles_from_soa_by_id(const float *x, const float *y, const float *z, const float *vx,
+                                            const float *vy, const float *vz, const unsigned int *id, int n,
+                                            float *pos3, float *vel3, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    from_soa_by_id_kernel<<<(n + 255) / 256, 256, 0, st>>>(x, y, z, vx, vy, vz, id, n, pos3, vel3);
+    return cudaGetLastError();
+}
+
+}  // namespace spe

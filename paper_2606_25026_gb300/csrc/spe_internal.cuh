@@ -102,6 +102,16 @@ enum PFlags : int {
     PK_DEPOSIT = 1 << 2,
 };
 
+struct SortParams {
+    float *src[7], *dst[7];        // x, y, z, vx, vy, vz, m
+    unsigned int *src_id, *dst_id;
+    int *key;                      // per star
+    int *count;                    // nbins counters / offsets
+    int n, nbins;
+    int nx, ny, nz, nbx, nby;
+    float Lx, Ly, Lz, inv_dx, inv_dy, inv_dz;
+};
+
 // ---------------------------------------------------------------- launchers
 // Each returns cudaGetLastError() after the launch.  blocks_out (if given)
 // receives the grid size, for the reductions' partial counts.
@@ -118,6 +128,12 @@ cudaError_t launch_particles_to_soa(const float *pos3, const float *vel3, const 
 cudaError_t launch_particles_from_soa(const float *x, const float *y, const float *z, const float *vx,
                                       const float *vy, const float *vz, int n, float *pos3, float *vel3,
                                       cudaStream_t st);
+
+cudaError_t launch_particle_sort(const SortParams &s, cudaStream_t st, int *launches);
+cudaError_t launch_particle_ids(unsigned int *id, int first, int n, cudaStream_t st);
+cudaError_t launch_particles_from_soa_by_id(const float *x, const float *y, const float *z, const float *vx,
+                                            const float *vy, const float *vz, const unsigned int *id, int n,
+                                            float *pos3, float *vel3, cudaStream_t st);
 
 // Grid diagnostics (raw sums): out[0] = sum |psi|^2, out[1] = sum (|psi|^2 + rho_*) phi,
 // out[2] = sum |psi|^4, out[3] = max |phi|, out[4] = max |psi|^2; clears dep if given.
