@@ -24,7 +24,8 @@ template <int N> struct XCfg {
     static constexpr int T = 16;
     static constexpr int TP = T + 1;
     static constexpr int NT = (N * T / 8 >= 256) ? 256 : ((N * T / 8 >= 128) ? 128 : 64);
-    static constexpr size_t smem = sizeof(float2) * N * TP + sizeof(float) * N * T;
+    // tile + aux; aux holds T real rows, or T half-spectrum rows of N/2 + 1 complex while staging
+    static constexpr size_t smem = sizeof(float2) * N * TP + sizeof(float2) * T * (N / 2 + 1);
 };
 
 template <int N>
@@ -40,17 +41,23 @@ __global__ void __launch_bounds__(XCfg<N>::NT) xpass_kernel(XParams p)
 
     // ---- Phi rows from the half spectrum: rows (2m, 2m+1) as one complex line
     if (flags & X_HAS_PHI) {
+        // stage the T half-spectrum rows in aux with asynchronous copies, then build the packed
+        // lines Z = A + iB (Hermitian extension of both rows) from shared memory
+        float2 *stage = reinterpret_cast<float2 *>(aux);
+        for (int idx = tid; idx < T * (H + 1); idx += NT) {
+            const int t = idx / (H + 1), k = idx % (H + 1);
+            const int row = row0 + t;
+            if (row < p.rows) cp_async8(&stage[idx], &p.phik[(size_t)row * p.P + k]);
+            else stage[idx] = make_float2(0.f, 0.f);
+        }
+        cp_async_wait_all();
+        __syncthreads();
         for (int idx = tid; idx < (T / 2) * N; idx += NT) {
             const int n = idx % N, m = idx / N;
-            const int ra = row0 + 2 * m;
-            float2 A = make_float2(0.f, 0.f), B = A;
-            if (ra + 1 < p.rows) {
-                const int kk = (n <= H) ? n : N - n;
-                A = p.phik[(size_t)ra * p.P + kk];
-                B = p.phik[(size_t)(ra + 1) * p.P + kk];
-                if (n > H) { A.y = -A.y; B.y = -B.y; }
-                if (n == 0 || n == H) { A.y = 0.f; B.y = 0.f; }
-            }
+            const int kk = (n <= H) ? n : N - n;
+            float2 A = stage[(2 * m) * (H + 1) + kk], B = stage[(2 * m + 1) * (H + 1) + kk];
+            if (n > H) { A.y = -A.y; B.y = -B.y; }
+            if (n == 0 || n == H) { A.y = 0.f; B.y = 0.f; }
             tile[n * TP + m] = make_float2(A.x - B.y, A.y + B.x);
         }
         __syncthreads();
