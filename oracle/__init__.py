@@ -64,6 +64,9 @@ def _load():
     lib.oracle_fft1.argtypes = [I, dp, I]
     lib.oracle_fft3.argtypes = [I, I, I, dp, I]
     lib.oracle_threads.restype = I
+    lib.oracle_set_absorb.argtypes = [P, D, I]
+    lib.oracle_set_static_phi.argtypes = [P, ctypes.c_void_p]
+    lib.oracle_virial.argtypes = [P, dp]
     _lib = lib
     return lib
 
@@ -168,6 +171,24 @@ class Oracle:
         out = np.empty(7)
         self._lib.oracle_energy(self._h, _dptr(out))
         return dict(zip(ENERGY_FIELDS, out.tolist()))
+
+    def set_absorb(self, alpha: float, nb: int):
+        """Absorbing layer of Sec. 3.1 after every step (alpha = 0 switches it off)."""
+        self._lib.oracle_set_absorb(self._h, float(alpha), int(nb))
+
+    def set_static_phi(self, phi_b):
+        """Static external potential added to Phi_total (None removes it)."""
+        if phi_b is None:
+            self._lib.oracle_set_static_phi(self._h, None)
+        else:
+            a = np.ascontiguousarray(phi_b, dtype=np.float64).reshape(self.shape)
+            self._lib.oracle_set_static_phi(self._h, a.ctypes.data)
+
+    def virial(self) -> dict:
+        """The paper's overall energy terms K, Q, V (Sec. 3.6), their sum and 2K + 2Q + V."""
+        out = np.empty(5)
+        self._lib.oracle_virial(self._h, _dptr(out))
+        return dict(zip(("K", "Q", "V", "E", "virial"), out.tolist()))
 
     def suggest_dt(self, safety: float = 0.9) -> float:
         return float(self._lib.oracle_suggest_dt(self._h, float(safety)))

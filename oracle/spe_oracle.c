@@ -171,6 +171,9 @@ typedef struct {
     int phi_valid;
     size_t np;
     double *pos, *vel, *mass;  /* n x 3, n x 3, n */
+    double *phi_b;             /* static external potential (Sec. 3.2.2 static mode), or NULL */
+    double absorb_alpha;       /* absorbing layer (Sec. 3.1): alpha, 0 = off */
+    int absorb_nb;             /* N_b */
 } oracle_t;
 
 static size_t ncells(const oracle_t *o) { return (size_t)o->nx * o->ny * o->nz; }
@@ -206,6 +209,7 @@ void oracle_destroy(oracle_t *o)
     if (!o) return;
     free(o->psi); free(o->phi); free(o->rho_star);
     free(o->pos); free(o->vel); free(o->mass);
+    free(o->phi_b);
     free(o);
 }
 
@@ -366,7 +370,7 @@ static void compute_phi(oracle_t *o)
             }
     fft3(w, o->nx, o->ny, o->nz, +1);
     #pragma omp parallel for schedule(static)
-    for (long c = 0; c < (long)n; ++c) o->phi[c] = creal(w[c]);
+    for (long c = 0; c < (long)n; ++c) o->phi[c] = creal(w[c]) + (o->phi_b ? o->phi_b[c] : 0.0);
     free(w);
     o->phi_valid = 1;
 }
@@ -421,6 +425,52 @@ static void particles_drift(oracle_t *o, double dt)
         }
 }
 
+/* Sec. 3.1 absorbing layer, applied after the second half kick (Algorithm 1):
+ * B = exp(-alpha dt (6 - sum_a [tanh((x_a + L_a/2)/(L_a/N_b)) - tanh((x_a - L_a/2)/(L_a/N_b))])),
+ * reading the trailing dt of the printed formula as multiplying the exponent. */
+static double absorb_factor(const oracle_t *o, int i, int j, int k, double dt)
+{
+    int idx[3] = {i, j, k};
+    int nn[3] = {o->nx, o->ny, o->nz};
+    double sum = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double L = o->L[a];
+        double x = -0.5 * L + idx[a] * (L / nn[a]);
+        double w = L / o->absorb_nb;
+        sum += tanh((x + 0.5 * L) / w) - tanh((x - 0.5 * L) / w);
+    }
+    return exp(-o->absorb_alpha * dt * (6.0 - sum));
+}
+
+static void absorb(oracle_t *o, double dt)
+{
+    if (o->absorb_alpha == 0.0 || o->absorb_nb <= 0) return;
+    #pragma omp parallel for schedule(static)
+    for (long k = 0; k < o->nz; ++k)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i)
+                o->psi[(size_t)i + (size_t)o->nx * ((size_t)j + (size_t)o->ny * (size_t)k)] *=
+                    absorb_factor(o, i, j, (int)k, dt);
+}
+
+void oracle_set_absorb(oracle_t *o, double alpha, int nb)
+{
+    o->absorb_alpha = alpha;
+    o->absorb_nb = nb;
+}
+
+/* Static external potential added to Phi_total (NULL removes it). */
+void oracle_set_static_phi(oracle_t *o, const double *phi_b)
+{
+    free(o->phi_b);
+    o->phi_b = NULL;
+    if (phi_b) {
+        o->phi_b = (double *)malloc(sizeof(double) * ncells(o));
+        memcpy(o->phi_b, phi_b, sizeof(double) * ncells(o));
+    }
+    o->phi_valid = 0;
+}
+
 /* nsteps kick-drift-kick steps of size dt (Sec. 3.1 Eq. (SPE_solver_KDK),
  * Algorithm 1), with the star particles advanced by a KDK leapfrog using the
  * same Phi_total (Sec. 3.2.2, dynamic mode). */
@@ -435,6 +485,7 @@ void oracle_step(oracle_t *o, int nsteps, double dt)
         compute_phi(o);                 /* (c) */
         kick(o, 0.5 * dt);              /* (d) */
         particles_kick(o, 0.5 * dt);
+        absorb(o, dt);                  /* absorbing layer (Algorithm 1) */
     }
 }
 
@@ -475,7 +526,8 @@ void oracle_energy(oracle_t *o, double *out)
     for (size_t c = 0; c < n; ++c) {
         double a2 = creal(o->psi[c]) * creal(o->psi[c]) + cimag(o->psi[c]) * cimag(o->psi[c]);
         mass += a2 * dv;
-        pot += 0.5 * (a2 + o->rho_star[c]) * o->phi[c] * dv;
+        /* self gravity counted once (the 1/2), a static external potential in full */
+        pot += 0.5 * (a2 + o->rho_star[c]) * (o->phi[c] + (o->phi_b ? o->phi_b[c] : 0.0)) * dv;
         inter += 0.5 * o->kappa * a2 * a2 * dv;
         if (fabs(o->phi[c]) > maxphi) maxphi = fabs(o->phi[c]);
     }
@@ -506,6 +558,47 @@ void oracle_energy(oracle_t *o, double *out)
     out[4] = skin;
     out[5] = kin + pot + inter + skin;
     out[6] = maxphi;
+}
+
+/* Sec. 3.6 overall energy terms, with the second-order central differences of
+ * Sec. 3.1 for the gradients (periodic), eta^2 restoring the dimensional
+ * prefactor the paper absorbs (eta = 1 gives the paper's expressions):
+ *   K = 1/2 sum (rho v)^2 / rho dV, rho v = eta Im(conj(psi) grad psi)
+ *   Q = eta^2 sum |grad sqrt(rho)|^2 dV
+ *   V = sum rho Phi_total dV         (rho = |psi|^2)
+ * out = {K, Q, V, K + Q + V, 2K + 2Q + V}. */
+void oracle_virial(oracle_t *o, double *out)
+{
+    if (!o->phi_valid) compute_phi(o);
+    double dv = cell_volume(o);
+    double h[3] = {o->L[0] / o->nx, o->L[1] / o->ny, o->L[2] / o->nz};
+    double K = 0.0, Q = 0.0, V = 0.0;
+    for (int k = 0; k < o->nz; ++k)
+        for (int j = 0; j < o->ny; ++j)
+            for (int i = 0; i < o->nx; ++i) {
+                size_t c = node(o, i, j, k);
+                cplx p = o->psi[c];
+                double rho = creal(p) * creal(p) + cimag(p) * cimag(p);
+                V += rho * o->phi[c] * dv;
+                size_t up[3] = {node(o, i + 1, j, k), node(o, i, j + 1, k), node(o, i, j, k + 1)};
+                size_t dn[3] = {node(o, i - 1, j, k), node(o, i, j - 1, k), node(o, i, j, k - 1)};
+                double j2 = 0.0, g2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    cplx d = (o->psi[up[a]] - o->psi[dn[a]]) / (2.0 * h[a]);
+                    double jj = o->eta * cimag(conj(p) * d);
+                    j2 += jj * jj;
+                    double su = cabs(o->psi[up[a]]), sd = cabs(o->psi[dn[a]]);
+                    double gs = (su - sd) / (2.0 * h[a]);
+                    g2 += gs * gs;
+                }
+                if (rho > 0.0) K += 0.5 * j2 / rho * dv;
+                Q += o->eta * o->eta * g2 * dv;
+            }
+    out[0] = K;
+    out[1] = Q;
+    out[2] = V;
+    out[3] = K + Q + V;
+    out[4] = 2.0 * K + 2.0 * Q + V;
 }
 
 /* Sec. 3.5: dt_max = 0.5 min{ 4/(3 pi) dx^2 / eta, 2 pi eta / max|Phi|,
