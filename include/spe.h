@@ -68,6 +68,7 @@ extern "C" {
 #define SPE_ASYNC         (1 << 2)  /* spe_step returns after enqueueing; no status check */
 #define SPE_PROFILE       (1 << 3)  /* time every kernel launch with CUDA events (spe_profile_read) */
 #define SPE_NO_GRAPH      (1 << 4)  /* launch the per-step kernels directly, never through a CUDA graph */
+#define SPE_STATIC_POTENTIAL (1 << 5) /* reserve a static external potential (spe_set_static_potential) */
 
 typedef struct spe_grid spe_grid;   /* opaque */
 
@@ -80,6 +81,8 @@ typedef struct {
     size_t max_particles;    /* particle capacity (0 = field only) */
     int flags;               /* SPE_* flags above */
     void *cuda_stream;       /* cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream; NULL = default */
+    double absorb_alpha;     /* absorbing layer of Sec. 3.1 (alpha; 0 = off; the paper's default is 10) */
+    int absorb_nb;           /* its transition parameter N_b (the paper's default is 50) */
 } spe_config;
 
 typedef struct {
@@ -91,6 +94,16 @@ typedef struct {
     double total;         /* kinetic + potential + interaction + star_kinetic */
     double max_abs_phi;   /* max |Phi| over the nodes */
 } spe_energy_t;
+
+/* The paper's overall energy terms (Sec. 3.6), gradients by second-order
+ * central differences (Sec. 3.1), eta^2 restoring the prefactor the paper
+ * absorbs:  K = 1/2 sum (rho v)^2/rho dV with rho v = eta Im(conj(psi) grad psi),
+ * Q = eta^2 sum |grad sqrt(rho)|^2 dV, V = sum |psi|^2 Phi dV (Phi total). */
+typedef struct {
+    double K, Q, V;
+    double E;        /* K + Q + V */
+    double virial;   /* 2K + 2Q + V (zero at virial equilibrium in the paper's statement) */
+} spe_virial_t;
 
 /* Device bytes a grid with this configuration needs (field buffers, the
  * half-spectrum potential buffer, particle arrays, tables and reduction
@@ -135,6 +148,15 @@ SPE_API int spe_density(spe_grid *g, float *out, int where);
 
 /* Phi on the nodes (zero mode removed): nx*ny*nz floats. */
 SPE_API int spe_potential(spe_grid *g, float *out, int where);
+
+/* Static external potential Phi_b (Sec. 3.2.2, static particle mode): added
+ * to Phi_total for the kick, the star accelerations, spe_potential and the
+ * energy (where it counts once, not halved).  nx*ny*nz floats; NULL removes
+ * it.  Needs SPE_STATIC_POTENTIAL at creation (else SPE_ESTATE). */
+SPE_API int spe_set_static_potential(spe_grid *g, const float *phi_b, int where);
+
+/* K, Q, V of Sec. 3.6 (FP64 accumulation on the device). */
+SPE_API int spe_virial(spe_grid *g, spe_virial_t *out);
 
 /* Mass and energy terms (FP64 accumulation on the device). */
 SPE_API int spe_energy(spe_grid *g, spe_energy_t *out);

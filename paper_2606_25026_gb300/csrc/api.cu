@@ -85,7 +85,7 @@ struct ProfRec {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t psi, phik, phi, dep, part, bins, tw, k2, drift, partials, counter, diag, total;
+    size_t psi, phik, phi, phib, dep, part, bins, tw, k2, drift, absorb, partials, counter, diag, total;
 };
 
 int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
@@ -94,6 +94,8 @@ int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
     if (!supported_n(c->nx) || !supported_n(c->ny) || !supported_n(c->nz)) return SPE_EINVAL;
     if (!(c->Lx > 0) || !(c->Ly > 0) || !(c->Lz > 0) || !(c->hbar_over_m > 0)) return SPE_EINVAL;
     if (!isfinite(c->G) || !isfinite(c->kappa)) return SPE_EINVAL;
+    if (!isfinite(c->absorb_alpha) || c->absorb_alpha < 0 || (c->absorb_alpha > 0 && c->absorb_nb <= 0))
+        return SPE_EINVAL;
     if (c->max_particles > (size_t)0x7fffffff) return SPE_EINVAL;
     const size_t ncells = (size_t)c->nx * c->ny * c->nz;
     const int w = c->nx / 2 + 1;
@@ -102,6 +104,7 @@ int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
     L->psi = off;      off = align256(off + ncells * sizeof(float2));
     L->phik = off;     off = align256(off + (size_t)c->ny * c->nz * p * sizeof(float2));
     L->phi = off;      off = align256(off + ncells * sizeof(float));
+    L->phib = off;     off = align256(off + ((c->flags & SPE_STATIC_POTENTIAL) ? ncells * sizeof(float) : 0));
     L->dep = off;      off = align256(off + (c->max_particles ? ncells * sizeof(long long) : 0));
     // two sets of star arrays (x, y, z, vx, vy, vz, m, id) for reordering, sort keys, block counters
     L->part = off;     off = align256(off + 17 * align256(c->max_particles * sizeof(float)));
@@ -109,6 +112,7 @@ int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
     L->tw = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float4));
     L->k2 = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float));
     L->drift = off;    off = align256(off + ((size_t)c->nx * c->ny + c->nz) * sizeof(float4));
+    L->absorb = off;   off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float));
     L->partials = off; off = align256(off + (size_t)kMaxPartials * 5 * sizeof(double));
     L->counter = off;  off = align256(off + 256);
     L->diag = off;     off = align256(off + 64 * sizeof(double));
@@ -148,7 +152,11 @@ struct spe_grid {
     double *partials;
     unsigned int *counter;
     double *diag;
-    float4 *h_stage;  // pinned staging for the drift tables
+    float4 *h_stage;  // pinned staging for the drift and absorbing-layer tables
+    float *phib;      // static external potential (SPE_STATIC_POTENTIAL)
+    bool static_set;
+    float *absorb;    // absorbing-layer factors per axis: nx, ny, nz floats (dt dependent)
+    bool absorbing;
     size_t np;
     double mstar;
     double quantum;
@@ -219,6 +227,11 @@ XParams base_x(spe_grid *g)
     p.partials = g->partials;
     p.counter = g->counter;
     p.result = g->diag;
+    p.absorb_x = g->absorb;
+    p.absorb_y = g->absorb + g->n[0];
+    p.absorb_z = g->absorb + g->n[0] + g->n[1];
+    p.phib = g->phib;
+    p.ny = g->n[1];
     return p;
 }
 
@@ -337,12 +350,32 @@ int ensure_drift_tables(spe_grid *g, double dt)
     e = cudaMemcpyAsync(g->dxy, g->h_stage, ((size_t)nx * ny + nz) * sizeof(float4), cudaMemcpyHostToDevice,
                         g->st);
     if (e != cudaSuccess) return SPE_ECUDA;
+    if (g->absorbing) {
+        // Sec. 3.1 layer per axis: exp(-alpha dt (2 - [tanh((x + L/2)/(L/N_b)) - tanh((x - L/2)/(L/N_b))]));
+        // the product over the three axes is the printed 3D factor
+        float *ab = reinterpret_cast<float *>(g->h_stage + (size_t)nx * ny + nz);
+        int off = 0;
+        for (int a = 0; a < 3; ++a) {
+            const double La = g->L[a], w = La / g->cfg.absorb_nb;
+            for (int i = 0; i < g->n[a]; ++i) {
+                const double x = -0.5 * La + i * g->dx[a];
+                const double sa = tanh((x + 0.5 * La) / w) - tanh((x - 0.5 * La) / w);
+                ab[off + i] = (float)exp(-g->cfg.absorb_alpha * dt * (2.0 - sa));
+            }
+            off += g->n[a];
+        }
+        e = cudaMemcpyAsync(g->absorb, ab, (size_t)off * sizeof(float), cudaMemcpyHostToDevice, g->st);
+        if (e != cudaSuccess) return SPE_ECUDA;
+    }
     g->tables_valid = true;
     g->table_dt = dt;
     return SPE_OK;
 }
 
-bool has_kick(spe_grid *g) { return g->gravity || g->cfg.kappa != 0.0; }
+bool has_kick(spe_grid *g) { return g->gravity || g->cfg.kappa != 0.0 || g->static_set; }
+// stars feel a potential (self gravity and / or the static one)
+bool stars_kicked(spe_grid *g) { return g->gravity || g->static_set; }
+int static_flag(spe_grid *g) { return g->static_set ? X_STATIC : 0; }
 
 // Phi from the current psi and particles (the state at n = 0 of Algorithm 1,
 // or after set_ic / add_particles).
@@ -419,19 +452,23 @@ int sort_particles(spe_grid *g)
 
 // One KDK step whose leading kick has size dtk (dt/2 for the first step of
 // a call, dt afterwards).
-int step_body(spe_grid *g, double dtk, double dt)
+// absorb_prev: apply the absorbing layer of the previous step (all steps of a
+// call but the first; the call's last step gets it in the final kick pass).
+int step_body(spe_grid *g, double dtk, double dt, bool absorb_prev)
 {
     int rc;
     const bool grav = g->gravity;
     const bool parts = g->np > 0;
+    const bool skick = parts && stars_kicked(g);
     XParams xp = base_x(g);
-    xp.flags = X_FFT | (has_kick(g) ? X_KICK : 0) | (grav ? X_HAS_PHI : 0) | ((parts && grav) ? X_WRITE_PHI : 0);
+    xp.flags = X_FFT | (has_kick(g) ? X_KICK : 0) | (grav ? X_HAS_PHI : 0) | (skick ? X_WRITE_PHI : 0) |
+               static_flag(g) | ((absorb_prev && g->absorbing) ? X_ABSORB : 0);
     xp.kick_scale = (float)(dtk / g->cfg.hbar_over_m);
     if ((rc = run_x(g, KIND_X_KICK_FFT, xp))) return rc;
     if (parts) {
         if (g->steps_done % kSortEvery == 0 && (rc = sort_particles(g))) return rc;
         PParams pp = base_p(g);
-        pp.flags = PK_DRIFT | (grav ? (PK_KICK | PK_DEPOSIT) : 0);
+        pp.flags = PK_DRIFT | (skick ? PK_KICK : 0) | (grav ? PK_DEPOSIT : 0);
         pp.kick = (float)dtk;
         pp.drift = (float)dt;
         if ((rc = launch(g, KIND_PARTICLES, [&] { return launch_particles(pp, g->st); }))) return rc;
@@ -464,13 +501,15 @@ int final_half_kick(spe_grid *g, double h)
     int rc;
     const bool grav = g->gravity;
     const bool parts = g->np > 0;
-    if (has_kick(g)) {
+    const bool skick = parts && stars_kicked(g);
+    if (has_kick(g) || g->absorbing) {
         XParams xp = base_x(g);
-        xp.flags = X_KICK | (grav ? X_HAS_PHI : 0) | ((parts && grav) ? X_WRITE_PHI : 0);
+        xp.flags = (has_kick(g) ? X_KICK : 0) | (grav ? X_HAS_PHI : 0) | (skick ? X_WRITE_PHI : 0) | static_flag(g) |
+                   (g->absorbing ? X_ABSORB : 0);
         xp.kick_scale = (float)(h / g->cfg.hbar_over_m);
         if ((rc = run_x(g, KIND_X_KICK_FINAL, xp))) return rc;
     }
-    if (parts && grav) {
+    if (skick) {
         PParams pp = base_p(g);
         pp.flags = PK_KICK;
         pp.kick = (float)h;
@@ -484,9 +523,13 @@ int potential_to_phi(spe_grid *g)
 {
     int rc;
     if (!g->phi_valid && (rc = compute_phi(g))) return rc;
-    if (!g->gravity) return cuerr(cudaMemsetAsync(g->phi, 0, g->ncells * sizeof(float), g->st));
+    if (!g->gravity) {
+        if (g->static_set)
+            return cuerr(cudaMemcpyAsync(g->phi, g->phib, g->ncells * sizeof(float), cudaMemcpyDeviceToDevice, g->st));
+        return cuerr(cudaMemsetAsync(g->phi, 0, g->ncells * sizeof(float), g->st));
+    }
     XParams xp = base_x(g);
-    xp.flags = X_HAS_PHI | X_WRITE_PHI;
+    xp.flags = X_HAS_PHI | X_WRITE_PHI | static_flag(g);
     return run_x(g, KIND_X_POTENTIAL, xp);
 }
 
@@ -580,7 +623,8 @@ int spe_create_grid(const spe_config *cfg, void *workspace, size_t workspace_byt
         }
         g->owns_ws = true;
     }
-    if (cudaMallocHost(&g->h_stage, ((size_t)cfg->nx * cfg->ny + cfg->nz) * sizeof(float4)) != cudaSuccess) {
+    if (cudaMallocHost(&g->h_stage, ((size_t)cfg->nx * cfg->ny + 2 * cfg->nz + cfg->nx + cfg->ny) * sizeof(float4)) !=
+        cudaSuccess) {
         cudaGetLastError();
         if (g->owns_ws) cudaFree(g->ws);
         delete g;
@@ -608,6 +652,9 @@ int spe_create_grid(const spe_config *cfg, void *workspace, size_t workspace_byt
     g->k2[0] = (float *)(b + L.k2);
     g->k2[1] = g->k2[0] + cfg->nx;
     g->k2[2] = g->k2[1] + cfg->ny;
+    g->phib = (cfg->flags & SPE_STATIC_POTENTIAL) ? (float *)(b + L.phib) : nullptr;
+    g->absorb = (float *)(b + L.absorb);
+    g->absorbing = cfg->absorb_alpha > 0.0;
     g->dxy = (float4 *)(b + L.drift);
     g->ez = g->dxy + (size_t)cfg->nx * cfg->ny;
     g->partials = (double *)(b + L.partials);
@@ -742,7 +789,7 @@ int spe_step(spe_grid *g, int nsteps, double dt)
     if (!g->phi_valid && (rc = compute_phi(g))) return rc;
     for (int s = 0; s < nsteps; ++s)
     {
-        if ((rc = step_body(g, s == 0 ? 0.5 * dt : dt, dt))) return rc;
+        if ((rc = step_body(g, s == 0 ? 0.5 * dt : dt, dt, s > 0))) return rc;
         g->steps_done++;
     }
     if ((rc = final_half_kick(g, 0.5 * dt))) return rc;
@@ -783,7 +830,7 @@ int spe_suggest_dt(spe_grid *g, double safety, double *dt_out)
     if (g->dx[2] < dx) dx = g->dx[2];
     const double eta = g->cfg.hbar_over_m;
     double t = 4.0 / (3.0 * kPi) * dx * dx / eta;
-    const double maxphi = g->gravity ? raw[3] : 0.0, maxrho = raw[4];
+    const double maxphi = (g->gravity || g->static_set) ? raw[3] : 0.0, maxrho = raw[4];
     if (maxphi > 0.0 && 2.0 * kPi * eta / maxphi < t) t = 2.0 * kPi * eta / maxphi;
     if (g->cfg.kappa != 0.0 && maxrho > 0.0) {
         const double ti = 2.0 * kPi * eta / (fabs(g->cfg.kappa) * maxrho);
@@ -828,6 +875,17 @@ int spe_energy(spe_grid *g, spe_energy_t *out)
                                      g->st);
          })))
         return rc;
+    double static_raw = 0.0;
+    if (g->static_set) {
+        // the static potential counts once, not halved: add 1/2 sum (|psi|^2 + rho_*) Phi_b dV
+        if ((rc = deposit_only(g))) return rc;
+        if ((rc = launch(g, KIND_DIAG, [&] {
+                 return launch_grid_diag(g->psi, g->phib, g->np ? g->dep : nullptr, (float)(g->quantum / g->dv),
+                                         0.f, g->dv, g->ncells, g->partials, g->counter, g->diag + 24, g->st);
+             })))
+            return rc;
+        if ((rc = copy_out(g, &static_raw, g->diag + 25, sizeof(double), SPE_HOST))) return rc;
+    }
     // kinetic: sum over axes of (1/N_a) sum_lines sum_k k_a^2 |F_a line|^2
     XParams xp = base_x(g);
     xp.flags = X_KIN;
@@ -854,12 +912,51 @@ int spe_energy(spe_grid *g, spe_energy_t *out)
     if (g->np) skin = raw[11];
     const double eta = g->cfg.hbar_over_m;
     out->mass = raw[0] * g->dv;
-    out->potential = g->gravity ? 0.5 * raw[1] * g->dv : 0.0;
+    const bool has_phi = g->gravity || g->static_set;
+    out->potential = has_phi ? 0.5 * (raw[1] + static_raw) * g->dv : 0.0;
     out->interaction = 0.5 * g->cfg.kappa * raw[2] * g->dv;
-    out->max_abs_phi = g->gravity ? raw[3] : 0.0;
+    out->max_abs_phi = has_phi ? raw[3] : 0.0;
     out->kinetic = 0.5 * eta * eta * g->dv * (raw[8] / g->n[0] + raw[9] / g->n[1] + raw[10] / g->n[2]);
     out->star_kinetic = skin;
     out->total = out->kinetic + out->potential + out->interaction + out->star_kinetic;
+    return SPE_OK;
+}
+
+int spe_set_static_potential(spe_grid *g, const float *phi_b, int where)
+{
+    if (!g || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
+    if (!g->phib) return SPE_ESTATE;
+    if (!phi_b) {
+        g->static_set = false;
+        return SPE_OK;
+    }
+    cudaError_t e = cudaMemcpyAsync(g->phib, phi_b, g->ncells * sizeof(float),
+                                    where == SPE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) return SPE_ECUDA;
+    g->static_set = true;
+    return SPE_OK;
+}
+
+int spe_virial(spe_grid *g, spe_virial_t *out)
+{
+    if (!g || !out) return SPE_EINVAL;
+    int rc;
+    if ((rc = potential_to_phi(g))) return rc;
+    if ((rc = launch(g, KIND_DIAG, [&] {
+             return launch_virial(g->psi, g->phi, g->n[0], g->n[1], g->n[2], (float)(0.5 / g->dx[0]),
+                                  (float)(0.5 / g->dx[1]), (float)(0.5 / g->dx[2]), g->partials, g->counter,
+                                  g->diag + 32, g->st);
+         })))
+        return rc;
+    double raw[3];
+    if ((rc = copy_out(g, raw, g->diag + 32, sizeof(raw), SPE_HOST))) return rc;
+    const double eta = g->cfg.hbar_over_m;
+    out->K = 0.5 * eta * eta * raw[0] * g->dv;
+    out->Q = eta * eta * raw[1] * g->dv;
+    out->V = raw[2] * g->dv;
+    out->E = out->K + out->Q + out->V;
+    out->virial = 2.0 * out->K + 2.0 * out->Q + out->V;
     return SPE_OK;
 }
 

@@ -92,3 +92,60 @@ cudaError_t launch_density(const float2 *psi, long long *dep, float dep_scale, f
 }
 
 }  // namespace spe
+
+namespace spe {
+
+// Raw sums of the Sec. 3.6 energy terms with second-order central differences
+// (Sec. 3.1), periodic: out[0] = sum |Im(conj psi D psi)|^2 / |psi|^2,
+// out[1] = sum |D |psi||^2, out[2] = sum |psi|^2 Phi (the caller scales).
+__global__ void __launch_bounds__(kDiagNT) virial_kernel(const float2 *__restrict__ psi,
+                                                         const float *__restrict__ phi, int nx, int ny, int nz,
+                                                         float ihx, float ihy, float ihz, double *partials,
+                                                         unsigned int *counter, double *out)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (size_t i = blockIdx.x * (size_t)kDiagNT + threadIdx.x; i < n; i += (size_t)gridDim.x * kDiagNT) {
+        const int x = (int)(i % nx);
+        const int y = (int)((i / nx) % ny);
+        const int z = (int)(i / ((size_t)nx * ny));
+        const float2 p = psi[i];
+        const double rho = (double)p.x * p.x + (double)p.y * p.y;
+        const size_t sx = 1, sy = nx, sz = (size_t)nx * ny;
+        size_t u[3], d[3];
+        u[0] = (x + 1 == nx) ? i - (size_t)(nx - 1) : i + sx;
+        d[0] = (x == 0) ? i + (size_t)(nx - 1) : i - sx;
+        u[1] = (y + 1 == ny) ? i - (size_t)(ny - 1) * sy : i + sy;
+        d[1] = (y == 0) ? i + (size_t)(ny - 1) * sy : i - sy;
+        u[2] = (z + 1 == nz) ? i - (size_t)(nz - 1) * sz : i + sz;
+        d[2] = (z == 0) ? i + (size_t)(nz - 1) * sz : i - sz;
+        const float ih[3] = {ihx, ihy, ihz};
+        double j2 = 0.0, g2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float2 pu = psi[u[a]], pd = psi[d[a]];
+            const double dre = ((double)pu.x - pd.x) * ih[a], dim = ((double)pu.y - pd.y) * ih[a];
+            const double j = (double)p.x * dim - (double)p.y * dre;
+            j2 += j * j;
+            const double gs = (sqrt((double)pu.x * pu.x + (double)pu.y * pu.y) -
+                               sqrt((double)pd.x * pd.x + (double)pd.y * pd.y)) * ih[a];
+            g2 += gs * gs;
+        }
+        if (rho > 0.0) acc[0] += j2 / rho;
+        acc[1] += g2;
+        acc[2] += rho * (phi ? (double)phi[i] : 0.0);
+    }
+    grid_reduce<3, kDiagNT>(acc, 0, partials, counter, out);
+}
+
+cudaError_t launch_virial(const float2 *psi, const float *phi, int nx, int ny, int nz, float ihx, float ihy,
+                          float ihz, double *partials, unsigned int *counter, double *out, cudaStream_t st)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    size_t blocks = (n + kDiagNT - 1) / kDiagNT;
+    if (blocks > (size_t)kReduceBlocks) blocks = kReduceBlocks;
+    virial_kernel<<<(unsigned)blocks, kDiagNT, 0, st>>>(psi, phi, nx, ny, nz, ihx, ihy, ihz, partials, counter, out);
+    return cudaGetLastError();
+}
+
+}  // namespace spe

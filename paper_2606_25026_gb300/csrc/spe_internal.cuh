@@ -26,6 +26,8 @@ enum XFlags : int {
     X_MASS = 1 << 6,       // reduce sum |psi|^2 into diag[0] (deterministic)
     X_R2C = 1 << 7,        // forward real-to-complex x transform of rho into the half spectrum
     X_KIN = 1 << 8,        // reduce sum_k kx^2 |psi_hat|^2 (energy diagnostic), no store
+    X_ABSORB = 1 << 9,     // psi *= absorbing-layer factor absorb_x[x] absorb_y[y] absorb_z[z]
+    X_STATIC = 1 << 10,    // add the static potential phib to Phi (kick and phi_out)
 };
 
 struct XParams {
@@ -44,6 +46,9 @@ struct XParams {
     unsigned int *counter;    // last-block ticket (returns to 0 after use)
     double *result;           // where the final reduction goes
     int *status;              // device status word (bit 0: non-finite mass)
+    const float *absorb_x, *absorb_y, *absorb_z;  // per-axis absorbing-layer factors (X_ABSORB)
+    const float *phib;        // static external potential, nodes (X_STATIC)
+    int ny;                   // rows are y + ny z
     int flags;
 };
 
@@ -141,6 +146,10 @@ cudaError_t launch_particles_from_soa_by_id(const float *x, const float *y, cons
 cudaError_t launch_grid_diag(const float2 *psi, const float *phi, long long *dep, float dep_scale, float kappa,
                              double dv, size_t ncells, double *partials, unsigned int *counter, double *out,
                              cudaStream_t st);
+// Raw sums of the Sec. 3.6 terms: out[0] = sum |Im(conj psi D psi)|^2/|psi|^2, out[1] = sum |D|psi||^2,
+// out[2] = sum |psi|^2 phi, D the central difference (ihx = 1/(2 dx), ...).
+cudaError_t launch_virial(const float2 *psi, const float *phi, int nx, int ny, int nz, float ihx, float ihy,
+                          float ihz, double *partials, unsigned int *counter, double *out, cudaStream_t st);
 // out[0] = 1/2 sum m v^2
 cudaError_t launch_particle_ke(const float *vx, const float *vy, const float *vz, const float *m, int n,
                                double *partials, unsigned int *counter, double *out, cudaStream_t st);

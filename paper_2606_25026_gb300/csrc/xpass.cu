@@ -69,8 +69,13 @@ __global__ void __launch_bounds__(XCfg<N>::NT) xpass_kernel(XParams p)
             aux[(2 * m + 1) * N + n] = z.y;
             const int ra = row0 + 2 * m;
             if ((flags & X_WRITE_PHI) && ra + 1 < p.rows) {
-                p.phi_out[(size_t)ra * N + n] = z.x;
-                p.phi_out[(size_t)(ra + 1) * N + n] = z.y;
+                float za = z.x, zb = z.y;
+                if (flags & X_STATIC) {
+                    za += __ldg(&p.phib[(size_t)ra * N + n]);
+                    zb += __ldg(&p.phib[(size_t)(ra + 1) * N + n]);
+                }
+                p.phi_out[(size_t)ra * N + n] = za;
+                p.phi_out[(size_t)(ra + 1) * N + n] = zb;
             }
         }
         __syncthreads();
@@ -96,11 +101,22 @@ __global__ void __launch_bounds__(XCfg<N>::NT) xpass_kernel(XParams p)
                 // the factor's modulus error is O(ph^2 eps) instead of the O(eps) of a rounded cos ph,
                 // which would otherwise recur identically step after step while Phi changes slowly.
                 const float a2 = v.x * v.x + v.y * v.y;
-                const float phi = (flags & X_HAS_PHI) ? aux[t * N + n] : 0.f;
+                float phi = (flags & X_HAS_PHI) ? aux[t * N + n] : 0.f;
+                if ((flags & X_STATIC) && row < p.rows) {
+                    const float pb = __ldg(&p.phib[(size_t)row * N + n]);
+                    phi += pb;
+                    if ((flags & X_WRITE_PHI) && !(flags & X_HAS_PHI)) p.phi_out[(size_t)row * N + n] = pb;
+                }
                 float sh, ch;
                 sincosf(0.5f * ((phi + p.kappa * a2) * p.kick_scale), &sh, &ch);
                 const float cm1 = -2.f * sh * sh, sn = 2.f * sh * ch;
                 v = make_float2(fmaf(v.x, cm1, fmaf(v.y, sn, v.x)), fmaf(v.y, cm1, fmaf(-v.x, sn, v.y)));
+            }
+            if ((flags & X_ABSORB) && row < p.rows) {
+                // absorbing layer of the step that just ended (Sec. 3.1, Algorithm 1): a real
+                // pointwise factor, so it commutes with the kick it is fused with
+                const float b = __ldg(&p.absorb_x[n]) * __ldg(&p.absorb_y[row % p.ny]) * __ldg(&p.absorb_z[row / p.ny]);
+                v = make_float2(v.x * b, v.y * b);
             }
             if (fft) tile[n * TP + t] = v;
             else if (row < p.rows) p.psi[(size_t)row * N + n] = v;

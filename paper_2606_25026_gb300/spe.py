@@ -22,6 +22,7 @@ SPE_NO_CFL_CHECK = 1 << 1
 SPE_ASYNC = 1 << 2
 SPE_PROFILE = 1 << 3
 SPE_NO_GRAPH = 1 << 4
+SPE_STATIC_POTENTIAL = 1 << 5
 
 SUPPORTED_N = (4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024)
 
@@ -31,6 +32,7 @@ EXPORTED = (
     "spe_clear_particles", "spe_step", "spe_suggest_dt", "spe_density", "spe_potential", "spe_energy",
     "spe_last_mass", "spe_get_psi", "spe_get_particles", "spe_particle_count", "spe_sync",
     "spe_launch_count", "spe_profile_read", "spe_strerror", "spe_field_energy_noalloc",
+    "spe_set_static_potential", "spe_virial",
 )
 
 
@@ -46,7 +48,12 @@ class spe_config(ctypes.Structure):
         ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
         ("hbar_over_m", ctypes.c_double), ("G", ctypes.c_double), ("kappa", ctypes.c_double),
         ("max_particles", ctypes.c_size_t), ("flags", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+        ("absorb_alpha", ctypes.c_double), ("absorb_nb", ctypes.c_int),
     ]
+
+
+class spe_virial_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("K", "Q", "V", "E", "virial")]
 
 
 class spe_energy_t(ctypes.Structure):
@@ -89,6 +96,8 @@ def load_library(path: str = LIB_PATH):
                                  ctypes.POINTER(D), I]),
         "spe_strerror": (ctypes.c_char_p, [I]),
         "spe_field_energy_noalloc": (I, [P, S, D, D, ctypes.POINTER(D), I, P]),
+        "spe_set_static_potential": (I, [P, fp, I]),
+        "spe_virial": (I, [P, ctypes.POINTER(spe_virial_t)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -131,7 +140,7 @@ class Grid:
     launch_count, profile_read, destroy."""
 
     def __init__(self, nx, ny=None, nz=None, L=1.0, hbar_over_m=1.0, G=1.0, kappa=0.0, max_particles=0,
-                 flags=0, stream=None, device=None):
+                 flags=0, stream=None, device=None, absorb_alpha=0.0, absorb_nb=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libspe needs a CUDA device; there is no CPU fallback")
@@ -145,7 +154,8 @@ class Grid:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.cfg = spe_config(nx, ny, nz, *(float(v) for v in L), float(hbar_over_m), float(G), float(kappa),
-                              int(max_particles), int(flags), ctypes.c_void_p(self.stream.cuda_stream))
+                              int(max_particles), int(flags), ctypes.c_void_p(self.stream.cuda_stream),
+                              float(absorb_alpha), int(absorb_nb))
         nbytes = ctypes.c_size_t()
         _check(self._lib.spe_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)), "spe_workspace_bytes")
         self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
@@ -239,6 +249,22 @@ class Grid:
         e = spe_energy_t()
         _check(self._lib.spe_energy(self._h, ctypes.byref(e)), "spe_energy")
         return {n: getattr(e, n) for n, _ in spe_energy_t._fields_}
+
+    def set_static_potential(self, phi_b):
+        """Static external potential (nz, ny, nx) float32, numpy or torch; None removes it."""
+        if phi_b is None:
+            _check(self._lib.spe_set_static_potential(self._h, None, SPE_HOST), "spe_set_static_potential")
+            return
+        import torch
+        if not isinstance(phi_b, torch.Tensor):
+            phi_b = np.ascontiguousarray(phi_b, dtype=np.float32)
+        ptr, where, keep = _ptr_where(phi_b)
+        _check(self._lib.spe_set_static_potential(self._h, ctypes.c_void_p(ptr), where), "spe_set_static_potential")
+
+    def virial(self) -> dict:
+        v = spe_virial_t()
+        _check(self._lib.spe_virial(self._h, ctypes.byref(v)), "spe_virial")
+        return {n: getattr(v, n) for n, _ in spe_virial_t._fields_}
 
     def last_mass(self) -> float:
         out = ctypes.c_double()
