@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="halo256_stars1e6",
-                    choices=["halo256_stars1e6", "halo512", "packets32"])
+                    choices=["halo256_stars1e6", "halo512", "packets32", "ensemble64"])
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -216,11 +217,64 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def ensemble_arm(args, rank, world, local):
+    """64 independent halos of uneven sizes stepped as one batch (a CUDA graph with a branch per
+    member); value = sum over members of cells x steps / time."""
+    import torch
+    import torch.distributed as dist
+    from paper_2606_25026_gb300 import build as spe_build, inputs, spe
+    spe_build.build()
+    torch.cuda.set_device(local)
+    members = inputs.ensemble()
+    stream = torch.cuda.Stream()
+    b = spe.Batch([dict(nx=m["n"], G=1.0, max_particles=len(m["mass"])) for m in members], stream=stream)
+    for g, m in zip(b.members, members):
+        g.set_ic(m["psi"])
+        if len(m["mass"]):
+            g.add_particles(m["pos"], m["vel"], m["mass"])
+    if not args.no_autotune:
+        b.autotune()
+    dts = [m["dt"] for m in members]
+    b.step(max(args.warmup, 3), dts)
+    cells = sum(m["n"] ** 3 for m in members)
+    stars = sum(len(m["mass"]) for m in members)
+    l0 = b.launch_count()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.step(args.steps, dts)
+    ev1.record(stream)
+    ev1.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    bytes_step = sum((148.0 if len(m["mass"]) else 112.0) * m["n"] ** 3 for m in members)
+    peak, kind = measured_peak()
+    ach = bytes_step * args.steps / (ms * 1e-3) / 1e9
+    line = {"metric": "grid_cell_steps_per_s", "value": world * cells * args.steps / (ms * 1e-3),
+            "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "ensemble64", "members": len(members),
+                       "sizes": {str(n): sum(1 for m in members if m["n"] == n) for n in (64, 96, 128, 192)},
+                       "cells": cells, "stars": stars, "autotune": not args.no_autotune},
+            "step_roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                              "model": "148 B/cell/step with stars, 112 without, per member"},
+            "gpu_launches": int(b.launch_count() - l0), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.destroy()
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload == "ensemble64":
+        return ensemble_arm(args, rank, world, local)
 
     import torch
     import torch.distributed as dist

@@ -215,6 +215,30 @@ SPE_API int spe_profile_read(spe_grid *g, const char **names, unsigned long long
 SPE_API int spe_field_energy_noalloc(const void *psi_c64, size_t n, double cell_volume, double kappa,
                                      double *out2, int where, void *cuda_stream);
 
+/* ---- tuning and batches (spec additions; the paper steps one grid) ----
+ * spe_autotune: time 16- and 32-column tiles of the strided (y, z) passes on a
+ * scratch copy of the field's size (allocated and freed inside the call) and
+ * keep the faster per axis; choices are cached per (axis, length, nx) for the
+ * process.  tiles_out (optional): the y and z widths chosen. */
+SPE_API int spe_autotune(spe_grid *g, int *tiles_out);
+
+/* A batch of independent grids (sizes, parameters and particle counts may
+ * all differ), stepped together: each member runs on its own stream and the
+ * members' full steps are the parallel branches of one CUDA graph replayed on
+ * the batch stream cfgs[0].cuda_stream.  Members allocate their own
+ * workspaces; use spe_batch_grid to reach a member for spe_set_ic,
+ * spe_add_particles, spe_get_psi, spe_energy, ... (not spe_destroy). */
+typedef struct spe_batch spe_batch;
+SPE_API int spe_batch_create(const spe_config *cfgs, int count, spe_batch **out);
+SPE_API int spe_batch_grid(spe_batch *b, int index, spe_grid **out);
+/* spe_autotune for every member */
+SPE_API int spe_batch_autotune(spe_batch *b);
+/* nsteps KDK steps of every member, dts[i] for member i; returns after the work completes */
+SPE_API int spe_batch_step(spe_batch *b, int nsteps, const double *dts);
+/* kernel launches of all members since creation (graph replays counted per node) */
+SPE_API int spe_batch_launch_count(spe_batch *b, unsigned long long *count_out);
+SPE_API int spe_batch_destroy(spe_batch *b);
+
 /* Human-readable text for a status code (static storage). */
 SPE_API const char *spe_strerror(int status);
 

@@ -21,7 +21,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "spe.h"
@@ -157,6 +160,16 @@ struct spe_grid {
     bool static_set;
     float *absorb;    // absorbing-layer factors per axis: nx, ny, nz floats (dt dependent)
     bool absorbing;
+    int stile[3];     // strided-pass tile width per axis (0 = default; set by the autotuner)
+    // CUDA graph of one full step (dt_k = dt), replayed on the caller's stream
+    cudaStream_t cap_st;
+    cudaGraphExec_t step_exec;
+    double graph_dt;
+    size_t graph_np;
+    bool graph_static;
+    int graph_tiles;
+    unsigned long long graph_nodes;
+    bool capturing;
     size_t np;
     double mstar;
     double quantum;
@@ -241,6 +254,7 @@ SParams base_y(spe_grid *g, float2 *data, int W, int P)
     SParams p;
     memset(&p, 0, sizeof(p));
     p.data = data;
+    p.tile = g->stile[1];
     p.S = P;
     p.bstride = (long long)P * g->n[1];
     p.W = W;
@@ -259,6 +273,7 @@ SParams base_z(spe_grid *g, float2 *data, int W, int P)
     SParams p;
     memset(&p, 0, sizeof(p));
     p.data = data;
+    p.tile = g->stile[2];
     p.S = (long long)P * g->n[1];
     p.bstride = P;
     p.W = W;
@@ -438,16 +453,14 @@ int sort_particles(spe_grid *g)
     int rc = launch(g, KIND_SORT, [&] { return launch_particle_sort(sp, g->st, &extra); });
     g->launches += extra > 0 ? extra - 1 : 0;
     if (rc) return rc;
-    float **mine[7] = {&g->px, &g->py, &g->pz, &g->vx, &g->vy, &g->vz, &g->pm};
-    for (int a = 0; a < 7; ++a) {
-        float *t = *mine[a];
-        *mine[a] = g->alt[a];
-        g->alt[a] = t;
-    }
-    unsigned int *t = g->pid;
-    g->pid = g->alt_id;
-    g->alt_id = t;
-    return SPE_OK;
+    // copy the reordered arrays back so that the star arrays never move (captured graphs hold
+    // their addresses)
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < 7 && e == cudaSuccess; ++a)
+        e = cudaMemcpyAsync(cur[a], g->alt[a], g->np * sizeof(float), cudaMemcpyDeviceToDevice, g->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->pid, g->alt_id, g->np * sizeof(unsigned int), cudaMemcpyDeviceToDevice, g->st);
+    return cuerr(e);
 }
 
 // One KDK step whose leading kick has size dtk (dt/2 for the first step of
@@ -466,7 +479,7 @@ int step_body(spe_grid *g, double dtk, double dt, bool absorb_prev)
     xp.kick_scale = (float)(dtk / g->cfg.hbar_over_m);
     if ((rc = run_x(g, KIND_X_KICK_FFT, xp))) return rc;
     if (parts) {
-        if (g->steps_done % kSortEvery == 0 && (rc = sort_particles(g))) return rc;
+        if (!g->capturing && g->steps_done % kSortEvery == 0 && (rc = sort_particles(g))) return rc;
         PParams pp = base_p(g);
         pp.flags = PK_DRIFT | (skick ? PK_KICK : 0) | (grav ? PK_DEPOSIT : 0);
         pp.kick = (float)dtk;
@@ -492,6 +505,75 @@ int step_body(spe_grid *g, double dtk, double dt, bool absorb_prev)
         if ((rc = run_s(g, KIND_Z_POISSON, g->n[2], zr))) return rc;
         yr.flags = S_INV;
         if ((rc = run_s(g, KIND_Y_RHO, g->n[1], yr))) return rc;
+    }
+    return SPE_OK;
+}
+
+bool graphs_enabled(spe_grid *g) { return !(g->cfg.flags & (SPE_NO_GRAPH | SPE_PROFILE)); }
+
+// One full step (dt_k = dt, the previous step's absorbing layer applied) as an
+// executable CUDA graph, captured on the grid's private stream and launched on
+// the caller's.  Re-captured when anything baked into the launches changes.
+int ensure_step_graph(spe_grid *g, double dt)
+{
+    const int tiles = g->stile[1] * 64 + g->stile[2];
+    if (g->step_exec && g->graph_dt == dt && g->graph_np == g->np && g->graph_static == g->static_set &&
+        g->graph_tiles == tiles)
+        return SPE_OK;
+    if (g->step_exec) {
+        cudaGraphExecDestroy(g->step_exec);
+        g->step_exec = nullptr;
+    }
+    if (!g->cap_st && cudaStreamCreateWithFlags(&g->cap_st, cudaStreamNonBlocking) != cudaSuccess) return SPE_ECUDA;
+    cudaStream_t user = g->st;
+    const unsigned long long before = g->launches;
+    g->st = g->cap_st;
+    g->capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(g->cap_st, cudaStreamCaptureModeThreadLocal);
+    int rc = (e == cudaSuccess) ? step_body(g, dt, dt, true) : SPE_ECUDA;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = (e == cudaSuccess) ? cudaStreamEndCapture(g->cap_st, &graph) : e;
+    g->st = user;
+    g->capturing = false;
+    g->graph_nodes = g->launches - before;
+    g->launches = before;
+    if (rc || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc ? rc : SPE_ECUDA;
+    }
+    e = cudaGraphInstantiate(&g->step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g->step_exec = nullptr;
+        cudaGetLastError();
+        return SPE_ECUDA;
+    }
+    g->graph_dt = dt;
+    g->graph_np = g->np;
+    g->graph_static = g->static_set;
+    g->graph_tiles = tiles;
+    return SPE_OK;
+}
+
+// Steps 2..nsteps of a call (dt_k = dt), by graph replay when allowed.
+int run_full_steps(spe_grid *g, int count, double dt)
+{
+    int rc;
+    if (count <= 0) return SPE_OK;
+    if (!graphs_enabled(g) || count < 2) {
+        for (int s = 0; s < count; ++s) {
+            if ((rc = step_body(g, dt, dt, true))) return rc;
+            g->steps_done++;
+        }
+        return SPE_OK;
+    }
+    if ((rc = ensure_step_graph(g, dt))) return rc;
+    for (int s = 0; s < count; ++s) {
+        if (g->np && g->steps_done % kSortEvery == 0 && (rc = sort_particles(g))) return rc;
+        if (cudaGraphLaunch(g->step_exec, g->st) != cudaSuccess) return SPE_ECUDA;
+        g->launches += g->graph_nodes;
+        g->steps_done++;
     }
     return SPE_OK;
 }
@@ -700,6 +782,8 @@ int spe_destroy(spe_grid *g)
         cudaEventDestroy(r.e1);
     }
     for (auto e : g->evfree) cudaEventDestroy(e);
+    if (g->step_exec) cudaGraphExecDestroy(g->step_exec);
+    if (g->cap_st) cudaStreamDestroy(g->cap_st);
     if (g->h_stage) cudaFreeHost(g->h_stage);
     if (g->owns_ws) cudaFree(g->ws);
     delete g;
@@ -787,11 +871,9 @@ int spe_step(spe_grid *g, int nsteps, double dt)
     int rc;
     if ((rc = ensure_drift_tables(g, dt))) return rc;
     if (!g->phi_valid && (rc = compute_phi(g))) return rc;
-    for (int s = 0; s < nsteps; ++s)
-    {
-        if ((rc = step_body(g, s == 0 ? 0.5 * dt : dt, dt, s > 0))) return rc;
-        g->steps_done++;
-    }
+    if ((rc = step_body(g, 0.5 * dt, dt, false))) return rc;
+    g->steps_done++;
+    if ((rc = run_full_steps(g, nsteps - 1, dt))) return rc;
     if ((rc = final_half_kick(g, 0.5 * dt))) return rc;
     if (g->cfg.flags & SPE_ASYNC) return SPE_OK;
     double mass = 0.0;
@@ -1043,6 +1125,307 @@ int spe_profile_read(spe_grid *g, const char **names, unsigned long long *launch
         ++w;
     }
     return w;
+}
+
+}  // extern "C"
+
+// ======================================================================== autotuning
+// The strided passes' tile width (16 or 32 columns per CTA) is picked per
+// (axis, transform length, row pitch) by timing a forward + inverse transform
+// of both widths on a scratch buffer the size of the field; choices are cached
+// for the process.
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned;  // (axis, n, nx) -> tile
+
+int time_tile(spe_grid *g, int axis, int tile, float2 *scratch, float *ms_out)
+{
+    SParams p = axis == 1 ? base_y(g, scratch, g->n[0], g->n[0]) : base_z(g, scratch, g->n[0], g->n[0]);
+    p.flags = S_FWD | S_INV;
+    p.tile = tile;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return SPE_ECUDA;
+    cudaError_t e = launch_spass(g->n[axis], p, g->st, nullptr);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(a, g->st);
+    for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_spass(g->n[axis], p, g->st, nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(b, g->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms_out, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return cuerr(e);
+}
+
+int autotune_grid(spe_grid *g, float2 *scratch)
+{
+    for (int axis = 1; axis <= 2; ++axis) {
+        const auto key = std::make_tuple(axis, g->n[axis], g->n[0]);
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                g->stile[axis] = it->second;
+                continue;
+            }
+        }
+        float t16 = 0.f, t32 = 0.f;
+        int rc = time_tile(g, axis, 16, scratch, &t16);
+        if (rc) return rc;
+        int best = 16;
+        if ((size_t)g->n[axis] * 32 * sizeof(float2) <= 227 * 1024) {
+            if ((rc = time_tile(g, axis, 32, scratch, &t32))) return rc;
+            if (t32 < t16) best = 32;
+        }
+        g->stile[axis] = best;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[key] = best;
+    }
+    return SPE_OK;
+}
+
+}  // namespace
+
+extern "C" int spe_autotune(spe_grid *g, int *tiles_out)
+{
+    if (!g) return SPE_EINVAL;
+    float2 *scratch = nullptr;
+    if (cudaMalloc(&scratch, g->ncells * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        return SPE_ENOMEM;
+    }
+    cudaMemsetAsync(scratch, 0, g->ncells * sizeof(float2), g->st);
+    int rc = autotune_grid(g, scratch);
+    cudaStreamSynchronize(g->st);
+    cudaFree(scratch);
+    if (!rc && tiles_out) {
+        tiles_out[0] = g->stile[1];
+        tiles_out[1] = g->stile[2];
+    }
+    return rc;
+}
+
+// ======================================================================== batches
+// Independent grids of any supported sizes stepped together: every member runs
+// on its own stream, and the members' full steps are captured as the parallel
+// branches of one CUDA graph replayed on the batch stream, so small grids
+// overlap on the GPU instead of each paying its own launch latency.
+
+struct spe_batch {
+    std::vector<spe_grid *> g;
+    std::vector<cudaStream_t> ms;
+    std::vector<cudaEvent_t> ev;
+    cudaStream_t st;
+    cudaStream_t cap;
+    cudaEvent_t fork;
+    cudaGraphExec_t exec;
+    std::vector<double> key_dt;
+    std::vector<size_t> key_np;
+    std::vector<int> key_tiles;
+    std::vector<unsigned long long> nodes;  // kernel launches per member in one captured step
+};
+
+namespace {
+
+// every member stream waits for the batch stream
+int batch_fork(spe_batch *b)
+{
+    if (cudaEventRecord(b->fork, b->st) != cudaSuccess) return SPE_ECUDA;
+    for (auto s : b->ms)
+        if (cudaStreamWaitEvent(s, b->fork, 0) != cudaSuccess) return SPE_ECUDA;
+    return SPE_OK;
+}
+
+// the batch stream waits for every member stream
+int batch_join(spe_batch *b)
+{
+    for (size_t i = 0; i < b->ms.size(); ++i) {
+        if (cudaEventRecord(b->ev[i], b->ms[i]) != cudaSuccess) return SPE_ECUDA;
+        if (cudaStreamWaitEvent(b->st, b->ev[i], 0) != cudaSuccess) return SPE_ECUDA;
+    }
+    return SPE_OK;
+}
+
+int batch_graph(spe_batch *b, const double *dts)
+{
+    const size_t n = b->g.size();
+    bool same = b->exec && b->key_dt.size() == n;
+    for (size_t i = 0; same && i < n; ++i)
+        same = b->key_dt[i] == dts[i] && b->key_np[i] == b->g[i]->np &&
+               b->key_tiles[i] == b->g[i]->stile[1] * 64 + b->g[i]->stile[2] && !b->g[i]->static_set;
+    if (same) return SPE_OK;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    std::vector<unsigned long long> before(n);
+    for (size_t i = 0; i < n; ++i) before[i] = b->g[i]->launches;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    int rc = SPE_OK;
+    if (e == cudaSuccess) {
+        e = cudaEventRecord(b->fork, b->cap);
+        for (size_t i = 0; i < n && e == cudaSuccess && !rc; ++i) {
+            spe_grid *g = b->g[i];
+            e = cudaStreamWaitEvent(b->ms[i], b->fork, 0);
+            g->capturing = true;
+            if (e == cudaSuccess) rc = step_body(g, dts[i], dts[i], true);
+            g->capturing = false;
+            if (e == cudaSuccess && !rc) e = cudaEventRecord(b->ev[i], b->ms[i]);
+            if (e == cudaSuccess && !rc) e = cudaStreamWaitEvent(b->cap, b->ev[i], 0);
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+    b->nodes.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        b->nodes[i] = b->g[i]->launches - before[i];  // captured, not run: counted per replay instead
+        b->g[i]->launches = before[i];
+    }
+    if (rc || e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc ? rc : SPE_ECUDA;
+    }
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        cudaGetLastError();
+        return SPE_ECUDA;
+    }
+    b->key_dt.assign(dts, dts + n);
+    b->key_np.resize(n);
+    b->key_tiles.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        b->key_np[i] = b->g[i]->np;
+        b->key_tiles[i] = b->g[i]->stile[1] * 64 + b->g[i]->stile[2];
+    }
+    return SPE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spe_batch_destroy(spe_batch *b)
+{
+    if (!b) return SPE_EINVAL;
+    cudaStreamSynchronize(b->st);
+    for (auto g : b->g) spe_destroy(g);
+    for (auto s : b->ms) cudaStreamDestroy(s);
+    for (auto e : b->ev) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return SPE_OK;
+}
+
+int spe_batch_create(const spe_config *cfgs, int count, spe_batch **out)
+{
+    if (!cfgs || count <= 0 || !out) return SPE_EINVAL;
+    *out = nullptr;
+    spe_batch *b = new (std::nothrow) spe_batch();
+    if (!b) return SPE_ENOMEM;
+    b->st = (cudaStream_t)cfgs[0].cuda_stream;
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        spe_batch_destroy(b);
+        return SPE_ECUDA;
+    }
+    for (int i = 0; i < count; ++i) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            spe_batch_destroy(b);
+            return SPE_ECUDA;
+        }
+        b->ms.push_back(s);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            spe_batch_destroy(b);
+            return SPE_ECUDA;
+        }
+        b->ev.push_back(e);
+        spe_config c = cfgs[i];
+        c.cuda_stream = s;
+        c.flags = (c.flags | SPE_NO_GRAPH) & ~SPE_PROFILE;
+        spe_grid *g = nullptr;
+        int rc = spe_create_grid(&c, nullptr, 0, &g);
+        if (rc) {
+            spe_batch_destroy(b);
+            return rc;
+        }
+        b->g.push_back(g);
+    }
+    *out = b;
+    return SPE_OK;
+}
+
+int spe_batch_grid(spe_batch *b, int i, spe_grid **out)
+{
+    if (!b || !out || i < 0 || i >= (int)b->g.size()) return SPE_EINVAL;
+    *out = b->g[i];
+    return SPE_OK;
+}
+
+int spe_batch_autotune(spe_batch *b)
+{
+    if (!b) return SPE_EINVAL;
+    for (auto g : b->g) {
+        int rc = spe_autotune(g, nullptr);
+        if (rc) return rc;
+    }
+    return SPE_OK;
+}
+
+int spe_batch_step(spe_batch *b, int nsteps, const double *dts)
+{
+    if (!b || nsteps < 0 || !dts) return SPE_EINVAL;
+    if (nsteps == 0) return SPE_OK;
+    const size_t n = b->g.size();
+    int rc;
+    for (size_t i = 0; i < n; ++i) {
+        spe_grid *g = b->g[i];
+        if (!isfinite(dts[i])) return SPE_EINVAL;
+        if (!(g->cfg.flags & SPE_NO_CFL_CHECK)) {
+            double dx = fmin(g->dx[0], fmin(g->dx[1], g->dx[2]));
+            if (fabs(dts[i]) > 0.5 * 4.0 / (3.0 * kPi) * dx * dx / g->cfg.hbar_over_m * (1.0 + 1e-12)) return SPE_ECFL;
+        }
+    }
+    if ((rc = batch_fork(b))) return rc;
+    for (size_t i = 0; i < n; ++i) {
+        spe_grid *g = b->g[i];
+        if ((rc = ensure_drift_tables(g, dts[i]))) return rc;
+        if (!g->phi_valid && (rc = compute_phi(g))) return rc;
+        if ((rc = step_body(g, 0.5 * dts[i], dts[i], false))) return rc;
+        g->steps_done++;
+    }
+    if ((rc = batch_join(b))) return rc;
+    if (nsteps > 1) {
+        if ((rc = batch_graph(b, dts))) return rc;
+        for (int s = 1; s < nsteps; ++s)
+            if (cudaGraphLaunch(b->exec, b->st) != cudaSuccess) return SPE_ECUDA;
+        for (size_t i = 0; i < n; ++i) {
+            b->g[i]->steps_done += nsteps - 1;
+            b->g[i]->launches += (unsigned long long)(nsteps - 1) * b->nodes[i];
+        }
+        if ((rc = batch_fork(b))) return rc;
+    }
+    for (size_t i = 0; i < n; ++i)
+        if ((rc = final_half_kick(b->g[i], 0.5 * dts[i]))) return rc;
+    if ((rc = batch_join(b))) return rc;
+    if (cudaStreamSynchronize(b->st) != cudaSuccess) return SPE_ECUDA;
+    return SPE_OK;
+}
+
+int spe_batch_launch_count(spe_batch *b, unsigned long long *count_out)
+{
+    if (!b || !count_out) return SPE_EINVAL;
+    unsigned long long c = 0;
+    for (auto g : b->g) c += g->launches;
+    *count_out = c;
+    return SPE_OK;
 }
 
 }  // extern "C"

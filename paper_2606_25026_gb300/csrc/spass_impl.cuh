@@ -1,0 +1,141 @@
+// Strided passes: transforms along y or z, where consecutive points of a
+// line are S complex values apart and neighbouring lines (columns) are
+// adjacent in memory.
+//
+// One CTA owns a tile of T adjacent columns x N points (T = 32 for N < 256,
+// 16 from 256 up), so every row of the tile is one coalesced 128/256-byte
+// segment.  Loads are asynchronous 16-byte copies straight into shared memory
+// (every load of the tile in flight at once); stores are float4.  The tile lives in
+// shared memory element-major (tile[n * T + t]) with lanes over t: the FFT
+// stages are then bank-conflict free without padding.
+//
+// Flags select forward transform, a pointwise multiply in k space, and the
+// inverse transform, all on the same tile; with a multiply, the last forward
+// stage, the multiply and the first inverse stage run in registers:
+//   drift   (S_FWD | S_DRIFT | S_INV on the z axis of psi):
+//       psi_hat *= exp(-i eta k^2 dt / 2) / (nx ny nz) = D_xy(kx, ky) E_z(kz),
+//       both factors built in FP64 on the host and applied as (hi + lo) float
+//       pairs with compensated products, so that the per-mode factor carries
+//       no fixed FP32 rounding that would repeat every step
+//       [Sec. 3.1 step (b), Algorithm 1 "kinetic drift in Fourier space"];
+//   Poisson (S_FWD | S_POISSON | S_INV on the z axis of the half spectrum):
+//       rho_hat *= -4 pi G / (k^2 nx ny nz), zero at k = 0
+//       [Sec. 3.1 step (c), Sec. 3.2.1: zero mode removed].
+#pragma once
+#include "fft_tile.cuh"
+#include "reduce.cuh"
+#include "spe_internal.cuh"
+
+namespace spe {
+
+template <class L> struct MaxRadix;
+template <int R> struct MaxRadix<RList<R>> { static constexpr int value = R; };
+template <int R0, int R1, int... Rs> struct MaxRadix<RList<R0, R1, Rs...>> {
+    static constexpr int rest = MaxRadix<RList<R1, Rs...>>::value;
+    static constexpr int value = R0 > rest ? R0 : rest;
+};
+
+// Tile width (columns per CTA): 32 below N = 256 and 16 from there by default;
+// the other width is the autotuner's alternative (SParams::tile).
+template <int N> constexpr int default_tile() { return N >= 256 ? 16 : 32; }
+
+template <int N, int TW> struct SCfg {
+    static constexpr int T = TW;
+    static constexpr int TP = T;
+    static constexpr int W = N * T / MaxRadix<typename Plan<N>::type>::value;  // butterflies per stage
+    static constexpr int NT = W >= 512 ? 512 : (W >= 256 ? 256 : (W >= 128 ? 128 : 64));
+    static constexpr size_t smem = sizeof(float2) * N * TP;
+};
+
+struct DriftOp {
+    const float4 *colfac, *ez;
+    __device__ __forceinline__ float2 operator()(float2 v, int n, int t) const
+    {
+        const float4 d = colfac[t];
+        const float4 e = __ldg(&ez[n]);
+        v = cmul_comp(v, make_float2(d.x, d.y), make_float2(d.z, d.w));
+        return cmul_comp(v, make_float2(e.x, e.y), make_float2(e.z, e.w));
+    }
+};
+
+struct PoissonOp {
+    const float *colk2, *linek2;
+    float scale;  // -4 pi G / (nx ny nz)
+    __device__ __forceinline__ float2 operator()(float2 v, int n, int t) const
+    {
+        const float k2 = colk2[t] + __ldg(&linek2[n]);
+        return cscale(v, (k2 > 0.f) ? scale / k2 : 0.f);
+    }
+};
+
+template <int N, int TW>
+__global__ void __launch_bounds__(SCfg<N, TW>::NT) spass_kernel(SParams p)
+{
+    constexpr int T = SCfg<N, TW>::T, TP = SCfg<N, TW>::TP, NT = SCfg<N, TW>::NT, HT = T / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+    __shared__ float4 colfac[T];
+    __shared__ float colk2[T];
+    const int c0 = blockIdx.x * T;
+    const int b = blockIdx.y;
+    const int tid = threadIdx.x;
+    const int flags = p.flags;
+    float2 *base = p.data + (size_t)b * p.bstride + c0;
+
+    if (tid < T) {
+        const int c = c0 + tid;
+        if (flags & S_DRIFT)
+            colfac[tid] = (c < p.W) ? __ldg(&p.dxy[(size_t)b * p.dxy_pitch + c]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (flags & S_POISSON) colk2[tid] = (c < p.W) ? __ldg(&p.colk2[c]) + __ldg(&p.batchk2[b]) : 0.f;
+    }
+
+    for (int idx = tid; idx < N * HT; idx += NT) {
+        const int n = idx / HT, q = idx % HT;
+        if (c0 + 2 * q < p.W) cp_async16(&tile[n * TP + 2 * q], base + (size_t)n * p.S + 2 * q);
+        else *reinterpret_cast<float4 *>(&tile[n * TP + 2 * q]) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if ((flags & (S_FWD | S_INV)) == (S_FWD | S_INV) && (flags & (S_DRIFT | S_POISSON))) {
+        if (flags & S_DRIFT) tile_fft_fwd_op_inv<N, T, TP, NT>(tile, p.tw, DriftOp{colfac, p.ez});
+        else tile_fft_fwd_op_inv<N, T, TP, NT>(tile, p.tw, PoissonOp{colk2, p.linek2, p.poisson * p.norm});
+    } else {
+        if (flags & S_FWD) tile_fft<N, T, TP, NT, -1>(tile, p.tw);
+        if (flags & S_INV) tile_fft<N, T, TP, NT, +1>(tile, p.tw);
+    }
+
+    if (flags & S_KIN) {
+        double acc = 0.0;
+        for (int idx = tid; idx < N * T; idx += NT) {
+            const int n = idx / T, t = idx % T;
+            if (c0 + t < p.W) {
+                const float2 v = tile[n * TP + t];
+                acc += (double)(__ldg(&p.linek2[n]) * (v.x * v.x + v.y * v.y));
+            }
+        }
+        double r[1] = {acc};
+        grid_reduce<1, NT>(r, 0, p.partials, p.counter, p.result);
+        return;
+    }
+
+    for (int idx = tid; idx < N * HT; idx += NT) {
+        const int n = idx / HT, q = idx % HT;
+        if (c0 + 2 * q < p.W)
+            *reinterpret_cast<float4 *>(base + (size_t)n * p.S + 2 * q) =
+                *reinterpret_cast<const float4 *>(&tile[n * TP + 2 * q]);
+    }
+}
+
+// widths that fit in shared memory for length N
+template <int N> constexpr bool tile_fits(int tw) { return (size_t)N * tw * sizeof(float2) <= 227 * 1024; }
+
+template <int N, int TW>
+static cudaError_t launch_s_nt(const SParams &p, cudaStream_t st, int *blocks_out)
+{
+    dim3 grid((p.W + TW - 1) / TW, p.batches);
+    if (blocks_out) *blocks_out = grid.x * grid.y;
+    spass_kernel<N, TW><<<grid, SCfg<N, TW>::NT, SCfg<N, TW>::smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace spe

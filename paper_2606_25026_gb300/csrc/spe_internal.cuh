@@ -80,6 +80,7 @@ struct SParams {
     double *partials;
     unsigned int *counter;
     double *result;
+    int tile;             // columns per CTA: 16 or 32 (0 = the per-length default)
     int flags;
 };
 

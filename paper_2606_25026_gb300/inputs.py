@@ -236,3 +236,25 @@ def make_workload(name, seed_offset=0, n=None, n_star=None):
         mass = np.zeros(0)
     dt = w["dt"] if w["dt"] is not None else kinetic_dt(N)
     return psi, pos, vel, mass, dt, w["steps"]
+
+
+def ensemble(count=64, sizes=(64, 96, 128, 192), rc_range=(0.03, 0.08), max_stars=100_000, seed=1239):
+    """Independent halos of uneven sizes: per member a seeded grid size from ``sizes``, soliton core
+    radius r_c uniform in ``rc_range`` (units of L), a star count uniform in [0, max_stars] (Plummer,
+    5% of the mass when present), the soliton + granular halo field, and the kinetic CFL dt of its
+    grid.  Returns a list of dicts (n, psi, pos, vel, mass, dt, r_c)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        rc = float(rng.uniform(*rc_range))
+        nstar = int(rng.integers(0, max_stars + 1))
+        psi_mass = 0.95 if nstar else 1.0
+        psi = soliton_halo(n, r_c=rc, psi_mass=psi_mass, seed=seed * 1000 + i)
+        if nstar:
+            pos, vel, mass = plummer(nstar, total_mass=1.0 - psi_mass, seed=seed * 1000 + 500 + i)
+        else:
+            pos = vel = np.zeros((0, 3))
+            mass = np.zeros(0)
+        out.append(dict(n=n, psi=psi, pos=pos, vel=vel, mass=mass, dt=kinetic_dt(n), r_c=rc))
+    return out

@@ -32,7 +32,8 @@ EXPORTED = (
     "spe_clear_particles", "spe_step", "spe_suggest_dt", "spe_density", "spe_potential", "spe_energy",
     "spe_last_mass", "spe_get_psi", "spe_get_particles", "spe_particle_count", "spe_sync",
     "spe_launch_count", "spe_profile_read", "spe_strerror", "spe_field_energy_noalloc",
-    "spe_set_static_potential", "spe_virial",
+    "spe_set_static_potential", "spe_virial", "spe_autotune", "spe_batch_create", "spe_batch_grid",
+    "spe_batch_autotune", "spe_batch_step", "spe_batch_launch_count", "spe_batch_destroy",
 )
 
 
@@ -98,6 +99,13 @@ def load_library(path: str = LIB_PATH):
         "spe_field_energy_noalloc": (I, [P, S, D, D, ctypes.POINTER(D), I, P]),
         "spe_set_static_potential": (I, [P, fp, I]),
         "spe_virial": (I, [P, ctypes.POINTER(spe_virial_t)]),
+        "spe_autotune": (I, [P, ctypes.POINTER(I)]),
+        "spe_batch_create": (I, [ctypes.POINTER(spe_config), I, ctypes.POINTER(P)]),
+        "spe_batch_grid": (I, [P, I, ctypes.POINTER(P)]),
+        "spe_batch_autotune": (I, [P]),
+        "spe_batch_step": (I, [P, I, ctypes.POINTER(D)]),
+        "spe_batch_launch_count": (I, [P, ctypes.POINTER(ctypes.c_ulonglong)]),
+        "spe_batch_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -166,6 +174,9 @@ class Grid:
 
     # -- lifetime
     def destroy(self):
+        if getattr(self, "_batch_member", False):
+            self._h = None      # the batch owns its members
+            return
         if getattr(self, "_h", None):
             self._lib.spe_destroy(self._h)
             self._h = None
@@ -261,6 +272,12 @@ class Grid:
         ptr, where, keep = _ptr_where(phi_b)
         _check(self._lib.spe_set_static_potential(self._h, ctypes.c_void_p(ptr), where), "spe_set_static_potential")
 
+    def autotune(self):
+        """Pick the strided passes' tile widths by timing (see spe_autotune); returns (y, z) widths."""
+        out = (ctypes.c_int * 2)()
+        _check(self._lib.spe_autotune(self._h, out), "spe_autotune")
+        return out[0], out[1]
+
     def virial(self) -> dict:
         v = spe_virial_t()
         _check(self._lib.spe_virial(self._h, ctypes.byref(v)), "spe_virial")
@@ -319,3 +336,72 @@ def field_energy_noalloc(psi, cell_volume, kappa=0.0, stream=None):
                                         float(kappa), out, SPE_HOST, ctypes.c_void_p(st)),
            "spe_field_energy_noalloc")
     return out[0], out[1]
+
+
+class Batch:
+    """Independent grids stepped together (spe_batch_*).  ``configs``: list of dicts with the
+    Grid keyword arguments nx, ny, nz, L, hbar_over_m, G, kappa, max_particles, flags,
+    absorb_alpha, absorb_nb.  ``members[i]`` behaves like a Grid (set_ic, add_particles, get_psi,
+    energy, ...) but belongs to the batch."""
+
+    def __init__(self, configs, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libspe needs a CUDA device; there is no CPU fallback")
+        self._lib = load_library()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        n = len(configs)
+        arr = (spe_config * n)()
+        shapes = []
+        for i, c in enumerate(configs):
+            nx = c["nx"]
+            ny = c.get("ny", nx)
+            nz = c.get("nz", nx)
+            L = c.get("L", 1.0)
+            if np.isscalar(L):
+                L = (float(L),) * 3
+            arr[i] = spe_config(nx, ny, nz, *(float(v) for v in L), float(c.get("hbar_over_m", 1.0)),
+                                float(c.get("G", 1.0)), float(c.get("kappa", 0.0)), int(c.get("max_particles", 0)),
+                                int(c.get("flags", 0)), ctypes.c_void_p(self.stream.cuda_stream),
+                                float(c.get("absorb_alpha", 0.0)), int(c.get("absorb_nb", 0)))
+            shapes.append((nz, ny, nx))
+        h = ctypes.c_void_p()
+        _check(self._lib.spe_batch_create(arr, n, ctypes.byref(h)), "spe_batch_create")
+        self._h = h
+        self.members = []
+        for i in range(n):
+            gh = ctypes.c_void_p()
+            _check(self._lib.spe_batch_grid(self._h, i, ctypes.byref(gh)), "spe_batch_grid")
+            m = Grid.__new__(Grid)
+            m._lib, m._h, m._batch_member = self._lib, gh, True
+            m.shape = shapes[i]
+            m.ncells = shapes[i][0] * shapes[i][1] * shapes[i][2]
+            m.workspace = None
+            m.stream = self.stream
+            self.members.append(m)
+
+    def autotune(self):
+        _check(self._lib.spe_batch_autotune(self._h), "spe_batch_autotune")
+
+    def step(self, nsteps, dts):
+        d = (ctypes.c_double * len(self.members))(*[float(v) for v in dts])
+        _check(self._lib.spe_batch_step(self._h, int(nsteps), d), "spe_batch_step")
+
+    def launch_count(self) -> int:
+        out = ctypes.c_ulonglong()
+        _check(self._lib.spe_batch_launch_count(self._h, ctypes.byref(out)), "spe_batch_launch_count")
+        return out.value
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            for m in self.members:
+                m._h = None
+            self._lib.spe_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
