@@ -69,6 +69,8 @@ extern "C" {
 #define SPE_PROFILE       (1 << 3)  /* time every kernel launch with CUDA events (spe_profile_read) */
 #define SPE_NO_GRAPH      (1 << 4)  /* launch the per-step kernels directly, never through a CUDA graph */
 #define SPE_STATIC_POTENTIAL (1 << 5) /* reserve a static external potential (spe_set_static_potential) */
+#define SPE_PREC_SPLIT16  (1 << 6)  /* axes of 256 or 512 points: radix-16 DFT stages on the tensor cores,
+                                       split FP16 (hi + lo) operands, FP32 accumulation */
 
 typedef struct spe_grid spe_grid;   /* opaque */
 

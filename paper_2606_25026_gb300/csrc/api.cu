@@ -27,6 +27,8 @@
 #include <tuple>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "spe.h"
 #include "spe_internal.cuh"
 
@@ -88,7 +90,7 @@ struct ProfRec {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t psi, phik, phi, phib, dep, part, bins, tw, k2, drift, absorb, partials, counter, diag, total;
+    size_t psi, phik, phi, phib, dep, part, bins, tw, k2, drift, absorb, tcw, partials, counter, diag, status, total;
 };
 
 int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
@@ -116,9 +118,11 @@ int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
     L->k2 = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float));
     L->drift = off;    off = align256(off + ((size_t)c->nx * c->ny + c->nz) * sizeof(float4));
     L->absorb = off;   off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float));
+    L->tcw = off;      off = align256(off + 4 * 1024 * sizeof(uint16_t));
     L->partials = off; off = align256(off + (size_t)kMaxPartials * 5 * sizeof(double));
     L->counter = off;  off = align256(off + 256);
     L->diag = off;     off = align256(off + 64 * sizeof(double));
+    L->status = off;   off = align256(off + sizeof(int));
     L->total = off;
     *W = w;
     *P = p;
@@ -161,6 +165,9 @@ struct spe_grid {
     float *absorb;    // absorbing-layer factors per axis: nx, ny, nz floats (dt dependent)
     bool absorbing;
     int stile[3];     // strided-pass tile width per axis (0 = default; set by the autotuner)
+    int tc;           // SPE_PREC_SPLIT16
+    __half *tcw;      // 32 x 32 DFT operands for the tensor stages: [dir][hi, lo][core layout]
+    int *status;      // device status word
     // CUDA graph of one full step (dt_k = dt), replayed on the caller's stream
     cudaStream_t cap_st;
     cudaGraphExec_t step_exec;
@@ -245,6 +252,9 @@ XParams base_x(spe_grid *g)
     p.absorb_z = g->absorb + g->n[0] + g->n[1];
     p.phib = g->phib;
     p.ny = g->n[1];
+    p.tc = g->tc;
+    p.tcw = g->tcw;
+    p.status = g->status;
     return p;
 }
 
@@ -255,6 +265,9 @@ SParams base_y(spe_grid *g, float2 *data, int W, int P)
     memset(&p, 0, sizeof(p));
     p.data = data;
     p.tile = g->stile[1];
+    p.tc = g->tc;
+    p.tcw = g->tcw;
+    p.status = g->status;
     p.S = P;
     p.bstride = (long long)P * g->n[1];
     p.W = W;
@@ -274,6 +287,9 @@ SParams base_z(spe_grid *g, float2 *data, int W, int P)
     memset(&p, 0, sizeof(p));
     p.data = data;
     p.tile = g->stile[2];
+    p.tc = g->tc;
+    p.tcw = g->tcw;
+    p.status = g->status;
     p.S = (long long)P * g->n[1];
     p.bstride = P;
     p.W = W;
@@ -735,6 +751,9 @@ int spe_create_grid(const spe_config *cfg, void *workspace, size_t workspace_byt
     g->k2[1] = g->k2[0] + cfg->nx;
     g->k2[2] = g->k2[1] + cfg->ny;
     g->phib = (cfg->flags & SPE_STATIC_POTENTIAL) ? (float *)(b + L.phib) : nullptr;
+    g->tc = (cfg->flags & SPE_PREC_SPLIT16) ? 1 : 0;
+    g->tcw = (__half *)(b + L.tcw);
+    g->status = (int *)(b + L.status);
     g->absorb = (float *)(b + L.absorb);
     g->absorbing = cfg->absorb_alpha > 0.0;
     g->dxy = (float4 *)(b + L.drift);
@@ -764,6 +783,28 @@ int spe_create_grid(const spe_config *cfg, void *workspace, size_t workspace_byt
         e = cudaMemcpyAsync(g->tw[0], tw.data(), ntot * sizeof(float4), cudaMemcpyHostToDevice, g->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->k2[0], k2.data(), ntot * sizeof(float), cudaMemcpyHostToDevice, g->st);
+    // 16-point DFT as a 32 x 32 real matrix for the tensor stages, rows = outputs [Re y, Im y],
+    // columns = inputs [Re x, Im x]; FP64 values split into fp16 hi + lo, stored in the
+    // no-swizzle K-major core-matrix layout (element (n, k) at byte
+    // (n/8)*512 + (k/8)*128 + (n%8)*16 + (k%8)*2)
+    std::vector<__half> wt(4 * 1024);
+    for (int d = 0; d < 2; ++d) {
+        const double dir = d == 0 ? -1.0 : 1.0;
+        for (int n = 0; n < 32; ++n)
+            for (int k = 0; k < 32; ++k) {
+                const double th = dir * 2.0 * kPi * (double)((n % 16) * (k % 16)) / 16.0;
+                double w;
+                if (n < 16) w = (k < 16) ? cos(th) : -sin(th);
+                else w = (k < 16) ? sin(th) : cos(th);
+                const __half hi = __float2half_rn((float)w);
+                const __half lo = __float2half_rn((float)(w - (double)__half2float(hi)));
+                const int idx = ((n >> 3) * 512 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2) / 2;
+                wt[(d * 2 + 0) * 1024 + idx] = hi;
+                wt[(d * 2 + 1) * 1024 + idx] = lo;
+            }
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->tcw, wt.data(), wt.size() * sizeof(__half), cudaMemcpyHostToDevice, g->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     if (e != cudaSuccess) {
         spe_destroy(g);
@@ -881,6 +922,16 @@ int spe_step(spe_grid *g, int nsteps, double dt)
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     if (e != cudaSuccess) return SPE_ECUDA;
     if (!isfinite(mass)) return SPE_ENONFINITE;
+    if (g->tc) {
+        int st = 0;
+        e = cudaMemcpyAsync(&st, g->status, sizeof(int), cudaMemcpyDeviceToHost, g->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+        if (e != cudaSuccess) return SPE_ECUDA;
+        if (st) {
+            cudaMemsetAsync(g->status, 0, sizeof(int), g->st);
+            return SPE_ETIMEOUT;
+        }
+    }
     return SPE_OK;
 }
 

@@ -25,6 +25,7 @@
 #include "fft_tile.cuh"
 #include "reduce.cuh"
 #include "spe_internal.cuh"
+#include "tc16.cuh"
 
 namespace spe {
 
@@ -39,12 +40,14 @@ template <int R0, int R1, int... Rs> struct MaxRadix<RList<R0, R1, Rs...>> {
 // the other width is the autotuner's alternative (SParams::tile).
 template <int N> constexpr int default_tile() { return N >= 256 ? 16 : 32; }
 
-template <int N, int TW> struct SCfg {
+template <int N, int TW, bool TC = false> struct SCfg {
     static constexpr int T = TW;
     static constexpr int TP = T;
     static constexpr int W = N * T / MaxRadix<typename Plan<N>::type>::value;  // butterflies per stage
     static constexpr int NT = W >= 512 ? 512 : (W >= 256 ? 256 : (W >= 128 ? 128 : 64));
-    static constexpr size_t smem = sizeof(float2) * N * TP;
+    static constexpr size_t base = sizeof(float2) * N * TP;
+    static constexpr size_t tc_off = (base + 127) & ~(size_t)127;
+    static constexpr size_t smem = TC ? tc_off + sizeof(TcSmem) : base;
 };
 
 struct DriftOp {
@@ -68,11 +71,16 @@ struct PoissonOp {
     }
 };
 
-template <int N, int TW>
-__global__ void __launch_bounds__(SCfg<N, TW>::NT) spass_kernel(SParams p)
+template <int N, int TW, bool TC = false>
+__global__ void __launch_bounds__(SCfg<N, TW, TC>::NT) spass_kernel(SParams p)
 {
-    constexpr int T = SCfg<N, TW>::T, TP = SCfg<N, TW>::TP, NT = SCfg<N, TW>::NT, HT = T / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int T = SCfg<N, TW, TC>::T, TP = SCfg<N, TW, TC>::TP, NT = SCfg<N, TW, TC>::NT, HT = T / 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TcSmem *tcs = nullptr;
+    if constexpr (TC) {
+        tcs = reinterpret_cast<TcSmem *>(smem_raw + SCfg<N, TW, TC>::tc_off);
+        tc_setup(*tcs, static_cast<const __half *>(p.tcw), NT);
+    }
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
     __shared__ float4 colfac[T];
     __shared__ float colk2[T];
@@ -97,8 +105,19 @@ __global__ void __launch_bounds__(SCfg<N, TW>::NT) spass_kernel(SParams p)
     cp_async_wait_all();
     __syncthreads();
     if ((flags & (S_FWD | S_INV)) == (S_FWD | S_INV) && (flags & (S_DRIFT | S_POISSON))) {
-        if (flags & S_DRIFT) tile_fft_fwd_op_inv<N, T, TP, NT>(tile, p.tw, DriftOp{colfac, p.ez});
-        else tile_fft_fwd_op_inv<N, T, TP, NT>(tile, p.tw, PoissonOp{colk2, p.linek2, p.poisson * p.norm});
+        if constexpr (TC) {
+            if (flags & S_DRIFT)
+                tile_fft_fwd_op_inv_tc<N, T, TP, NT>(tile, p.tw, DriftOp{colfac, p.ez}, *tcs, p.status);
+            else
+                tile_fft_fwd_op_inv_tc<N, T, TP, NT>(tile, p.tw, PoissonOp{colk2, p.linek2, p.poisson * p.norm},
+                                                     *tcs, p.status);
+        } else {
+            if (flags & S_DRIFT) tile_fft_fwd_op_inv<N, T, TP, NT>(tile, p.tw, DriftOp{colfac, p.ez});
+            else tile_fft_fwd_op_inv<N, T, TP, NT>(tile, p.tw, PoissonOp{colk2, p.linek2, p.poisson * p.norm});
+        }
+    } else if constexpr (TC) {
+        if (flags & S_FWD) tile_fft_tc<N, T, TP, NT, -1>(tile, p.tw, *tcs, p.status);
+        if (flags & S_INV) tile_fft_tc<N, T, TP, NT, +1>(tile, p.tw, *tcs, p.status);
     } else {
         if (flags & S_FWD) tile_fft<N, T, TP, NT, -1>(tile, p.tw);
         if (flags & S_INV) tile_fft<N, T, TP, NT, +1>(tile, p.tw);
@@ -115,6 +134,7 @@ __global__ void __launch_bounds__(SCfg<N, TW>::NT) spass_kernel(SParams p)
         }
         double r[1] = {acc};
         grid_reduce<1, NT>(r, 0, p.partials, p.counter, p.result);
+        if constexpr (TC) tc_teardown(*tcs);
         return;
     }
 
@@ -124,17 +144,18 @@ __global__ void __launch_bounds__(SCfg<N, TW>::NT) spass_kernel(SParams p)
             *reinterpret_cast<float4 *>(base + (size_t)n * p.S + 2 * q) =
                 *reinterpret_cast<const float4 *>(&tile[n * TP + 2 * q]);
     }
+    if constexpr (TC) tc_teardown(*tcs);
 }
 
 // widths that fit in shared memory for length N
 template <int N> constexpr bool tile_fits(int tw) { return (size_t)N * tw * sizeof(float2) <= 227 * 1024; }
 
-template <int N, int TW>
+template <int N, int TW, bool TC = false>
 static cudaError_t launch_s_nt(const SParams &p, cudaStream_t st, int *blocks_out)
 {
     dim3 grid((p.W + TW - 1) / TW, p.batches);
     if (blocks_out) *blocks_out = grid.x * grid.y;
-    spass_kernel<N, TW><<<grid, SCfg<N, TW>::NT, SCfg<N, TW>::smem, st>>>(p);
+    spass_kernel<N, TW, TC><<<grid, SCfg<N, TW, TC>::NT, SCfg<N, TW, TC>::smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -49,6 +49,8 @@ struct XParams {
     const float *absorb_x, *absorb_y, *absorb_z;  // per-axis absorbing-layer factors (X_ABSORB)
     const float *phib;        // static external potential, nodes (X_STATIC)
     int ny;                   // rows are y + ny z
+    int tc;                   // radix-16 stages on the tensor cores (split FP16), N = 256 and 512
+    const void *tcw;          // the 32 x 32 DFT operands for them (fp16 hi / lo, both directions)
     int flags;
 };
 
@@ -81,6 +83,9 @@ struct SParams {
     unsigned int *counter;
     double *result;
     int tile;             // columns per CTA: 16 or 32 (0 = the per-length default)
+    int tc;               // radix-16 stages on the tensor cores (split FP16), N = 256 and 512
+    const void *tcw;
+    int *status;          // device status word (tensor-stage timeouts)
     int flags;
 };
 

@@ -1,240 +1,22 @@
-// x-axis passes: lines along x are contiguous rows of the field.
-//
-// One CTA owns T = 16 consecutive rows.  Rows are staged in shared memory
-// element-major (tile[n * (T+1) + t], the +1 pad keeps both the row-wise
-// global<->shared copies and the FFT stages free of bank conflicts).  What a
-// launch does is selected by XParams::flags; the step uses two combinations:
-//
-//   kick pass     (X_HAS_PHI | X_KICK | X_FFT [| X_WRITE_PHI]):
-//       Phi rows rebuilt from the x half spectrum (inverse real transform,
-//       two rows packed as one complex line), psi *= exp(-i (Phi +
-//       kappa|psi|^2) dt_k / eta)  [Sec. 3.1 steps (a)/(d), Algorithm 1],
-//       then the forward x transform of psi  [step (b), first axis].
-//   density pass  (X_IFFT | X_MASS | X_R2C [| X_DEP]):
-//       inverse x transform of psi  [step (b), last axis], rho = |psi|^2 +
-//       rho_*  [step (c)], the mass reduced on the fly, and the forward real
-//       x transform of rho into the half spectrum  [step (c), first axis].
-#include "fft_tile.cuh"
-#include "reduce.cuh"
-#include "spe_internal.cuh"
+// x passes (FP32 instances); the kernel is in xpass_impl.cuh.
+#include "xpass_impl.cuh"
 
 namespace spe {
-
-template <int N> struct XCfg {
-    static constexpr int T = 16;
-    static constexpr int TP = T + 1;
-    static constexpr int NT = (N * T / 8 >= 256) ? 256 : ((N * T / 8 >= 128) ? 128 : 64);
-    // tile + aux; aux holds T real rows, or T half-spectrum rows of N/2 + 1 complex while staging
-    static constexpr size_t smem = sizeof(float2) * N * TP + sizeof(float2) * T * (N / 2 + 1);
-};
-
-template <int N>
-__global__ void __launch_bounds__(XCfg<N>::NT) xpass_kernel(XParams p)
-{
-    constexpr int T = XCfg<N>::T, TP = XCfg<N>::TP, NT = XCfg<N>::NT, H = N / 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
-    float *aux = reinterpret_cast<float *>(tile + N * TP);  // aux[t * N + n]: real row t
-    const int row0 = blockIdx.x * T;
-    const int tid = threadIdx.x;
-    const int flags = p.flags;
-
-    // ---- Phi rows from the half spectrum: rows (2m, 2m+1) as one complex line
-    if (flags & X_HAS_PHI) {
-        // stage the T half-spectrum rows in aux with asynchronous copies, then build the packed
-        // lines Z = A + iB (Hermitian extension of both rows) from shared memory
-        float2 *stage = reinterpret_cast<float2 *>(aux);
-        for (int idx = tid; idx < T * (H + 1); idx += NT) {
-            const int t = idx / (H + 1), k = idx % (H + 1);
-            const int row = row0 + t;
-            if (row < p.rows) cp_async8(&stage[idx], &p.phik[(size_t)row * p.P + k]);
-            else stage[idx] = make_float2(0.f, 0.f);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        for (int idx = tid; idx < (T / 2) * N; idx += NT) {
-            const int n = idx % N, m = idx / N;
-            const int kk = (n <= H) ? n : N - n;
-            float2 A = stage[(2 * m) * (H + 1) + kk], B = stage[(2 * m + 1) * (H + 1) + kk];
-            if (n > H) { A.y = -A.y; B.y = -B.y; }
-            if (n == 0 || n == H) { A.y = 0.f; B.y = 0.f; }
-            tile[n * TP + m] = make_float2(A.x - B.y, A.y + B.x);
-        }
-        __syncthreads();
-        tile_fft<N, T / 2, TP, NT, +1>(tile, p.tw);
-        for (int idx = tid; idx < (T / 2) * N; idx += NT) {
-            const int n = idx % N, m = idx / N;
-            const float2 z = tile[n * TP + m];
-            aux[(2 * m) * N + n] = z.x;
-            aux[(2 * m + 1) * N + n] = z.y;
-            const int ra = row0 + 2 * m;
-            if ((flags & X_WRITE_PHI) && ra + 1 < p.rows) {
-                float za = z.x, zb = z.y;
-                if (flags & X_STATIC) {
-                    za += __ldg(&p.phib[(size_t)ra * N + n]);
-                    zb += __ldg(&p.phib[(size_t)(ra + 1) * N + n]);
-                }
-                p.phi_out[(size_t)ra * N + n] = za;
-                p.phi_out[(size_t)(ra + 1) * N + n] = zb;
-            }
-        }
-        __syncthreads();
-    }
-
-    // ---- kick and forward x transform of psi
-    if (flags & (X_KICK | X_FFT)) {
-        const bool fft = flags & X_FFT;
-        for (int idx = tid; idx < T * N; idx += NT) {
-            const int n = idx % N, t = idx / N;
-            const int row = row0 + t;
-            if (row < p.rows) cp_async8(&tile[n * TP + t], &p.psi[(size_t)row * N + n]);
-            else tile[n * TP + t] = make_float2(0.f, 0.f);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        for (int idx = tid; idx < T * N; idx += NT) {
-            const int n = idx % N, t = idx / N;
-            const int row = row0 + t;
-            float2 v = tile[n * TP + t];
-            if (flags & X_KICK) {
-                // v * exp(-i ph) = v + v * (cos ph - 1 - i sin ph), with cos ph - 1 = -2 sin^2(ph/2):
-                // the factor's modulus error is O(ph^2 eps) instead of the O(eps) of a rounded cos ph,
-                // which would otherwise recur identically step after step while Phi changes slowly.
-                const float a2 = v.x * v.x + v.y * v.y;
-                float phi = (flags & X_HAS_PHI) ? aux[t * N + n] : 0.f;
-                if ((flags & X_STATIC) && row < p.rows) {
-                    const float pb = __ldg(&p.phib[(size_t)row * N + n]);
-                    phi += pb;
-                    if ((flags & X_WRITE_PHI) && !(flags & X_HAS_PHI)) p.phi_out[(size_t)row * N + n] = pb;
-                }
-                float sh, ch;
-                sincosf(0.5f * ((phi + p.kappa * a2) * p.kick_scale), &sh, &ch);
-                const float cm1 = -2.f * sh * sh, sn = 2.f * sh * ch;
-                v = make_float2(fmaf(v.x, cm1, fmaf(v.y, sn, v.x)), fmaf(v.y, cm1, fmaf(-v.x, sn, v.y)));
-            }
-            if ((flags & X_ABSORB) && row < p.rows) {
-                // absorbing layer of the step that just ended (Sec. 3.1, Algorithm 1): a real
-                // pointwise factor, so it commutes with the kick it is fused with
-                const float b = __ldg(&p.absorb_x[n]) * __ldg(&p.absorb_y[row % p.ny]) * __ldg(&p.absorb_z[row / p.ny]);
-                v = make_float2(v.x * b, v.y * b);
-            }
-            if (fft) tile[n * TP + t] = v;
-            else if (row < p.rows) p.psi[(size_t)row * N + n] = v;
-        }
-        if (fft) {
-            __syncthreads();
-            tile_fft<N, T, TP, NT, -1>(tile, p.tw);
-            for (int idx = tid; idx < T * N; idx += NT) {
-                const int n = idx % N, t = idx / N;
-                const int row = row0 + t;
-                if (row < p.rows) p.psi[(size_t)row * N + n] = tile[n * TP + t];
-            }
-        }
-    }
-
-    // ---- inverse x transform, density, mass, real-to-complex x transform of rho
-    if (flags & (X_R2C | X_MASS | X_IFFT)) {
-        const bool ifft = flags & X_IFFT;
-        // psi (transformed or not) streams into the tile asynchronously while the star
-        // deposit of the same rows is read, converted and cleared into aux
-        for (int idx = tid; idx < T * N; idx += NT) {
-            const int n = idx % N, t = idx / N;
-            const int row = row0 + t;
-            if (row < p.rows) cp_async8(&tile[n * TP + t], &p.psi[(size_t)row * N + n]);
-            else tile[n * TP + t] = make_float2(0.f, 0.f);
-        }
-        if (flags & X_DEP) {
-            // loads only: a zero store to an address whose load is still in flight has to wait
-            // for that load, which serialises the loop on memory latency (measured 4x slower)
-            const long long *__restrict__ dep = p.dep + (size_t)row0 * N;
-#pragma unroll 4
-            for (int idx = tid; idx < T * N; idx += NT) {
-                const int row = row0 + idx / N;
-                aux[idx] = (row < p.rows) ? (float)__ldcs(&dep[idx]) * p.dep_scale : 0.f;
-            }
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        if (flags & X_DEP) {
-            // every deposit value of the tile has been consumed by now: clear for the next step
-            long long *__restrict__ dep = p.dep + (size_t)row0 * N;
-            for (int idx = tid; idx < T * N; idx += NT)
-                if (row0 + idx / N < p.rows) __stcs(&dep[idx], 0ll);
-        }
-        if (ifft) tile_fft<N, T, TP, NT, +1>(tile, p.tw);
-        float msum = 0.f;
-        for (int idx = tid; idx < T * N; idx += NT) {
-            const int n = idx % N, t = idx / N;
-            const int row = row0 + t;
-            const float2 v = tile[n * TP + t];
-            if (ifft && row < p.rows) p.psi[(size_t)row * N + n] = v;
-            float r = v.x * v.x + v.y * v.y;
-            msum += r;
-            if (flags & X_DEP) r += aux[t * N + n];
-            aux[t * N + n] = r;
-        }
-        __syncthreads();
-        if (flags & X_R2C) {
-            for (int idx = tid; idx < (T / 2) * N; idx += NT) {
-                const int n = idx % N, m = idx / N;
-                tile[n * TP + m] = make_float2(aux[(2 * m) * N + n], aux[(2 * m + 1) * N + n]);
-            }
-            __syncthreads();
-            tile_fft<N, T / 2, TP, NT, -1>(tile, p.tw);
-            // separate the two real rows: A_k = (Z_k + conj Z_{N-k}) / 2, B_k = (Z_k - conj Z_{N-k}) / (2i)
-            for (int idx = tid; idx < (T / 2) * (H + 1); idx += NT) {
-                const int k = idx % (H + 1), m = idx / (H + 1);
-                const int ra = row0 + 2 * m;
-                const float2 Z = tile[k * TP + m];
-                const float2 Zc = cconj(tile[((N - k) % N) * TP + m]);
-                const float2 A = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
-                const float2 D = csub(Z, Zc);
-                const float2 B = make_float2(0.5f * D.y, -0.5f * D.x);
-                if (ra + 1 < p.rows) {
-                    p.phik[(size_t)ra * p.P + k] = A;
-                    p.phik[(size_t)(ra + 1) * p.P + k] = B;
-                }
-            }
-        }
-        if (flags & X_MASS) {
-            double v[1] = {(double)msum};
-            grid_reduce<1, NT>(v, 0, p.partials, p.counter, p.result);
-        }
-    }
-
-    // ---- kinetic-energy diagnostic along x: sum_k kx^2 |F_x psi|^2 (no store)
-    if (flags & X_KIN) {
-        for (int idx = tid; idx < T * N; idx += NT) {
-            const int n = idx % N, t = idx / N;
-            const int row = row0 + t;
-            if (row < p.rows) cp_async8(&tile[n * TP + t], &p.psi[(size_t)row * N + n]);
-            else tile[n * TP + t] = make_float2(0.f, 0.f);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        tile_fft<N, T, TP, NT, -1>(tile, p.tw);
-        double acc = 0.0;
-        for (int idx = tid; idx < T * N; idx += NT) {
-            const int n = idx % N, t = idx / N;
-            const float2 v = tile[n * TP + t];
-            acc += (double)(__ldg(&p.k2[n]) * (v.x * v.x + v.y * v.y));
-        }
-        double v[1] = {acc};
-        grid_reduce<1, NT>(v, 0, p.partials, p.counter, p.result);
-    }
-}
 
 template <int N>
 static cudaError_t launch_x_n(const XParams &p, cudaStream_t st, int *blocks_out)
 {
     const int blocks = (p.rows + XCfg<N>::T - 1) / XCfg<N>::T;
     if (blocks_out) *blocks_out = blocks;
-    xpass_kernel<N><<<blocks, XCfg<N>::NT, XCfg<N>::smem, st>>>(p);
+    xpass_kernel<N, false><<<blocks, XCfg<N>::NT, XCfg<N>::smem, st>>>(p);
     return cudaGetLastError();
 }
 
+cudaError_t launch_xpass_tc(int nx, const XParams &p, cudaStream_t st, int *blocks_out);
+
 cudaError_t launch_xpass(int nx, const XParams &p, cudaStream_t st, int *blocks_out)
 {
+    if (p.tc && (nx == 256 || nx == 512)) return launch_xpass_tc(nx, p, st, blocks_out);
     switch (nx) {
 #define X(n) \
     case n: return launch_x_n<n>(p, st, blocks_out);
@@ -251,7 +33,7 @@ cudaError_t setup_xpass_attributes()
     cudaError_t e = cudaSuccess;
 #define X(n)                                                                                                    \
     if (e == cudaSuccess)                                                                                        \
-        e = cudaFuncSetAttribute(xpass_kernel<n>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XCfg<n>::smem);
+        e = cudaFuncSetAttribute(xpass_kernel<n, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XCfg<n>::smem);
     SPE_FOR_EACH_N(X)
 #undef X
     return e;
