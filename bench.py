@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--workload", default="halo256_stars1e6",
                     choices=["halo256_stars1e6", "halo512", "packets32", "ensemble64"])
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "split16"],
+                    help="split16: radix-16 DFT stages of 256/512-point axes on the tensor cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -249,7 +251,7 @@ def ensemble_arm(args, rank, world, local):
     ev1.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    bytes_step = sum((148.0 if len(m["mass"]) else 112.0) * m["n"] ** 3 for m in members)
+    bytes_step = sum((132.0 if len(m["mass"]) else 112.0) * m["n"] ** 3 for m in members)
     peak, kind = measured_peak()
     ach = bytes_step * args.steps / (ms * 1e-3) / 1e9
     line = {"metric": "grid_cell_steps_per_s", "value": world * cells * args.steps / (ms * 1e-3),
@@ -260,7 +262,7 @@ def ensemble_arm(args, rank, world, local):
                        "sizes": {str(n): sum(1 for m in members if m["n"] == n) for n in (64, 96, 128, 192)},
                        "cells": cells, "stars": stars, "autotune": not args.no_autotune},
             "step_roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                              "model": "148 B/cell/step with stars, 112 without, per member"},
+                              "model": "132 B/cell/step with stars, 112 without, per member"},
             "gpu_launches": int(b.launch_count() - l0), "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -301,8 +303,9 @@ def main():
             torch.cuda.synchronize()
 
     # ---------------- device-resident timed region
-    g = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, flags=spe.SPE_ASYNC | spe.SPE_PROFILE,
-                 stream=stream)
+    prec_flag = spe.SPE_PREC_SPLIT16 if args.prec == "split16" else 0
+    g = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar,
+                 flags=spe.SPE_ASYNC | spe.SPE_PROFILE | prec_flag, stream=stream)
     g.set_ic(torch.from_numpy(psi).cuda())
     if nstar:
         g.add_particles(torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda(), torch.from_numpy(mass).cuda())
@@ -338,8 +341,9 @@ def main():
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / per_launch_s / 1e9
     traffic = recorded_traffic(dom, args.workload)
-    step_bytes = sum(bpc[k] for k in ("x_kick_fwd", "y_fft_psi", "z_fft_drift", "x_inv_density_r2c")) + \
-        2 * bpc["y_fft_psi"] + (3 * 8.0)
+    # x kick pass, y fwd, z drift, y inv, x density pass, and the three half-spectrum passes
+    step_bytes = (bpc["x_kick_fwd"] + 2 * bpc["y_fft_psi"] + bpc["z_fft_drift"] + bpc["x_inv_density_r2c"] +
+                  2 * bpc["y_fft_rho"] + bpc["z_fft_poisson"])
     kernel_split = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / max(1e-9, sum(
         x[1] for x in prof.values())), 4)} for k, v in prof.items() if v[0]}
 
@@ -348,6 +352,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": [nx, ny, nz], "n_star": nstar, "dt": dt,
+                   "precision": args.prec,
                    "l2": f"working set {g.workspace.numel() / 2**20:.0f} MiB > 129 MB L2 (no flush needed)",
                    "parallelism": f"{world} independent replica(s)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -374,7 +379,7 @@ def main():
         h_mass = torch.from_numpy(mass).pin_memory()
         o_psi = torch.empty(psi.shape, dtype=torch.complex64).pin_memory()
         o_pos = np.empty((nstar, 3), np.float32)
-        ge = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, stream=stream)
+        ge = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, flags=prec_flag, stream=stream)
         ke = max(1, min(args.steps, 200))
         # warm the path once
         ge.set_ic(h_psi)
@@ -415,7 +420,7 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{nsteps} KDK steps of the {args.workload} workload ({sec:.1f} s), "
                                           "Phi(0) solve untimed"}
-        gc = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, stream=stream)
+        gc = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, flags=prec_flag, stream=stream)
         gc.set_ic(psi)
         if nstar:
             gc.add_particles(pos, vel, mass)
