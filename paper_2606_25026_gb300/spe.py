@@ -35,7 +35,16 @@ EXPORTED = (
     "spe_launch_count", "spe_profile_read", "spe_strerror", "spe_field_energy_noalloc",
     "spe_set_static_potential", "spe_virial", "spe_autotune", "spe_batch_create", "spe_batch_grid",
     "spe_batch_autotune", "spe_batch_step", "spe_batch_launch_count", "spe_batch_destroy",
+    # include/spe_fno.h
+    "spe_fno_param_count", "spe_fno_create", "spe_fno_destroy", "spe_fno_set_params", "spe_fno_get_params",
+    "spe_fno_get_grads", "spe_fno_forward", "spe_fno_backward", "spe_fno_adam", "spe_fno_launch_count",
+    "spe_surrogate_create", "spe_surrogate_destroy", "spe_surrogate_advance",
 )
+
+# include/spe_fno.h
+SPE_FNO_WIDTH, SPE_FNO_HIDDEN = 32, 64
+SPE_FNO_TRAIN = 1 << 0
+SPE_FNO_ACT_FP32 = 1 << 1
 
 
 class SpeError(RuntimeError):
@@ -61,6 +70,21 @@ class spe_virial_t(ctypes.Structure):
 class spe_energy_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("mass", "kinetic", "potential", "interaction", "star_kinetic", "total", "max_abs_phi")]
+
+
+class spe_fno_config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("layers", ctypes.c_int), ("modes", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("flags", ctypes.c_int), ("inv_A", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+
+
+class spe_judge_config(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("max_mass_drift", "max_energy_drift", "max_rel_l2")]
+
+
+class spe_judge_result(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_int), ("spot_checked", ctypes.c_int), ("used_proposal", ctypes.c_int),
+                ("mass_drift", ctypes.c_double), ("energy_drift", ctypes.c_double), ("rel_l2", ctypes.c_double)]
 
 
 _lib = None
@@ -107,6 +131,20 @@ def load_library(path: str = LIB_PATH):
         "spe_batch_step": (I, [P, I, ctypes.POINTER(D)]),
         "spe_batch_launch_count": (I, [P, ctypes.POINTER(ctypes.c_ulonglong)]),
         "spe_batch_destroy": (I, [P]),
+        "spe_fno_param_count": (I, [ctypes.POINTER(spe_fno_config), ctypes.POINTER(S)]),
+        "spe_fno_create": (I, [ctypes.POINTER(spe_fno_config), ctypes.POINTER(P)]),
+        "spe_fno_destroy": (I, [P]),
+        "spe_fno_set_params": (I, [P, fp, S, I]),
+        "spe_fno_get_params": (I, [P, fp, S, I]),
+        "spe_fno_get_grads": (I, [P, fp, S, I]),
+        "spe_fno_forward": (I, [P, P, P, P, I]),
+        "spe_fno_backward": (I, [P, P, ctypes.POINTER(D)]),
+        "spe_fno_adam": (I, [P, D, D, D, D]),
+        "spe_fno_launch_count": (I, [P, ctypes.POINTER(ctypes.c_ulonglong), I]),
+        "spe_surrogate_create": (I, [ctypes.POINTER(spe_config), P, ctypes.POINTER(spe_judge_config),
+                                     ctypes.POINTER(P)]),
+        "spe_surrogate_destroy": (I, [P]),
+        "spe_surrogate_advance": (I, [P, P, I, D, I, ctypes.POINTER(spe_judge_result)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -406,3 +444,130 @@ class Batch:
         except Exception:
             pass
 
+
+
+class Fno:
+    """The FNO surrogate network (include/spe_fno.h) on the current CUDA device: create, set/get
+    the flat parameter vector, forward, backward, Adam.  Fields are complex64 torch tensors on the
+    device, shaped (batch, n, n, n) or (n, n, n)."""
+
+    def __init__(self, n=64, layers=4, modes=16, max_batch=1, train=False, act_fp32=False, inv_A=1.0,
+                 sigma=1.0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libspe needs a CUDA device; there is no CPU fallback")
+        self._lib = load_library()
+        self.n, self.layers, self.modes, self.max_batch = int(n), int(layers), int(modes), int(max_batch)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        flags = (SPE_FNO_TRAIN if train else 0) | (SPE_FNO_ACT_FP32 if act_fp32 else 0)
+        self.cfg = spe_fno_config(self.n, self.layers, self.modes, self.max_batch, flags, float(inv_A),
+                                  float(sigma), ctypes.c_void_p(self.stream.cuda_stream))
+        cnt = ctypes.c_size_t()
+        _check(self._lib.spe_fno_param_count(ctypes.byref(self.cfg), ctypes.byref(cnt)), "spe_fno_param_count")
+        self.param_count = cnt.value
+        h = ctypes.c_void_p()
+        _check(self._lib.spe_fno_create(ctypes.byref(self.cfg), ctypes.byref(h)), "spe_fno_create")
+        self._h = h
+        self._keep = None
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            self._lib.spe_fno_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        import torch
+        if isinstance(params, torch.Tensor):
+            params = params.contiguous().float()
+            ptr, where, keep = _ptr_where(params)
+        else:
+            ptr, where, keep = _ptr_where(np.ascontiguousarray(params, dtype=np.float32))
+        _check(self._lib.spe_fno_set_params(self._h, ctypes.c_void_p(ptr), self.param_count, where),
+               "spe_fno_set_params")
+        if where == SPE_DEVICE:
+            self.stream.synchronize()
+
+    def _vec_out(self, fn, what):
+        out = np.empty(self.param_count, dtype=np.float32)
+        _check(fn(self._h, ctypes.c_void_p(out.ctypes.data), self.param_count, SPE_HOST), what)
+        return out
+
+    def get_params(self) -> np.ndarray:
+        return self._vec_out(self._lib.spe_fno_get_params, "spe_fno_get_params")
+
+    def grads(self) -> np.ndarray:
+        return self._vec_out(self._lib.spe_fno_get_grads, "spe_fno_get_grads")
+
+    @staticmethod
+    def _dev(t, what):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()):
+            raise TypeError(f"{what} must be a contiguous complex64 CUDA tensor")
+        return t
+
+    def forward(self, psi, psi_b, out=None):
+        """Proposal for (psi, psi_b); in training mode keeps the activations for backward()."""
+        import torch
+        psi, psi_b = self._dev(psi, "psi"), self._dev(psi_b, "psi_b")
+        batch = psi.shape[0] if psi.dim() == 4 else 1
+        if out is None:
+            out = torch.empty_like(psi_b)
+        self._dev(out, "out")
+        _check(self._lib.spe_fno_forward(self._h, ctypes.c_void_p(psi.data_ptr()),
+                                          ctypes.c_void_p(psi_b.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                          int(batch)), "spe_fno_forward")
+        self._keep = (psi, psi_b, out)
+        return out
+
+    def backward(self, target, want_loss=True):
+        target = self._dev(target, "target")
+        loss = ctypes.c_double()
+        _check(self._lib.spe_fno_backward(self._h, ctypes.c_void_p(target.data_ptr()),
+                                           ctypes.byref(loss) if want_loss else None), "spe_fno_backward")
+        return loss.value if want_loss else None
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(self._lib.spe_fno_adam(self._h, float(lr), float(beta1), float(beta2), float(eps)), "spe_fno_adam")
+
+    def launch_count(self, reset=False) -> int:
+        out = ctypes.c_ulonglong()
+        _check(self._lib.spe_fno_launch_count(self._h, ctypes.byref(out), int(bool(reset))), "spe_fno_launch_count")
+        return out.value
+
+
+class Surrogate:
+    """The judge (include/spe_fno.h): advance(grid, K, dt) moves the grid K steps by the network's
+    proposal when the mass and energy drifts pass, by the solver otherwise; spot_check=True runs
+    the solver as well and measures the proposal's relative L2 error."""
+
+    def __init__(self, grid: Grid, fno: Fno, max_mass_drift=1e-4, max_energy_drift=1e-3, max_rel_l2=1e-3):
+        self._lib = load_library()
+        self.fno = fno
+        self.jc = spe_judge_config(float(max_mass_drift), float(max_energy_drift), float(max_rel_l2))
+        h = ctypes.c_void_p()
+        _check(self._lib.spe_surrogate_create(ctypes.byref(grid.cfg), fno._h, ctypes.byref(self.jc),
+                                              ctypes.byref(h)), "spe_surrogate_create")
+        self._h = h
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            self._lib.spe_surrogate_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def advance(self, grid: Grid, K: int, dt: float, spot_check=False) -> dict:
+        r = spe_judge_result()
+        _check(self._lib.spe_surrogate_advance(self._h, grid._h, int(K), float(dt), int(bool(spot_check)),
+                                               ctypes.byref(r)), "spe_surrogate_advance")
+        return {k: getattr(r, k) for k, _ in spe_judge_result._fields_}

@@ -1,0 +1,112 @@
+"""The judge of the FNO surrogate on the GPU: a proposal that equals the solver's coarse step
+passes the mass and energy checks and the grid takes it; a wild proposal is rejected and the grid
+ends up exactly where the solver alone puts it; a spot check measures the proposal's error against
+the solver's own K steps (the coarse step's error, pinned against the FP64 oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fno_oracle as fo
+from paper_2606_25026_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+N, K = 32, 16
+
+
+@pytest.fixture(scope="module")
+def spe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_25026_gb300 import build
+    build.build()
+    oracle.build()
+    from paper_2606_25026_gb300 import spe as mod
+    mod.load_library()
+    return mod
+
+
+def zero_head_params(layers=2, modes=8):
+    shape = fo.FnoShape(n=N, modes=modes, layers=layers)
+    flat = fo.init_params(shape, seed=1)
+    p = fo.unpack(shape, flat)
+    p["Q2"][:] = 0.0
+    p["q2"][:] = 0.0
+    return flat.astype(np.float32)
+
+
+def make(spe, flat, **judge):
+    g = spe.Grid(N, G=1.0)
+    net = spe.Fno(n=N, layers=2, modes=8, sigma=0.05)
+    net.set_params(flat)
+    s = spe.Surrogate(g, net, **judge)
+    return g, net, s
+
+
+def test_coarse_step_proposal_is_accepted(spe):
+    psi = inputs.soliton_halo(N, seed=2)
+    dt = inputs.kinetic_dt(N)
+    g, net, s = make(spe, zero_head_params())
+    g.set_ic(psi)
+    r = s.advance(g, K, dt)
+    assert r["accepted"] == 1 and r["used_proposal"] == 1 and r["spot_checked"] == 0
+    # the grid now holds one solver step of K dt (the zero-head proposal is psi_b itself)
+    o = oracle.Oracle(N, N, N, 1.0, G=1.0)
+    o.set_ic(psi.astype(np.complex64).astype(np.complex128))
+    o.step(1, K * dt)
+    got, want = g.get_psi(), o.get_psi()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) <= 1e-5
+    assert r["mass_drift"] <= 1e-5 and r["energy_drift"] <= 1e-3
+
+
+def test_wild_proposal_falls_back_to_the_solver(spe):
+    psi = inputs.soliton_halo(N, seed=3)
+    dt = inputs.kinetic_dt(N)
+    shape = fo.FnoShape(n=N, modes=8, layers=2)
+    flat = fo.init_params(shape, seed=2, out_gain=50.0).astype(np.float32)
+    g, net, s = make(spe, flat)
+    g.set_ic(psi)
+    r = s.advance(g, K, dt)
+    assert r["accepted"] == 0 and r["used_proposal"] == 0
+    ref = spe.Grid(N, G=1.0)
+    ref.set_ic(psi)
+    ref.step(K, dt)
+    assert np.array_equal(g.get_psi(), ref.get_psi())
+
+
+def test_spot_check_measures_the_coarse_step_error(spe):
+    psi = inputs.soliton_halo(N, seed=4)
+    dt = inputs.kinetic_dt(N)
+    g, net, s = make(spe, zero_head_params(), max_rel_l2=1.0)
+    g.set_ic(psi)
+    r = s.advance(g, K, dt, spot_check=True)
+    assert r["spot_checked"] == 1 and r["used_proposal"] == 0 and r["accepted"] == 1
+    o = oracle.Oracle(N, N, N, 1.0, G=1.0)
+    p64 = psi.astype(np.complex64).astype(np.complex128)
+    o.set_ic(p64)
+    o.step(K, dt)
+    fine = o.get_psi()
+    c = oracle.Oracle(N, N, N, 1.0, G=1.0)
+    c.set_ic(p64)
+    c.step(1, K * dt)
+    want = np.linalg.norm(c.get_psi() - fine) / np.linalg.norm(fine)
+    assert r["rel_l2"] == pytest.approx(want, rel=0.05, abs=2e-6)
+    # the grid kept the solver's K steps
+    assert np.linalg.norm(g.get_psi() - fine) / np.linalg.norm(fine) <= 1e-5
+    # a tighter spot-check limit than the coarse step's error rejects the same proposal
+    g2, net2, s2 = make(spe, zero_head_params(), max_rel_l2=0.5 * want)
+    g2.set_ic(psi)
+    assert s2.advance(g2, K, dt, spot_check=True)["accepted"] == 0
+
+
+def test_surrogate_rejects_stars_and_mismatched_grid(spe):
+    g = spe.Grid(N, G=1.0, max_particles=10)
+    net = spe.Fno(n=N, layers=1, modes=8, sigma=0.05)
+    s = spe.Surrogate(g, net)
+    g.set_ic(inputs.soliton_halo(N, seed=5))
+    g.add_particles(np.zeros((1, 3)), np.zeros((1, 3)), np.full(1, 1e-3))
+    with pytest.raises(spe.SpeError):
+        s.advance(g, K, 1e-5)
+    with pytest.raises(spe.SpeError):
+        spe.Surrogate(spe.Grid(64, G=1.0), net)
