@@ -55,7 +55,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="halo256_stars1e6",
-                    choices=["halo256_stars1e6", "halo512", "packets32", "ensemble64"])
+                    choices=["halo256_stars1e6", "halo512", "packets32", "ensemble64", "fno64"])
+    ap.add_argument("--fno-epochs", type=int, default=8, help="fno64: training epochs over the pairs")
+    ap.add_argument("--fno-train", type=int, default=2000, help="fno64: training trajectories")
+    ap.add_argument("--fno-test", type=int, default=200, help="fno64: held-out trajectories")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "split16"],
                     help="split16: radix-16 DFT stages of 256/512-point axes on the tensor cores")
@@ -270,6 +273,167 @@ def ensemble_arm(args, rank, world, local):
     return 0
 
 
+def fno_flops(n=64, C=32, M=16, H=64, L=4, fin=4):
+    """Algorithmic FLOPs of one forward pass of the FNO on one n^3 sample (2 per multiply-add; a
+    complex multiply-add counts 4): the lift with the first x DFT, per layer the y and z DFTs, the
+    mode mixing, the z and y inverses and the row kernel (W v, the real x inverse, the next x
+    DFT), and the projection."""
+    cells = n ** 3
+    spectral = 4 * (2 * n * n * M * M * C + 2 * n * M ** 3 * C + M ** 3 * C * C)
+    row = cells * (C * C + 2 * M * C + 2 * M * C)
+    last_row = cells * (C * C + 2 * M * C + C * H + H * 2)
+    lift = cells * (C * fin + 2 * M * C)
+    return 2.0 * (lift + (L - 1) * (spectral + row) + spectral + last_row)
+
+
+def surrogate_arm(args, rank, world, local):
+    """The FNO surrogate against the plain solver on 64^3 halos: train on solver trajectories,
+    then advance held-out grids by K = 16 steps through the judge (proposal accepted when its mass
+    and energy drifts pass, spot-checked against the solver every 8th advance) and by the solver
+    alone.  value = cell-steps/s of the surrogate path; plain.value the solver's."""
+    import torch
+    from paper_2606_25026_gb300 import build as spe_build, inputs, spe, surrogate as sg
+    n, K = 64, 16
+    specs = sg.ic_specs(args.fno_train + args.fno_test, seed=2026)
+    ics = sg.make_ics(n, specs)
+    spe_build.build()
+    torch.cuda.set_device(local)
+    dt = inputs.kinetic_dt(n)
+    t0 = time.perf_counter()
+    train = sg.generate_pairs(ics[:args.fno_train], n, K, dt, pairs_per_ic=2, warmup_steps=16)
+    test = sg.generate_pairs(ics[args.fno_train:], n, K, dt, pairs_per_ic=1, warmup_steps=48)
+    t_gen = time.perf_counter() - t0
+    sigma = sg.correction_scale(train)
+    inv_A = 1.0 / math.sqrt(0.95)
+    net = spe.Fno(n=n, layers=4, modes=16, max_batch=8, train=True, inv_A=inv_A, sigma=sigma)
+    net.set_params(inputs.fno_init_params(seed=0, out_gain=0.1))
+    t0 = time.perf_counter()
+    l_train0 = net.launch_count()
+    hist = sg.train(net, train, epochs=args.fno_epochs, batch=8, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    e_coarse, e_prop = sg.evaluate(net, test)
+    params = net.get_params()
+    del train, net
+    torch.cuda.empty_cache()
+
+    inf = spe.Fno(n=n, layers=4, modes=16, max_batch=1, inv_A=inv_A, sigma=sigma)
+    inf.set_params(params)
+    g = spe.Grid(n, G=1.0)
+    jc = dict(max_mass_drift=1e-5, max_energy_drift=1e-4, max_rel_l2=2e-5)
+    sur = spe.Surrogate(g, inf, **jc)
+    S = len(test)
+    steps = max(1, min(args.steps, S))
+    spot_every = 8
+    # untimed pass: the error of what the surrogate path leaves on the grid, per held-out sample
+    errs, verdicts = [], []
+    for i in range(S):
+        g.set_ic(test.psi[i])
+        verdicts.append(sur.advance(g, K, dt, spot_check=(i % spot_every == 0)))
+        got = torch.empty_like(test.psi[i])
+        g.get_psi(out=got)
+        torch.cuda.synchronize()
+        errs.append(float(sg.rel_errors(got[None], test.target[i][None])[0]))
+    accepted = [v for v in verdicts if v["accepted"]]
+    spot = [v for v in verdicts if v["spot_checked"]]
+
+    def run_plain(count):
+        for i in range(count):
+            g.set_ic(test.psi[i % S])
+            g.step(K, dt)
+
+    def run_surrogate(count):
+        for i in range(count):
+            g.set_ic(test.psi[i % S])
+            sur.advance(g, K, dt, spot_check=(i % spot_every == 0))
+
+    warm = max(args.warmup, 3)
+    run_plain(warm)
+    run_surrogate(warm)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_plain = sg.timed(lambda: run_plain(steps), reps=1)
+    l0 = inf.launch_count()
+    t_sur = sg.timed(lambda: run_surrogate(steps), reps=1)
+    fno_launches = inf.launch_count() - l0
+    clk = clocks.stop()
+    cells = n ** 3
+    value = world * cells * K * steps / t_sur
+    plain = world * cells * K * steps / t_plain
+
+    # the forward pass alone (batch 1), CUDA events on the network's stream
+    x1, b1 = test.psi[:1].contiguous(), test.psi_b[:1].contiguous()
+    o1 = torch.empty_like(x1)
+    for _ in range(3):
+        inf.forward(x1, b1, out=o1)
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 50
+    ev0.record(st)
+    for _ in range(reps):
+        inf.forward(x1, b1, out=o1)
+    ev1.record(st)
+    ev1.synchronize()
+    fwd_s = ev0.elapsed_time(ev1) * 1e-3 / reps
+    flops = fno_flops()
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+
+    # e2e: the initial field from pinned host memory and the result back to it, every advance
+    h_in = test.psi[:min(S, 16)].cpu().pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    ke = min(steps, 16)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(ke):
+        g.set_ic(h_in[i % len(h_in)])
+        sur.advance(g, K, dt, spot_check=(i % spot_every == 0))
+        g.get_psi(out=h_out[i % len(h_out)])
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+
+    line = {
+        "metric": "grid_cell_steps_per_s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * t_sur / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 solver + bf16/fp32 network", "data": "synthetic",
+        "config": {"workload": "fno64", "grid": [n, n, n], "K": K, "dt": dt,
+                   "step": "one advance of one held-out grid by K solver steps (surrogate path)",
+                   "train_trajectories": args.fno_train, "train_pairs": 2 * args.fno_train,
+                   "held_out": S, "epochs": args.fno_epochs, "batch": 8, "judge": jc,
+                   "spot_check_every": spot_every, "l2": "2 MB fields, launch-bound; no flush"},
+        "plain": {"value": plain, "unit": "cell-steps/s", "ms_per_advance": 1e3 * t_plain / steps},
+        "speedup_vs_plain": value / plain,
+        "psi_error": {"vs": "solver K fine steps (FP32)", "surrogate_path_mean": float(np.mean(errs)),
+                      "proposal_mean": float(e_prop.mean()), "coarse_step_mean": float(e_coarse.mean()),
+                      "proposal_better_than_coarse": float(np.mean(e_prop < e_coarse))},
+        "judge": {"accept_rate": len(accepted) / S, "spot_checked": len(spot),
+                  "spot_rel_l2_mean": float(np.mean([v["rel_l2"] for v in spot])) if spot else None,
+                  "mass_drift_max": float(max(v["mass_drift"] for v in verdicts)),
+                  "energy_drift_max": float(max(v["energy_drift"] for v in verdicts))},
+        "training": {"loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "seconds": t_train,
+                     "pair_generation_s": t_gen, "sigma": sigma},
+        "roofline": {"bound": "alu", "kernel": "fno forward (all kernels, batch 1)", "achieved": flops / fwd_s / 1e12,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": flops / fwd_s / 1e12 / alu_peak,
+                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz", "traffic": None,
+                     "flops_per_launch": flops, "avg_launch_ms": fwd_s * 1e3},
+        "gpu_launches": int(fno_launches),
+        "clocks": clk,
+        "e2e": {"value": world * cells * K * ke / t_e2e, "unit": "cell-steps/s", "steps": ke,
+                "h2d_bytes_per_step": cells * 8, "d2h_bytes_per_step": cells * 8,
+                "what": "pinned-host upload of each held-out field, the judged advance, download of the result"},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        psi0 = test.psi[0].cpu().numpy()
+        z = np.zeros((0, 3), np.float32)
+        v, cores, sec, nsteps, _ = cpu_baseline(psi0, z, z, np.zeros(0, np.float32), dt)
+        line["cpu_baseline"] = {"value": v, "unit": "cell-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{nsteps} plain KDK steps of one held-out 64^3 field ({sec:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sur.destroy()
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -277,6 +441,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.workload == "ensemble64":
         return ensemble_arm(args, rank, world, local)
+    if args.workload == "fno64":
+        return surrogate_arm(args, rank, world, local)
 
     import torch
     import torch.distributed as dist

@@ -74,26 +74,6 @@ def unpack(s: FnoShape, flat):
     return out
 
 
-def init_params(s: FnoShape, seed: int = 0, out_gain: float = 0.1) -> np.ndarray:
-    """Seeded initialisation: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) for the pointwise maps
-    (PyTorch Linear default), R uniform in [0, 1/(C C)) per real component (the usual FNO scale),
-    and the last projection shrunk by ``out_gain`` so the untrained proposal stays near psi_b."""
-    rng = np.random.default_rng(seed)
-    parts = []
-    for name, shape in param_layout(s):
-        if name.startswith("R"):
-            a = rng.random(shape) / (s.width * s.width)
-        else:
-            fan_in = {"P": s.in_ch, "p": s.in_ch, "Q1": s.width, "q1": s.width,
-                      "Q2": s.hidden, "q2": s.hidden}.get(name, s.width)
-            bound = 1.0 / math.sqrt(fan_in)
-            a = rng.uniform(-bound, bound, shape)
-            if name in ("Q2", "q2"):
-                a = a * out_gain
-        parts.append(a.ravel())
-    return np.concatenate(parts)
-
-
 def gelu(u):
     """Exact GELU: u Phi(u) with Phi the standard normal CDF."""
     return 0.5 * u * (1.0 + torch.erf(u / math.sqrt(2.0)))

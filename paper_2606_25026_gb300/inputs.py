@@ -258,3 +258,33 @@ def ensemble(count=64, sizes=(64, 96, 128, 192), rc_range=(0.03, 0.08), max_star
             mass = np.zeros(0)
         out.append(dict(n=n, psi=psi, pos=pos, vel=vel, mass=mass, dt=kinetic_dt(n), r_c=rc))
     return out
+
+
+def fno_param_shapes(layers=4, modes=16, width=32, hidden=64, in_ch=4, out_ch=2):
+    """[(name, shape)] of the FNO surrogate's flat parameter vector, in order: P, p, then per
+    layer W, b, R (modes^3 x C_in x C_out x (re, im)), then Q1, q1, Q2, q2."""
+    out = [("P", (width, in_ch)), ("p", (width,))]
+    for l in range(layers):
+        out += [(f"W{l}", (width, width)), (f"b{l}", (width,)), (f"R{l}", (modes ** 3, width, width, 2))]
+    out += [("Q1", (hidden, width)), ("q1", (hidden,)), ("Q2", (out_ch, hidden)), ("q2", (out_ch,))]
+    return out
+
+
+def fno_init_params(layers=4, modes=16, seed=0, out_gain=0.1, width=32, hidden=64, in_ch=4, out_ch=2):
+    """Seeded initial parameters of the FNO surrogate (float32): uniform(-1/sqrt(fan_in),
+    1/sqrt(fan_in)) for the pointwise maps, spectral weights uniform in [0, 1/(C C)) per real
+    component, and the last projection shrunk by out_gain so the untrained proposal stays close
+    to the coarse step."""
+    rng = np.random.default_rng(seed)
+    fan = {"P": in_ch, "p": in_ch, "Q1": width, "q1": width, "Q2": hidden, "q2": hidden}
+    parts = []
+    for name, shape in fno_param_shapes(layers, modes, width, hidden, in_ch, out_ch):
+        if name.startswith("R"):
+            a = rng.random(shape) / (width * width)
+        else:
+            bound = 1.0 / math.sqrt(fan.get(name, width))
+            a = rng.uniform(-bound, bound, shape)
+            if name in ("Q2", "q2"):
+                a = a * out_gain
+        parts.append(a.ravel())
+    return np.concatenate(parts).astype(np.float32)

@@ -48,7 +48,7 @@ def problem(n, batch, seed):
 
 
 def params_for(shape, seed):
-    flat = fo.init_params(shape, seed=seed, out_gain=1.0)
+    flat = inputs.fno_init_params(shape.layers, shape.modes, seed=seed, out_gain=1.0).astype(np.float64)
     rng = np.random.default_rng(seed + 100)
     p = fo.unpack(shape, flat)
     for l in range(shape.layers):   # signed spectral weights, large enough to matter
@@ -131,10 +131,12 @@ def test_adam_step_matches_oracle(spe):
 
 def test_training_reduces_loss(spe):
     """A few Adam steps on one fixed batch lower the loss (the kernels' gradient is a descent
-    direction of their own forward)."""
+    direction of their own forward).  The target's correction, 0.03 i psi, is a pointwise linear
+    map of the features, so the network can represent it."""
     shape = fo.FnoShape(n=32, modes=8, layers=2)
-    flat = fo.init_params(shape, seed=5).astype(np.float32)
-    psis, pbs, tgs = problem(32, 2, seed=21)
+    flat = inputs.fno_init_params(shape.layers, shape.modes, seed=5)
+    psis, pbs, _ = problem(32, 2, seed=21)
+    tgs = [b + 0.03j * p for p, b in zip(psis, pbs)]
     net = spe.Fno(n=32, layers=2, modes=8, max_batch=2, train=True, sigma=0.03)
     net.set_params(flat)
     P, B, T = to_dev(psis), to_dev(pbs), to_dev(tgs)
@@ -144,7 +146,7 @@ def test_training_reduces_loss(spe):
         losses.append(net.backward(T))
         net.adam(lr=3e-3)
     print("losses", losses[0], losses[-1])
-    assert losses[-1] < 0.8 * losses[0]
+    assert losses[-1] < 0.5 * losses[0]
 
 
 def test_inference_mode_matches_training_forward(spe):

@@ -29,7 +29,7 @@ def spe():
 
 def zero_head_params(layers=2, modes=8):
     shape = fo.FnoShape(n=N, modes=modes, layers=layers)
-    flat = fo.init_params(shape, seed=1)
+    flat = inputs.fno_init_params(shape.layers, shape.modes, seed=1).astype(np.float64)
     p = fo.unpack(shape, flat)
     p["Q2"][:] = 0.0
     p["q2"][:] = 0.0
@@ -64,7 +64,7 @@ def test_wild_proposal_falls_back_to_the_solver(spe):
     psi = inputs.soliton_halo(N, seed=3)
     dt = inputs.kinetic_dt(N)
     shape = fo.FnoShape(n=N, modes=8, layers=2)
-    flat = fo.init_params(shape, seed=2, out_gain=50.0).astype(np.float32)
+    flat = inputs.fno_init_params(shape.layers, shape.modes, seed=2, out_gain=50.0)
     g, net, s = make(spe, flat)
     g.set_ic(psi)
     r = s.advance(g, K, dt)

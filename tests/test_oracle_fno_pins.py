@@ -10,6 +10,7 @@ import pytest
 import torch
 
 from oracle import fno_oracle as fo
+from paper_2606_25026_gb300 import inputs
 
 # Phi(1) and Phi(-1) of the standard normal distribution (tabulated values).
 PHI_1 = 0.8413447460685429
@@ -121,7 +122,8 @@ def tiny_shape():
 def tiny_problem(seed=0):
     s = tiny_shape()
     rng = np.random.default_rng(seed)
-    flat = fo.init_params(s, seed=seed, out_gain=1.0)
+    flat = inputs.fno_init_params(s.layers, s.modes, seed=seed, out_gain=1.0, width=s.width,
+                                  hidden=s.hidden).astype(np.float64)
     # make the spectral weights as large as the pointwise ones so their gradients matter
     p = fo.unpack(s, flat)
     for l in range(s.layers):
@@ -203,3 +205,11 @@ def test_param_count_of_config():
     # P, p, 4 x (W, b, R), Q1, q1, Q2, q2
     want = 32 * 4 + 32 + 4 * (32 * 32 + 32 + 16 ** 3 * 32 * 32 * 2) + 64 * 32 + 64 + 2 * 64 + 2
     assert fo.param_count(s) == want
+
+
+def test_seeded_initialiser_uses_the_oracle_layout():
+    """The shared seeded initialiser and the oracle agree on the flat parameter format."""
+    s = fo.FnoShape(n=32, modes=8, layers=3)
+    shapes = inputs.fno_param_shapes(s.layers, s.modes)
+    assert [(a, tuple(b)) for a, b in shapes] == [(a, tuple(b)) for a, b in fo.param_layout(s)]
+    assert inputs.fno_init_params(s.layers, s.modes).size == fo.param_count(s)
