@@ -28,7 +28,11 @@
  *   Q1 [H][C], q1 [H], Q2 [2][H], q2 [2].
  * The library keeps an FP32 master copy (Adam updates it) and a BF16 mirror;
  * every kernel reads the BF16 weights and accumulates in FP32.  Activations
- * are stored in BF16 (default) or FP32 (SPE_FNO_ACT_FP32).
+ * are stored in BF16 (default) or FP32 (SPE_FNO_ACT_FP32).  With BF16
+ * activations the forward pass runs its dense row stages (W v, the real x
+ * inverse, the next x DFT, the projection) on the tensor cores with BF16
+ * operands (the DFT tables and the spectral inputs rounded to BF16); with FP32
+ * activations every stage runs on the CUDA cores in FP32.
  *
  * Batch loss (spe_fno_backward):  sum_b sum_cells |psi_pred - psi_target|^2
  *                                 / (sigma^2 B n^3).
@@ -101,6 +105,11 @@ SPE_API int spe_fno_backward(spe_fno *f, const void *psi_target, double *loss_ou
 /* One Adam step (Kingma & Ba 2015) on the FP32 master with the current
  * gradient, then refresh the BF16 mirror.  Asynchronous. */
 SPE_API int spe_fno_adam(spe_fno *f, double lr, double beta1, double beta2, double eps);
+
+/* Synchronise the network's stream; SPE_ETIMEOUT if a bounded device-side wait
+ * of a tensor-core kernel gave up since the last call (the affected results
+ * are wrong; the flag is cleared). */
+SPE_API int spe_fno_sync(spe_fno *f);
 
 /* Kernels launched by this network since creation (or the last reset). */
 SPE_API int spe_fno_launch_count(spe_fno *f, unsigned long long *count_out, int reset);

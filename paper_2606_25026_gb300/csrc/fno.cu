@@ -39,6 +39,7 @@ struct spe_fno {
     float2 *xrow, *ym, *Ybuf, *Xbbuf, *Xsave[8];
     float *ubar, *partials;
     double *dres;
+    int *status;
     const float2 *last_psi, *last_psib;
     int last_batch;
     bool have_fwd;
@@ -111,6 +112,7 @@ cudaError_t ensure_x_tables()
     }
     e = upload_fwd_tables(G[0].data(), F[0].data(), G[1].data(), F[1].data());
     if (e == cudaSuccess) e = upload_bwd_tables(G[0].data(), F[0].data(), G[1].data(), F[1].data());
+    if (e == cudaSuccess) e = upload_tc_tables(G[0].data(), F[0].data(), G[1].data(), F[1].data());
     if (e == cudaSuccess && dev < 64) g_tables_done[dev] = true;
     return e;
 }
@@ -147,6 +149,7 @@ RowArgs base_args(spe_fno *f, int batch)
     a.xrow = f->xrow;
     a.ubar = f->ubar;
     a.partials = f->partials;
+    a.status = f->status;
     return a;
 }
 
@@ -251,6 +254,7 @@ SPE_API int spe_fno_create(const spe_fno_config *cfg, spe_fno **out)
     if (f->train) ok(dalloc(f, &f->ubar, B * cells * kC));
     ok(dalloc(f, &f->partials, (size_t)kRowBlocks * kTopSeg));
     ok(dalloc(f, &f->dres, 8));
+    ok(dalloc(f, &f->status, 1));
     if (e == cudaSuccess) {
         std::vector<float2> Ef(M * n), Ei(n * M);
         for (size_t m = 0; m < M; ++m)
@@ -268,6 +272,7 @@ SPE_API int spe_fno_create(const spe_fno_config *cfg, spe_fno **out)
         ok(cudaMemset(f->am, 0, f->nparams * sizeof(float)));
         ok(cudaMemset(f->av, 0, f->nparams * sizeof(float)));
         ok(cudaMemset(f->w16, 0, f->nparams * sizeof(__nv_bfloat16)));
+        ok(cudaMemset(f->status, 0, sizeof(int)));
     }
     if (e != cudaSuccess) {
         const int rc = (e == cudaErrorMemoryAllocation) ? SPE_ENOMEM : SPE_ECUDA;
@@ -330,7 +335,13 @@ SPE_API int spe_fno_forward(spe_fno *f, const void *psi, const void *psi_b, void
     a.psib = (const float2 *)psi_b;
     a.out = (float2 *)psi_out;
     a.vout = v_buf(f, 0);
-    SPE_TRY(launch_lift_fwd(n, M, f->fp32, a, grid, f->st));
+    // BF16 activations run the row stages on the tensor cores; FP32 keeps the CUDA-core kernels
+    const bool tc = !f->fp32;
+    const int tiles = rows / kTcTile, tgrid = tiles < kTcBlocks ? tiles : kTcBlocks;
+    if (tc)
+        SPE_TRY(launch_layer_fwd_tc(n, M, 2, a, tgrid, f->st));
+    else
+        SPE_TRY(launch_lift_fwd(n, M, f->fp32, a, grid, f->st));
     for (int l = 0; l < L; ++l) {
         int rc = spectral_fwd(f, l, batch);
         if (rc) return rc;
@@ -343,7 +354,19 @@ SPE_API int spe_fno_forward(spe_fno *f, const void *psi, const void *psi_b, void
         b.store_u = (f->train && l < L - 1) ? 1 : 0;
         b.oW = f->off.W[l];
         b.ob = f->off.b[l];
-        SPE_TRY(launch_layer_fwd(n, M, f->fp32, l == L - 1, b, grid, f->st));
+        if (tc) {
+            SPE_TRY(launch_layer_fwd_tc(n, M, l == L - 1 ? 1 : 0, b, tgrid, f->st));
+        } else {
+            SPE_TRY(launch_layer_fwd(n, M, f->fp32, l == L - 1, b, grid, f->st));
+        }
+    }
+    if (tc) {
+        RowArgs p = base_args(f, batch);
+        p.vin = v_buf(f, L);
+        p.psib = (const float2 *)psi_b;
+        p.out = (float2 *)psi_out;
+        const int cells = rows * n, ptiles = cells / 128;
+        SPE_TRY(launch_proj_tc(p, cells, ptiles < kTcBlocks ? ptiles : kTcBlocks, f->st));
     }
     f->last_psi = (const float2 *)psi;
     f->last_psib = (const float2 *)psi_b;
@@ -391,6 +414,7 @@ SPE_API int spe_fno_backward(spe_fno *f, const void *psi_target, double *loss_ou
         cudaError_t e = cudaMemcpyAsync(&s, f->dres, sizeof(double), cudaMemcpyDeviceToHost, f->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(f->st);
         if (e != cudaSuccess) return SPE_ECUDA;
+        if ((rc = spe_fno_sync(f))) return rc;
         *loss_out = s / (f->cfg.sigma * f->cfg.sigma * (double)batch * (double)n * n * n);
     }
     return SPE_OK;
@@ -405,6 +429,20 @@ SPE_API int spe_fno_adam(spe_fno *f, double lr, double beta1, double beta2, doub
     const double c2 = 1.0 / (1.0 - std::pow(beta2, (double)f->adam_t));
     SPE_TRY(launch_adam(f->master, f->am, f->av, f->grad, f->w16, f->nparams, (float)lr, (float)beta1,
                         (float)beta2, (float)eps, (float)c1, (float)c2, f->st));
+    return SPE_OK;
+}
+
+SPE_API int spe_fno_sync(spe_fno *f)
+{
+    if (!f) return SPE_EINVAL;
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, f->status, sizeof(int), cudaMemcpyDeviceToHost, f->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->st);
+    if (e != cudaSuccess) return SPE_ECUDA;
+    if (st) {
+        cudaMemsetAsync(f->status, 0, sizeof(int), f->st);
+        return SPE_ETIMEOUT;
+    }
     return SPE_OK;
 }
 

@@ -57,6 +57,7 @@ struct RowArgs {
     size_t oW, ob, oP, op, oQ1, oq1, oQ2, oq2;
     float inv_A, sigma, loss_scale;
     float *partials;                // [gridDim.x][segment]
+    int *status;                    // device status word (tensor-core wait timeouts)
 };
 
 // forward row kernels (fno_fwd.cu)
@@ -70,6 +71,14 @@ cudaError_t launch_top_bwd(int n, bool fp32, const RowArgs &a, int grid, cudaStr
 cudaError_t launch_grad_start(int n, int M, bool fp32, const RowArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_layer_bwd(int n, int M, bool fp32, const RowArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_lift_bwd(int n, int M, bool fp32, const RowArgs &a, int grid, cudaStream_t st);
+
+// tensor-core forward kernels, BF16 activations (fno_tc.cu)
+// mode: 0 = Fourier layer, 1 = last Fourier layer (no GELU, no next x DFT), 2 = lift
+constexpr int kTcTile = 4;          // rows per tensor-core tile
+constexpr int kTcBlocks = 304;      // 2 CTAs per SM (about 82 KB of shared memory each)
+cudaError_t upload_tc_tables(const float2 *G64, const float2 *F64, const float2 *G32, const float2 *F32);
+cudaError_t launch_layer_fwd_tc(int n, int M, int mode, const RowArgs &a, int grid, cudaStream_t st);
+cudaError_t launch_proj_tc(const RowArgs &a, int cells, int grid, cudaStream_t st);
 
 // mode-space and elementwise kernels (fno_modes.cu)
 // out[o][m][i] = scale * sum_j mat[m][j] in[o][j][i], m < Mout, j < nin

@@ -37,11 +37,6 @@ void release(spe_surrogate *s)
     cudaFree(s->counter);
 }
 
-int sync_or(cudaStream_t st)
-{
-    return cudaStreamSynchronize(st) == cudaSuccess ? SPE_OK : SPE_ECUDA;
-}
-
 }  // namespace
 
 extern "C" {
@@ -104,7 +99,6 @@ SPE_API int spe_surrogate_advance(spe_surrogate *s, spe_grid *g, int K, double d
     if (np) return SPE_EINVAL;
     spe_judge_result r{};
     r.rel_l2 = -1.0;
-    cudaStream_t fst = net_stream(s->f);
     // 1. the state and its energy
     if ((rc = spe_get_psi(g, s->psi0, SPE_DEVICE))) return rc;
     spe_energy_t e0{}, e1{};
@@ -115,7 +109,7 @@ SPE_API int spe_surrogate_advance(spe_surrogate *s, spe_grid *g, int K, double d
     if ((rc = spe_get_psi(s->coarse, s->psib, SPE_DEVICE))) return rc;
     if ((rc = spe_sync(s->coarse))) return rc;
     if ((rc = spe_fno_forward(s->f, s->psi0, s->psib, s->prop, 1))) return rc;
-    if ((rc = sync_or(fst))) return rc;
+    if ((rc = spe_fno_sync(s->f))) return rc;
     // 3. drifts of the proposal
     if ((rc = spe_set_ic(s->coarse, s->prop, s->ncells, SPE_DEVICE))) return rc;
     if ((rc = spe_energy(s->coarse, &e1))) return rc;

@@ -37,7 +37,8 @@ EXPORTED = (
     "spe_batch_autotune", "spe_batch_step", "spe_batch_launch_count", "spe_batch_destroy",
     # include/spe_fno.h
     "spe_fno_param_count", "spe_fno_create", "spe_fno_destroy", "spe_fno_set_params", "spe_fno_get_params",
-    "spe_fno_get_grads", "spe_fno_forward", "spe_fno_backward", "spe_fno_adam", "spe_fno_launch_count",
+    "spe_fno_get_grads", "spe_fno_forward", "spe_fno_backward", "spe_fno_adam", "spe_fno_sync",
+    "spe_fno_launch_count",
     "spe_surrogate_create", "spe_surrogate_destroy", "spe_surrogate_advance",
 )
 
@@ -140,6 +141,7 @@ def load_library(path: str = LIB_PATH):
         "spe_fno_forward": (I, [P, P, P, P, I]),
         "spe_fno_backward": (I, [P, P, ctypes.POINTER(D)]),
         "spe_fno_adam": (I, [P, D, D, D, D]),
+        "spe_fno_sync": (I, [P]),
         "spe_fno_launch_count": (I, [P, ctypes.POINTER(ctypes.c_ulonglong), I]),
         "spe_surrogate_create": (I, [ctypes.POINTER(spe_config), P, ctypes.POINTER(spe_judge_config),
                                      ctypes.POINTER(P)]),
@@ -534,6 +536,9 @@ class Fno:
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(self._lib.spe_fno_adam(self._h, float(lr), float(beta1), float(beta2), float(eps)), "spe_fno_adam")
+
+    def sync(self):
+        _check(self._lib.spe_fno_sync(self._h), "spe_fno_sync")
 
     def launch_count(self, reset=False) -> int:
         out = ctypes.c_ulonglong()

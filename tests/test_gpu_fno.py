@@ -4,9 +4,11 @@ The oracle runs with the BF16-rounded weights the kernels read.  Tolerances:
   * FP32 activations: the kernels differ from the oracle only by FP32 rounding of the tables and
     of sums of up to a few thousand terms, so the proposal's correction, the loss and every
     parameter group's gradient agree to 1e-4 relative (measured ~1e-6).
-  * BF16 activations: each stored activation carries a relative rounding error of up to 2^-9
-    (about 2e-3); five stored activations lie on the path (v_0 .. v_4), so the correction agrees
-    to 2e-2 and the gradients, which multiply two rounded activations, to 5e-2."""
+  * BF16 activations (the forward's row stages then run on the tensor cores with BF16 operands,
+    the DFT tables and the spectral inputs included): each stored activation and each operand
+    carries a relative rounding error of up to 2^-9 (about 2e-3); five stored activations lie on
+    the path (v_0 .. v_4), so the correction agrees to 2e-2 and the gradients, which multiply two
+    rounded activations, to 5e-2."""
 import numpy as np
 import torch
 import pytest
@@ -74,6 +76,8 @@ CASES = [
     (32, 8, 2, 1, True),
     (64, 16, 2, 1, True),
     (32, 16, 4, 2, False),
+    (64, 16, 2, 1, False),
+    (32, 8, 3, 2, False),
 ]
 
 
@@ -195,3 +199,21 @@ def test_bad_arguments(spe):
     with pytest.raises(spe.SpeError):
         net.forward(torch.zeros((2, 32, 32, 32), dtype=torch.complex64, device="cuda"),
                     torch.zeros((2, 32, 32, 32), dtype=torch.complex64, device="cuda"))
+
+
+@pytest.mark.parametrize("n,M", [(64, 16), (32, 8)])
+def test_tensor_core_forward_matches_fp32_path(spe, n, M):
+    """The BF16 tensor-core forward against the FP32 CUDA-core forward of the same weights."""
+    shape = fo.FnoShape(n=n, modes=M, layers=3)
+    flat = params_for(shape, seed=40 + n)
+    psis, pbs, _ = problem(n, 2, seed=50 + n)
+    outs = []
+    for fp32 in (True, False):
+        net = spe.Fno(n=n, layers=3, modes=M, max_batch=2, act_fp32=fp32, sigma=0.05)
+        net.set_params(flat)
+        outs.append(net.forward(to_dev(psis), to_dev(pbs)).cpu().numpy())
+        net.sync()
+    for b in range(2):
+        c32 = (outs[0][b] - pbs[b]) / 0.05
+        c16 = (outs[1][b] - pbs[b]) / 0.05
+        assert rel_l2(c16, c32) <= 2e-2, rel_l2(c16, c32)
