@@ -35,6 +35,7 @@ struct spe_fno {
     __nv_bfloat16 *w16;
     long long adam_t;
     float2 *Efwd, *Einv;
+    uint4 *tcG, *tcF;
     void *act[16];
     float2 *xrow, *ym, *Ybuf, *Xbbuf, *Xsave[8];
     float *ubar, *partials;
@@ -84,6 +85,42 @@ Offsets make_offsets(int L, int M)
 
 int signed_freq(int m, int M) { return m < M / 2 ? m : m - M; }
 
+// float -> bfloat16 bits, round to nearest even (finite inputs)
+unsigned short host_bf16(float v)
+{
+    uint32_t b;
+    std::memcpy(&b, &v, 4);
+    b += 0x7FFFu + ((b >> 16) & 1u);
+    return (unsigned short)(b >> 16);
+}
+
+// byte offset of (row, k) in a no-swizzle K-major tensor-core operand with K columns
+int kmaj_host(int row, int k, int K) { return (row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2; }
+
+// BF16 operand images of the x stages for the tensor-core row kernels:
+// G' [n][2M]: (Re Gx, -Im Gx) pairs; F' [2M][n]: rows (Re Fx), (Im Fx).
+void build_tc_images(int n, int M, std::vector<unsigned char> &g, std::vector<unsigned char> &fimg)
+{
+    const int KM = 2 * M;
+    g.assign((size_t)n * KM * 2, 0);
+    fimg.assign((size_t)n * KM * 2, 0);
+    for (int x = 0; x < n; ++x)
+        for (int k = 0; k < M; ++k) {
+            const double th = 2.0 * kPi * (double)((long long)k * x % n) / n;
+            const double w = (k == 0 ? 1.0 : 2.0) / n;
+            const float gr = (float)(w * std::cos(th)), gi = (float)(w * std::sin(th));
+            const float fr = (float)std::cos(th), fi = (float)-std::sin(th);
+            auto put = [](std::vector<unsigned char> &v, int off, float val) {
+                const unsigned short h = host_bf16(val);
+                std::memcpy(v.data() + off, &h, 2);
+            };
+            put(g, kmaj_host(x, 2 * k, KM), gr);
+            put(g, kmaj_host(x, 2 * k + 1, KM), -gi);
+            put(fimg, kmaj_host(2 * k, x, n), fr);
+            put(fimg, kmaj_host(2 * k + 1, x, n), fi);
+        }
+}
+
 std::mutex g_tables_mu;
 bool g_tables_done[64];
 
@@ -112,7 +149,6 @@ cudaError_t ensure_x_tables()
     }
     e = upload_fwd_tables(G[0].data(), F[0].data(), G[1].data(), F[1].data());
     if (e == cudaSuccess) e = upload_bwd_tables(G[0].data(), F[0].data(), G[1].data(), F[1].data());
-    if (e == cudaSuccess) e = upload_tc_tables(G[0].data(), F[0].data(), G[1].data(), F[1].data());
     if (e == cudaSuccess && dev < 64) g_tables_done[dev] = true;
     return e;
 }
@@ -150,6 +186,8 @@ RowArgs base_args(spe_fno *f, int batch)
     a.ubar = f->ubar;
     a.partials = f->partials;
     a.status = f->status;
+    a.tcG = f->tcG;
+    a.tcF = f->tcF;
     return a;
 }
 
@@ -239,6 +277,8 @@ SPE_API int spe_fno_create(const spe_fno_config *cfg, spe_fno **out)
     ok(dalloc(f, &f->av, f->nparams));
     ok(dalloc(f, &f->w16, f->nparams));
     ok(dalloc(f, &f->Efwd, M * n));
+    ok(dalloc(f, &f->tcG, n * 2 * M * 2 / 16));
+    ok(dalloc(f, &f->tcF, n * 2 * M * 2 / 16));
     ok(dalloc(f, &f->Einv, n * M));
     const int nact = f->train ? 2 * f->L : 2;
     for (int i = 0; i < nact; ++i) {
@@ -267,6 +307,10 @@ SPE_API int spe_fno_create(const spe_fno_config *cfg, spe_fno **out)
             }
         ok(cudaMemcpy(f->Efwd, Ef.data(), Ef.size() * sizeof(float2), cudaMemcpyHostToDevice));
         ok(cudaMemcpy(f->Einv, Ei.data(), Ei.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        std::vector<unsigned char> gimg, fimg;
+        build_tc_images((int)n, (int)M, gimg, fimg);
+        ok(cudaMemcpy(f->tcG, gimg.data(), gimg.size(), cudaMemcpyHostToDevice));
+        ok(cudaMemcpy(f->tcF, fimg.data(), fimg.size(), cudaMemcpyHostToDevice));
         ok(cudaMemset(f->master, 0, f->nparams * sizeof(float)));
         ok(cudaMemset(f->grad, 0, f->nparams * sizeof(float)));
         ok(cudaMemset(f->am, 0, f->nparams * sizeof(float)));
@@ -366,7 +410,7 @@ SPE_API int spe_fno_forward(spe_fno *f, const void *psi, const void *psi_b, void
         p.psib = (const float2 *)psi_b;
         p.out = (float2 *)psi_out;
         const int cells = rows * n, ptiles = cells / 128;
-        SPE_TRY(launch_proj_tc(p, cells, ptiles < kTcBlocks ? ptiles : kTcBlocks, f->st));
+        SPE_TRY(launch_proj_tc(p, cells, ptiles < kProjBlocks ? ptiles : kProjBlocks, f->st));
     }
     f->last_psi = (const float2 *)psi;
     f->last_psib = (const float2 *)psi_b;

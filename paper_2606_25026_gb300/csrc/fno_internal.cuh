@@ -58,6 +58,7 @@ struct RowArgs {
     float inv_A, sigma, loss_scale;
     float *partials;                // [gridDim.x][segment]
     int *status;                    // device status word (tensor-core wait timeouts)
+    const uint4 *tcG, *tcF;         // BF16 operand images of G' [n][2M] and F' [2M][n] (K-major)
 };
 
 // forward row kernels (fno_fwd.cu)
@@ -76,7 +77,7 @@ cudaError_t launch_lift_bwd(int n, int M, bool fp32, const RowArgs &a, int grid,
 // mode: 0 = Fourier layer, 1 = last Fourier layer (no GELU, no next x DFT), 2 = lift
 constexpr int kTcTile = 4;          // rows per tensor-core tile
 constexpr int kTcBlocks = 304;      // 2 CTAs per SM (about 82 KB of shared memory each)
-cudaError_t upload_tc_tables(const float2 *G64, const float2 *F64, const float2 *G32, const float2 *F32);
+constexpr int kProjBlocks = 1216;   // up to 8 CTAs per SM
 cudaError_t launch_layer_fwd_tc(int n, int M, int mode, const RowArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_proj_tc(const RowArgs &a, int cells, int grid, cudaStream_t st);
 

@@ -171,17 +171,39 @@ __global__ void __launch_bounds__(256) diff_norms_kernel(const float2 *__restric
 
 }  // namespace
 
+template <int NIN>
+cudaError_t axis_nin(int MT, const float2 *in, float2 *out, const float2 *mat, int Mout, int O, int I, float scale,
+                     cudaStream_t st)
+{
+    switch (MT) {
+        case 1: return axis_run<NIN, 1>(in, out, mat, Mout, O, I, scale, st);
+        case 2: return axis_run<NIN, 2>(in, out, mat, Mout, O, I, scale, st);
+        case 4: return axis_run<NIN, 4>(in, out, mat, Mout, O, I, scale, st);
+        case 8: return axis_run<NIN, 8>(in, out, mat, Mout, O, I, scale, st);
+        default: return axis_run<NIN, 16>(in, out, mat, Mout, O, I, scale, st);
+    }
+}
+
+// Outputs per thread: as many as keep about 128 K threads in flight (the
+// contractions are short; latency, not arithmetic, bounds them), at most 16.
+int pick_mt(int Mout, long long OI)
+{
+    int mt = 16;
+    while (mt > 1 && (Mout % mt != 0 || OI * (Mout / mt) < (128ll << 10))) mt >>= 1;
+    return mt;
+}
+
 cudaError_t launch_axis(const float2 *in, float2 *out, const float2 *mat, int nin, int Mout, int O, int I,
                         float scale, cudaStream_t st)
 {
-    // forward stages: nin = n, Mout = M (one chunk); inverse stages: nin = M, Mout = n (chunks of 16)
-    if (nin == 64 && Mout == 16) return axis_run<64, 16>(in, out, mat, Mout, O, I, scale, st);
-    if (nin == 64 && Mout == 8) return axis_run<64, 8>(in, out, mat, Mout, O, I, scale, st);
-    if (nin == 32 && Mout == 16) return axis_run<32, 16>(in, out, mat, Mout, O, I, scale, st);
-    if (nin == 32 && Mout == 8) return axis_run<32, 8>(in, out, mat, Mout, O, I, scale, st);
-    if (nin == 16 && Mout % 16 == 0) return axis_run<16, 16>(in, out, mat, Mout, O, I, scale, st);
-    if (nin == 8 && Mout % 16 == 0) return axis_run<8, 16>(in, out, mat, Mout, O, I, scale, st);
-    return cudaErrorInvalidValue;
+    const int mt = pick_mt(Mout, (long long)O * I);
+    switch (nin) {
+        case 64: return axis_nin<64>(mt, in, out, mat, Mout, O, I, scale, st);
+        case 32: return axis_nin<32>(mt, in, out, mat, Mout, O, I, scale, st);
+        case 16: return axis_nin<16>(mt, in, out, mat, Mout, O, I, scale, st);
+        case 8: return axis_nin<8>(mt, in, out, mat, Mout, O, I, scale, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_mix_fwd(int M, const float2 *X, float2 *Y, const __nv_bfloat16 *R, int B, cudaStream_t st)

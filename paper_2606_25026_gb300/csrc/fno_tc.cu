@@ -111,12 +111,27 @@ struct LayerSmem {
     static constexpr int BYTES = CTL + 64;
 };
 
+template <int COLS>
+__device__ __forceinline__ void tmem_alloc_n(uint32_t *dst)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+template <int COLS>
+__device__ __forceinline__ void tmem_free_n(uint32_t base)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(COLS) : "memory");
+}
+
 struct TcCtl {
     unsigned long long mbar;
     uint32_t tmem_base;
     uint32_t phase;
 };
 
+template <int COLS>
 __device__ __forceinline__ void ctl_setup(TcCtl *ctl)
 {
     if (threadIdx.x == 0) {
@@ -124,7 +139,7 @@ __device__ __forceinline__ void ctl_setup(TcCtl *ctl)
         ctl->phase = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (threadIdx.x < 32) tmem_alloc(&ctl->tmem_base);
+    if (threadIdx.x < 32) tmem_alloc_n<COLS>(&ctl->tmem_base);
 }
 
 // make the generic-proxy shared-memory writes visible to the tensor cores and
@@ -165,27 +180,22 @@ __global__ void __launch_bounds__(kRowThreads) layer_fwd_tc_kernel(RowArgs a)
     TcCtl *ctl = reinterpret_cast<TcCtl *>(sm + S::CTL);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // ---- per-CTA constants: blockdiag(W), G', F'
+    // ---- per-CTA constants: blockdiag(W) (zero off the diagonal), G', F' (prebuilt images)
     if (!LIFT) {
-        for (int e = tid; e < 128 * 128 / 2; e += kRowThreads) reinterpret_cast<uint32_t *>(sm + S::A1)[e] = 0u;
+        for (int e = tid; e < 128 * 128 * 2 / 16; e += kRowThreads)
+            reinterpret_cast<uint4 *>(sm + S::A1)[e] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
-        for (int e = tid; e < kTile * kC * kC; e += kRowThreads) {
-            const int r = e / (kC * kC), c = (e / kC) % kC, j = e % kC;
-            *reinterpret_cast<unsigned short *>(sm + S::A1 + kmaj(r * 32 + c, r * 32 + j, 128)) =
-                __bfloat16_as_ushort(a.w[a.oW + c * kC + j]);
+        for (int e = tid; e < kTile * kC * 4; e += kRowThreads) {
+            const int r = e / (kC * 4), c = (e / 4) % kC, q = e % 4;
+            *reinterpret_cast<uint4 *>(sm + S::A1 + kmaj(r * 32 + c, r * 32 + q * 8, 128)) =
+                *reinterpret_cast<const uint4 *>(a.w + a.oW + c * kC + q * 8);
         }
     }
-    for (int e = tid; e < N * M; e += kRowThreads) {
-        const int x = e / M, kx = e % M;
-        const float2 g = Gx<N>(x, kx);
-        *reinterpret_cast<uint32_t *>(sm + S::B2 + kmaj(x, 2 * kx, KM)) = pack_bf16(g.x, -g.y);
-        if (!LAST) {
-            const float2 f = Fx<N>(kx, x);
-            *reinterpret_cast<unsigned short *>(sm + S::B3 + kmaj(2 * kx, x, N)) = bf16_bits(f.x);
-            *reinterpret_cast<unsigned short *>(sm + S::B3 + kmaj(2 * kx + 1, x, N)) = bf16_bits(f.y);
-        }
+    for (int e = tid; e < N * KM * 2 / 16; e += kRowThreads) {
+        reinterpret_cast<uint4 *>(sm + S::B2)[e] = a.tcG[e];
+        if (!LAST) reinterpret_cast<uint4 *>(sm + S::B3)[e] = a.tcF[e];
     }
-    ctl_setup(ctl);
+    ctl_setup<128>(ctl);
     const float bc = LIFT ? wload(a.w, a.op + lane) : wload(a.w, a.ob + lane);
     float Pr[kFin];
 #pragma unroll
@@ -312,7 +322,7 @@ __global__ void __launch_bounds__(kRowThreads) layer_fwd_tc_kernel(RowArgs a)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_free(tbase);
+    if (warp == 0) tmem_free_n<128>(tbase);
 }
 
 // Projection: H[cell][j] = sum_c V_L[cell][c] Q1[j][c] on the tensor cores
@@ -323,8 +333,7 @@ struct ProjSmem {
     static constexpr int PART = B + 64 * 32 * 2;  // [128][2] partial outputs of columns 32..63
     static constexpr int PAR = PART + 128 * 2 * 4;// q1 [64], Q2 [2][64], q2 [2]
     static constexpr int CTL = PAR + (64 + 128 + 2) * 4 + 8;
-    // padded so that at most 2 CTAs share an SM: each holds 128 TMEM columns of the SM's 512
-    static constexpr int BYTES = 80 * 1024;
+    static constexpr int BYTES = CTL + 64;   // at most 8 CTAs of 256 threads per SM: 8 x 64 TMEM columns
 };
 
 __global__ void __launch_bounds__(kRowThreads) proj_tc_kernel(RowArgs a, int cells)
@@ -337,14 +346,15 @@ __global__ void __launch_bounds__(kRowThreads) proj_tc_kernel(RowArgs a, int cel
     float *q2w = q1 + 64;
     float *q2b = q2w + 128;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < kH * kC; e += kRowThreads) {
-        const int j = e / kC, c = e % kC;
-        *reinterpret_cast<unsigned short *>(sm + S::B + kmaj(j, c, 32)) = __bfloat16_as_ushort(a.w[a.oQ1 + e]);
+    for (int e = tid; e < kH * 4; e += kRowThreads) {
+        const int j = e / 4, q = e % 4;
+        *reinterpret_cast<uint4 *>(sm + S::B + kmaj(j, q * 8, 32)) =
+            *reinterpret_cast<const uint4 *>(a.w + a.oQ1 + j * kC + q * 8);
     }
     for (int e = tid; e < kH; e += kRowThreads) q1[e] = wload(a.w, a.oq1 + e);
     for (int e = tid; e < 2 * kH; e += kRowThreads) q2w[e] = wload(a.w, a.oQ2 + e);
     if (tid < 2) q2b[tid] = wload(a.w, a.oq2 + tid);
-    ctl_setup(ctl);
+    ctl_setup<64>(ctl);
     to_tensor_cores();
     const uint32_t tbase = ctl->tmem_base;
     const __nv_bfloat16 *vin = (const __nv_bfloat16 *)a.vin;
@@ -395,7 +405,7 @@ __global__ void __launch_bounds__(kRowThreads) proj_tc_kernel(RowArgs a, int cel
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_free(tbase);
+    if (warp == 0) tmem_free_n<64>(tbase);
 }
 
 template <int N, int M, int MODE>
@@ -450,10 +460,6 @@ cudaError_t launch_proj_tc(const RowArgs &a, int cells, int grid, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t upload_tc_tables(const float2 *G64, const float2 *F64, const float2 *G32, const float2 *F32)
-{
-    return upload_tables_here(G64, F64, G32, F32);
-}
 
 }  // namespace fno
 }  // namespace spe
