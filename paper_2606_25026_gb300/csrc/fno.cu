@@ -3,9 +3,9 @@
 //
 // Forward (per layer l, after the lift has written v_0 and its x DFT):
 //   y DFT  (axis over y, Efwd)      x-row buffer -> y-stage buffer
-//   z DFT  (axis over z, Efwd)      -> modes X_l
-//   mixing (R_l per mode)           -> Y
-//   z IDFT (axis, Einv, 1/n)        -> y-stage buffer
+//   z DFT, mixing (R_l per mode), z IDFT (Einv, 1/n): one fused kernel per
+//          (ky, kx) column, in place in the y-stage buffer (modes X_l kept
+//          for training)
 //   y IDFT (axis, Einv, 1/n)        -> x-row buffer
 //   row kernel: x IDFT (Gx, 1/n) + W v + b, GELU, next x DFT (or projection)
 // Backward runs the adjoints in reverse: an adjoint of a stage with matrix A
@@ -204,11 +204,9 @@ int row_grid(int rows) { return rows < kRowBlocks ? rows : kRowBlocks; }
 int spectral_fwd(spe_fno *f, int l, int batch)
 {
     const int n = f->n, M = f->M;
-    float2 *X = f->train ? f->Xsave[l] : f->Xsave[0];
     SPE_TRY(launch_axis(f->xrow, f->ym, f->Efwd, n, M, batch * n, M * kC, 1.f, f->st));
-    SPE_TRY(launch_axis(f->ym, X, f->Efwd, n, M, batch, M * M * kC, 1.f, f->st));
-    SPE_TRY(launch_mix_fwd(M, X, f->Ybuf, f->w16 + f->off.R[l], batch, f->st));
-    SPE_TRY(launch_axis(f->Ybuf, f->ym, f->Einv, M, n, batch, M * M * kC, 1.f / n, f->st));
+    SPE_TRY(launch_zmix_fwd(n, M, f->ym, f->train ? f->Xsave[l] : nullptr, f->w16 + f->off.R[l], f->Efwd, f->Einv,
+                            batch, f->st));
     SPE_TRY(launch_axis(f->ym, f->xrow, f->Einv, M, n, batch * n, M * kC, 1.f / n, f->st));
     return SPE_OK;
 }
@@ -242,6 +240,16 @@ void free_all(spe_fno *f)
 
 int spe::fno::net_n(const spe_fno *f) { return f->n; }
 cudaStream_t spe::fno::net_stream(const spe_fno *f) { return f->st; }
+
+int spe::fno::forward_on_stream(spe_fno *f, cudaStream_t st, const void *psi, const void *psi_b, void *psi_out,
+                                int batch)
+{
+    const cudaStream_t keep = f->st;
+    f->st = st;
+    const int rc = spe_fno_forward(f, psi, psi_b, psi_out, batch);
+    f->st = keep;
+    return rc;
+}
 
 extern "C" {
 
@@ -290,7 +298,7 @@ SPE_API int spe_fno_create(const spe_fno_config *cfg, spe_fno **out)
     ok(dalloc(f, &f->ym, B * n * M * M * kC));
     ok(dalloc(f, &f->Ybuf, B * M * M * M * kC));
     ok(dalloc(f, &f->Xbbuf, B * M * M * M * kC));
-    for (int l = 0; l < (f->train ? f->L : 1); ++l) ok(dalloc(f, &f->Xsave[l], B * M * M * M * kC));
+    for (int l = 0; l < (f->train ? f->L : 0); ++l) ok(dalloc(f, &f->Xsave[l], B * M * M * M * kC));
     if (f->train) ok(dalloc(f, &f->ubar, B * cells * kC));
     ok(dalloc(f, &f->partials, (size_t)kRowBlocks * kTopSeg));
     ok(dalloc(f, &f->dres, 8));

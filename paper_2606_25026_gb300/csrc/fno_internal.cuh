@@ -85,6 +85,9 @@ cudaError_t launch_proj_tc(const RowArgs &a, int cells, int grid, cudaStream_t s
 // out[o][m][i] = scale * sum_j mat[m][j] in[o][j][i], m < Mout, j < nin
 cudaError_t launch_axis(const float2 *in, float2 *out, const float2 *mat, int nin, int Mout, int O, int I,
                         float scale, cudaStream_t st);
+// fused z DFT + mixing + z inverse of one layer, in place over the y-stage buffer
+cudaError_t launch_zmix_fwd(int n, int M, float2 *A, float2 *Xsave, const __nv_bfloat16 *R, const float2 *Efwd,
+                            const float2 *Einv, int B, cudaStream_t st);
 cudaError_t launch_mix_fwd(int M, const float2 *X, float2 *Y, const __nv_bfloat16 *R, int B, cudaStream_t st);
 cudaError_t launch_mix_bwd(int M, const float2 *Ybar, const float2 *X, float2 *Xbar, const __nv_bfloat16 *R,
                            float *gradR, int B, cudaStream_t st);
@@ -109,6 +112,8 @@ namespace fno {
 // grid points per axis and stream of a network (fno.cu)
 int net_n(const spe_fno *f);
 cudaStream_t net_stream(const spe_fno *f);
+// spe_fno_forward issued on another stream (the caller serialises use of f)
+int forward_on_stream(spe_fno *f, cudaStream_t st, const void *psi, const void *psi_b, void *psi_out, int batch);
 
 }  // namespace fno
 }  // namespace spe

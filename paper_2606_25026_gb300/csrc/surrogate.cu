@@ -1,7 +1,11 @@
 // The judge of the FNO surrogate (include/spe_fno.h): propose psi K steps
 // ahead, check the proposal's mass and energy drift (and, when asked, its
 // error against the solver's own K steps), and fall back to the solver when a
-// check fails.  Built only from the public solver API and the network's API.
+// check fails.  Built from the public solver API and the network's API.
+//
+// The coarse step, the network and the proposal's energy run on a private
+// stream (the coarse grid's), so the energy of the current state, computed on
+// the grid's stream, overlaps them; the coarse grid steps without host syncs.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -21,7 +25,9 @@ struct spe_surrogate {
     double *partials, *out;
     unsigned int *counter;
     size_t ncells;
-    cudaStream_t st;
+    cudaStream_t st;      // the grids' stream (grid_cfg.cuda_stream)
+    cudaStream_t own;     // private stream of the coarse grid and the network
+    cudaEvent_t ready;
 };
 
 namespace {
@@ -35,6 +41,8 @@ void release(spe_surrogate *s)
     cudaFree(s->partials);
     cudaFree(s->out);
     cudaFree(s->counter);
+    if (s->ready) cudaEventDestroy(s->ready);
+    if (s->own) cudaStreamDestroy(s->own);
 }
 
 }  // namespace
@@ -55,11 +63,15 @@ SPE_API int spe_surrogate_create(const spe_config *grid_cfg, spe_fno *f, const s
     s->jc = *jc;
     s->st = (cudaStream_t)grid_cfg->cuda_stream;
     s->ncells = (size_t)grid_cfg->nx * grid_cfg->ny * grid_cfg->nz;
+    int rc = SPE_OK;
+    if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ready, cudaEventDisableTiming) != cudaSuccess)
+        rc = SPE_ECUDA;
     spe_config cc = *grid_cfg;
-    cc.flags |= SPE_NO_CFL_CHECK;
-    cc.flags &= ~SPE_ASYNC;
+    cc.flags |= SPE_NO_CFL_CHECK | SPE_ASYNC;
     cc.max_particles = 0;
-    int rc = spe_create_grid(&cc, nullptr, 0, &s->coarse);
+    cc.cuda_stream = s->own;
+    if (rc == SPE_OK) rc = spe_create_grid(&cc, nullptr, 0, &s->coarse);
     cudaError_t e = cudaSuccess;
     if (rc == SPE_OK) {
         e = cudaMalloc(&s->psi0, s->ncells * sizeof(float2));
@@ -99,20 +111,21 @@ SPE_API int spe_surrogate_advance(spe_surrogate *s, spe_grid *g, int K, double d
     if (np) return SPE_EINVAL;
     spe_judge_result r{};
     r.rel_l2 = -1.0;
-    // 1. the state and its energy
+    // 1. the state, handed to the private stream
     if ((rc = spe_get_psi(g, s->psi0, SPE_DEVICE))) return rc;
-    spe_energy_t e0{}, e1{};
-    if ((rc = spe_energy(g, &e0))) return rc;
-    // 2. the coarse step and the proposal
+    if (cudaEventRecord(s->ready, s->st) != cudaSuccess || cudaStreamWaitEvent(s->own, s->ready, 0) != cudaSuccess)
+        return SPE_ECUDA;
+    // 2. the coarse step and the proposal (private stream, no host sync)
     if ((rc = spe_set_ic(s->coarse, s->psi0, s->ncells, SPE_DEVICE))) return rc;
     if ((rc = spe_step(s->coarse, 1, K * dt))) return rc;
     if ((rc = spe_get_psi(s->coarse, s->psib, SPE_DEVICE))) return rc;
-    if ((rc = spe_sync(s->coarse))) return rc;
-    if ((rc = spe_fno_forward(s->f, s->psi0, s->psib, s->prop, 1))) return rc;
-    if ((rc = spe_fno_sync(s->f))) return rc;
-    // 3. drifts of the proposal
+    if ((rc = forward_on_stream(s->f, s->own, s->psi0, s->psib, s->prop, 1))) return rc;
     if ((rc = spe_set_ic(s->coarse, s->prop, s->ncells, SPE_DEVICE))) return rc;
+    // 3. the state's energy on the grid's stream meanwhile, then the proposal's
+    spe_energy_t e0{}, e1{};
+    if ((rc = spe_energy(g, &e0))) return rc;
     if ((rc = spe_energy(s->coarse, &e1))) return rc;
+    if ((rc = spe_fno_sync(s->f))) return rc;
     r.mass_drift = std::fabs(e1.mass - e0.mass) / std::fabs(e0.mass);
     r.energy_drift = std::fabs(e1.total - e0.total) / std::fabs(e0.total);
     const bool drift_ok = std::isfinite(r.mass_drift) && std::isfinite(r.energy_drift) &&
