@@ -76,15 +76,18 @@ cudaError_t launch_lift_bwd(int n, int M, bool fp32, const RowArgs &a, int grid,
 // tensor-core forward kernels, BF16 activations (fno_tc.cu)
 // mode: 0 = Fourier layer, 1 = last Fourier layer (no GELU, no next x DFT), 2 = lift
 constexpr int kTcTile = 4;          // rows per tensor-core tile
-constexpr int kTcBlocks = 304;      // 2 CTAs per SM (about 82 KB of shared memory each)
+constexpr int kTcBlocks = 456;      // 3 CTAs per SM (about 66 KB of shared memory each)
 constexpr int kProjBlocks = 1216;   // up to 8 CTAs per SM
 cudaError_t launch_layer_fwd_tc(int n, int M, int mode, const RowArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_proj_tc(const RowArgs &a, int cells, int grid, cudaStream_t st);
 
 // mode-space and elementwise kernels (fno_modes.cu)
-// out[o][m][i] = scale * sum_j mat[m][j] in[o][j][i], m < Mout, j < nin
-cudaError_t launch_axis(const float2 *in, float2 *out, const float2 *mat, int nin, int Mout, int O, int I,
-                        float scale, cudaStream_t st);
+// out[o][m][i] = scale * sum_j Mat[m][j] in[o][j][i] with Mat = Efwd [M][n]
+// (fwd: j < n, m < M) or Einv [n][M] (j < M, m < n); I a multiple of 64
+cudaError_t launch_axis(const float2 *in, float2 *out, int n, int M, bool fwd, int O, int I, float scale,
+                        cudaStream_t st);
+// the constant-memory copies of Efwd and Einv used by launch_axis
+cudaError_t upload_axis_tables(int n, int M, const float2 *Efwd, const float2 *Einv);
 // fused z DFT + mixing + z inverse of one layer, in place over the y-stage buffer
 cudaError_t launch_zmix_fwd(int n, int M, float2 *A, float2 *Xsave, const __nv_bfloat16 *R, const float2 *Efwd,
                             const float2 *Einv, int B, cudaStream_t st);

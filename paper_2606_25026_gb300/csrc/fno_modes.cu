@@ -9,46 +9,74 @@ namespace spe {
 namespace fno {
 namespace {
 
-constexpr int kAxisThreads = 128;
+// The DFT matrices of the y and z stages, for (n, M) in {64, 32} x {16, 8}:
+// Efwd [M][n] = e^{-2 pi i f(m) j / n}, Einv [n][M] = e^{+2 pi i f(m) j / n}.
+// Every thread of a warp reads the same entry at the same time, which the
+// constant cache serves as a broadcast.
+__constant__ float2 cEf64_16[16 * 64], cEi64_16[64 * 16], cEf64_8[8 * 64], cEi64_8[64 * 8];
+__constant__ float2 cEf32_16[16 * 32], cEi32_16[32 * 16], cEf32_8[8 * 32], cEi32_8[32 * 8];
 
-// out[o][m][i] = scale * sum_j mat[m][j] in[o][j][i] for m in this block's
-// MT outputs; threads run over i (contiguous), blocks over (i, o, m chunk).
-template <int NIN, int MT>
-__global__ void __launch_bounds__(kAxisThreads) axis_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
-                                                           const float2 *__restrict__ mat, int I, int Mout,
-                                                           float scale)
+template <int N, int M, bool FWD>
+__device__ __forceinline__ float2 emat(int idx)
 {
-    __shared__ float2 ms[MT][NIN];
-    const int o = blockIdx.y, m0 = blockIdx.z * MT;
-    for (int e = threadIdx.x; e < MT * NIN; e += kAxisThreads) ms[e / NIN][e % NIN] = mat[(size_t)m0 * NIN + e];
+    if constexpr (FWD) {
+        if constexpr (N == 64 && M == 16) return cEf64_16[idx];
+        else if constexpr (N == 64) return cEf64_8[idx];
+        else if constexpr (M == 16) return cEf32_16[idx];
+        else return cEf32_8[idx];
+    } else {
+        if constexpr (N == 64 && M == 16) return cEi64_16[idx];
+        else if constexpr (N == 64) return cEi64_8[idx];
+        else if constexpr (M == 16) return cEi32_16[idx];
+        else return cEi32_8[idx];
+    }
+}
+
+constexpr int kAxisThreads = 256;
+constexpr int kAxisCols = 64;      // inner indices per block
+
+// out[o][m][i] = scale * sum_j Mat[m][j] in[o][j][i], Mat = Efwd (FWD: j < n,
+// m < M) or Einv (inverse: j < M, m < n).  A block stages in[o][0..NIN)[i0,
+// i0 + 64) in shared memory (each input read once) and its four thread groups
+// (whole warps) each produce a quarter of the outputs for the 64 columns.
+template <int N, int M, bool FWD>
+__global__ void __launch_bounds__(kAxisThreads) axis_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
+                                                           int I, float scale)
+{
+    constexpr int NIN = FWD ? N : M, MOUT = FWD ? M : N, MT = MOUT / 4;
+    __shared__ float2 tile[NIN][kAxisCols];
+    const int o = blockIdx.y, i0 = blockIdx.x * kAxisCols;
+    const float2 *src = in + (size_t)o * NIN * I + i0;
+    for (int e = threadIdx.x; e < NIN * kAxisCols; e += kAxisThreads)
+        tile[e / kAxisCols][e % kAxisCols] = src[(size_t)(e / kAxisCols) * I + e % kAxisCols];
     __syncthreads();
-    const int i = blockIdx.x * kAxisThreads + threadIdx.x;
-    if (i >= I) return;
+    const int il = threadIdx.x % kAxisCols, grp = threadIdx.x / kAxisCols;
     float2 acc[MT];
 #pragma unroll
     for (int t = 0; t < MT; ++t) acc[t] = make_float2(0.f, 0.f);
-    const float2 *src = in + (size_t)o * NIN * I + i;
 #pragma unroll 4
     for (int j = 0; j < NIN; ++j) {
-        const float2 x = src[(size_t)j * I];
+        const float2 x = tile[j][il];
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
-            const float2 m = ms[t][j];
+            const float2 m = emat<N, M, FWD>((grp * MT + t) * NIN + j);
             acc[t].x = fmaf(m.x, x.x, fmaf(-m.y, x.y, acc[t].x));
             acc[t].y = fmaf(m.x, x.y, fmaf(m.y, x.x, acc[t].y));
         }
     }
-    float2 *dst = out + ((size_t)o * Mout + m0) * I + i;
+    float2 *dst = out + ((size_t)o * MOUT + grp * MT) * I + i0 + il;
 #pragma unroll
     for (int t = 0; t < MT; ++t) dst[(size_t)t * I] = make_float2(acc[t].x * scale, acc[t].y * scale);
 }
 
-template <int NIN, int MT>
-cudaError_t axis_run(const float2 *in, float2 *out, const float2 *mat, int Mout, int O, int I, float scale,
-                     cudaStream_t st)
+template <int N, int M>
+cudaError_t axis_nm(bool fwd, const float2 *in, float2 *out, int O, int I, float scale, cudaStream_t st)
 {
-    dim3 grid((I + kAxisThreads - 1) / kAxisThreads, O, Mout / MT);
-    axis_kernel<NIN, MT><<<grid, kAxisThreads, 0, st>>>(in, out, mat, I, Mout, scale);
+    dim3 grid(I / kAxisCols, O);
+    if (fwd)
+        axis_kernel<N, M, true><<<grid, kAxisThreads, 0, st>>>(in, out, I, scale);
+    else
+        axis_kernel<N, M, false><<<grid, kAxisThreads, 0, st>>>(in, out, I, scale);
     return cudaGetLastError();
 }
 
@@ -144,6 +172,16 @@ __global__ void __launch_bounds__(256) zmix_fwd_kernel(float2 *__restrict__ A, f
         ei[e / M][e % M] = Einv[e];
     }
     const float inv_n = 1.f / N;
+    // this warp's modes kz = warp, warp + 8: column lane of R[k], loaded before the batch loop
+    constexpr int KW = (M + 7) / 8;
+    __nv_bfloat162 rr[KW][kC];
+#pragma unroll
+    for (int q = 0; q < KW; ++q) {
+        const int kz = warp + 8 * q;
+        const __nv_bfloat162 *Rk = R + ((size_t)(kz < M ? kz : 0) * COLS + col) * kC * kC;
+#pragma unroll
+        for (int i = 0; i < kC; ++i) rr[q][i] = Rk[i * kC + lane];
+    }
     for (int b = 0; b < B; ++b) {
         __syncthreads();
         for (int e = threadIdx.x; e < N * kC; e += 256) {
@@ -163,12 +201,14 @@ __global__ void __launch_bounds__(256) zmix_fwd_kernel(float2 *__restrict__ A, f
             if (Xsave) Xsave[((size_t)b * K + (size_t)kz * COLS + col) * kC + lane] = acc;
         }
         __syncthreads();
-        for (int kz = warp; kz < M; kz += 8) {
-            const __nv_bfloat162 *Rk = R + ((size_t)kz * COLS + col) * kC * kC;
+#pragma unroll
+        for (int q = 0; q < KW; ++q) {
+            const int kz = warp + 8 * q;
+            if (kz >= M) break;
             float2 y = make_float2(0.f, 0.f);
-#pragma unroll 8
+#pragma unroll
             for (int i = 0; i < kC; ++i) {
-                const float2 r = __bfloat1622float2(Rk[i * kC + lane]);
+                const float2 r = __bfloat1622float2(rr[q][i]);
                 const float2 x = xs[kz][i];
                 y.x = fmaf(r.x, x.x, fmaf(-r.y, x.y, y.x));
                 y.y = fmaf(r.x, x.y, fmaf(r.y, x.x, y.y));
@@ -240,39 +280,29 @@ __global__ void __launch_bounds__(256) diff_norms_kernel(const float2 *__restric
 
 }  // namespace
 
-template <int NIN>
-cudaError_t axis_nin(int MT, const float2 *in, float2 *out, const float2 *mat, int Mout, int O, int I, float scale,
-                     cudaStream_t st)
+cudaError_t launch_axis(const float2 *in, float2 *out, int n, int M, bool fwd, int O, int I, float scale,
+                        cudaStream_t st)
 {
-    switch (MT) {
-        case 1: return axis_run<NIN, 1>(in, out, mat, Mout, O, I, scale, st);
-        case 2: return axis_run<NIN, 2>(in, out, mat, Mout, O, I, scale, st);
-        case 4: return axis_run<NIN, 4>(in, out, mat, Mout, O, I, scale, st);
-        case 8: return axis_run<NIN, 8>(in, out, mat, Mout, O, I, scale, st);
-        default: return axis_run<NIN, 16>(in, out, mat, Mout, O, I, scale, st);
-    }
+    if (I % kAxisCols) return cudaErrorInvalidValue;
+    if (n == 64 && M == 16) return axis_nm<64, 16>(fwd, in, out, O, I, scale, st);
+    if (n == 64 && M == 8) return axis_nm<64, 8>(fwd, in, out, O, I, scale, st);
+    if (n == 32 && M == 16) return axis_nm<32, 16>(fwd, in, out, O, I, scale, st);
+    if (n == 32 && M == 8) return axis_nm<32, 8>(fwd, in, out, O, I, scale, st);
+    return cudaErrorInvalidValue;
 }
 
-// Outputs per thread: as many as keep about 128 K threads in flight (the
-// contractions are short; latency, not arithmetic, bounds them), at most 16.
-int pick_mt(int Mout, long long OI)
+cudaError_t upload_axis_tables(int n, int M, const float2 *Efwd, const float2 *Einv)
 {
-    int mt = 16;
-    while (mt > 1 && (Mout % mt != 0 || OI * (Mout / mt) < (128ll << 10))) mt >>= 1;
-    return mt;
-}
-
-cudaError_t launch_axis(const float2 *in, float2 *out, const float2 *mat, int nin, int Mout, int O, int I,
-                        float scale, cudaStream_t st)
-{
-    const int mt = pick_mt(Mout, (long long)O * I);
-    switch (nin) {
-        case 64: return axis_nin<64>(mt, in, out, mat, Mout, O, I, scale, st);
-        case 32: return axis_nin<32>(mt, in, out, mat, Mout, O, I, scale, st);
-        case 16: return axis_nin<16>(mt, in, out, mat, Mout, O, I, scale, st);
-        case 8: return axis_nin<8>(mt, in, out, mat, Mout, O, I, scale, st);
-        default: return cudaErrorInvalidValue;
-    }
+    const size_t bytes = sizeof(float2) * (size_t)n * M;
+    const void *ef = nullptr, *ei = nullptr;
+    if (n == 64 && M == 16) { ef = cEf64_16; ei = cEi64_16; }
+    else if (n == 64 && M == 8) { ef = cEf64_8; ei = cEi64_8; }
+    else if (n == 32 && M == 16) { ef = cEf32_16; ei = cEi32_16; }
+    else if (n == 32 && M == 8) { ef = cEf32_8; ei = cEi32_8; }
+    else return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpyToSymbol(ef, Efwd, bytes);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(ei, Einv, bytes);
+    return e;
 }
 
 cudaError_t launch_zmix_fwd(int n, int M, float2 *A, float2 *Xsave, const __nv_bfloat16 *R, const float2 *Efwd,

@@ -105,8 +105,10 @@ struct LayerSmem {
     static constexpr int B1 = A1 + 128 * 128 * 2;             // [N][128]
     static constexpr int A2 = B1 + N * 128 * 2;               // [128][KM]
     static constexpr int B2 = A2 + 128 * KM * 2;              // [N][KM]
-    static constexpr int A3 = B2 + N * KM * 2;                // [128][N]
-    static constexpr int B3 = A3 + 128 * N * 2;               // [KM][N]
+    // A3 shares B1's bytes: B1 is last read by G1, A3 first written after G1 completes, and the
+    // next tile stages B1 only after G3 (which reads A3) has completed
+    static constexpr int A3 = B1;                             // [128][N] <= [N][128]
+    static constexpr int B3 = B2 + N * KM * 2;                // [KM][N]
     static constexpr int CTL = B3 + KM * N * 2;               // mbarrier, tmem base, phase
     static constexpr int BYTES = CTL + 64;
 };
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(kRowThreads) layer_fwd_tc_kernel(RowArgs a)
     float Pr[kFin];
 #pragma unroll
     for (int f = 0; f < kFin; ++f) Pr[f] = LIFT ? wload(a.w, a.oP + lane * kFin + f) : 0.f;
-    float *fs = reinterpret_cast<float *>(sm + S::B1);   // lift: features [kTile][N][4]
+    float *fs = reinterpret_cast<float *>(sm + S::A1);   // lift: features [kTile][N][4] (A1 unused)
     to_tensor_cores();
     const uint32_t tbase = ctl->tmem_base;
 
