@@ -204,10 +204,10 @@ int row_grid(int rows) { return rows < kRowBlocks ? rows : kRowBlocks; }
 int spectral_fwd(spe_fno *f, int l, int batch)
 {
     const int n = f->n, M = f->M;
-    SPE_TRY(launch_axis(f->xrow, f->ym, n, M, true, batch * n, M * kC, 1.f, f->st));
+    SPE_TRY(launch_axis(f->xrow, f->ym, f->Efwd, n, M, true, batch * n, M * kC, 1.f, f->st));
     SPE_TRY(launch_zmix_fwd(n, M, f->ym, f->train ? f->Xsave[l] : nullptr, f->w16 + f->off.R[l], f->Efwd, f->Einv,
                             batch, f->st));
-    SPE_TRY(launch_axis(f->ym, f->xrow, n, M, false, batch * n, M * kC, 1.f / n, f->st));
+    SPE_TRY(launch_axis(f->ym, f->xrow, f->Einv, n, M, false, batch * n, M * kC, 1.f / n, f->st));
     return SPE_OK;
 }
 
@@ -215,12 +215,12 @@ int spectral_fwd(spe_fno *f, int l, int batch)
 int spectral_bwd(spe_fno *f, int l, int batch)
 {
     const int n = f->n, M = f->M;
-    SPE_TRY(launch_axis(f->xrow, f->ym, n, M, true, batch * n, M * kC, 1.f / n, f->st));
-    SPE_TRY(launch_axis(f->ym, f->Ybuf, n, M, true, batch, M * M * kC, 1.f / n, f->st));
+    SPE_TRY(launch_axis(f->xrow, f->ym, f->Efwd, n, M, true, batch * n, M * kC, 1.f / n, f->st));
+    SPE_TRY(launch_axis(f->ym, f->Ybuf, f->Efwd, n, M, true, batch, M * M * kC, 1.f / n, f->st));
     SPE_TRY(launch_mix_bwd(M, f->Ybuf, f->Xsave[l], f->Xbbuf, f->w16 + f->off.R[l], f->grad + f->off.R[l], batch,
                            f->st));
-    SPE_TRY(launch_axis(f->Xbbuf, f->ym, n, M, false, batch, M * M * kC, 1.f, f->st));
-    SPE_TRY(launch_axis(f->ym, f->xrow, n, M, false, batch * n, M * kC, 1.f, f->st));
+    SPE_TRY(launch_axis(f->Xbbuf, f->ym, f->Einv, n, M, false, batch, M * M * kC, 1.f, f->st));
+    SPE_TRY(launch_axis(f->ym, f->xrow, f->Einv, n, M, false, batch * n, M * kC, 1.f, f->st));
     return SPE_OK;
 }
 
@@ -315,7 +315,6 @@ SPE_API int spe_fno_create(const spe_fno_config *cfg, spe_fno **out)
             }
         ok(cudaMemcpy(f->Efwd, Ef.data(), Ef.size() * sizeof(float2), cudaMemcpyHostToDevice));
         ok(cudaMemcpy(f->Einv, Ei.data(), Ei.size() * sizeof(float2), cudaMemcpyHostToDevice));
-        ok(upload_axis_tables((int)n, (int)M, Ef.data(), Ei.data()));
         std::vector<unsigned char> gimg, fimg;
         build_tc_images((int)n, (int)M, gimg, fimg);
         ok(cudaMemcpy(f->tcG, gimg.data(), gimg.size(), cudaMemcpyHostToDevice));

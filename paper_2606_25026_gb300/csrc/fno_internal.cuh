@@ -84,10 +84,8 @@ cudaError_t launch_proj_tc(const RowArgs &a, int cells, int grid, cudaStream_t s
 // mode-space and elementwise kernels (fno_modes.cu)
 // out[o][m][i] = scale * sum_j Mat[m][j] in[o][j][i] with Mat = Efwd [M][n]
 // (fwd: j < n, m < M) or Einv [n][M] (j < M, m < n); I a multiple of 64
-cudaError_t launch_axis(const float2 *in, float2 *out, int n, int M, bool fwd, int O, int I, float scale,
-                        cudaStream_t st);
-// the constant-memory copies of Efwd and Einv used by launch_axis
-cudaError_t upload_axis_tables(int n, int M, const float2 *Efwd, const float2 *Einv);
+cudaError_t launch_axis(const float2 *in, float2 *out, const float2 *mat, int n, int M, bool fwd, int O, int I,
+                        float scale, cudaStream_t st);
 // fused z DFT + mixing + z inverse of one layer, in place over the y-stage buffer
 cudaError_t launch_zmix_fwd(int n, int M, float2 *A, float2 *Xsave, const __nv_bfloat16 *R, const float2 *Efwd,
                             const float2 *Einv, int B, cudaStream_t st);

@@ -9,46 +9,26 @@ namespace spe {
 namespace fno {
 namespace {
 
-// The DFT matrices of the y and z stages, for (n, M) in {64, 32} x {16, 8}:
-// Efwd [M][n] = e^{-2 pi i f(m) j / n}, Einv [n][M] = e^{+2 pi i f(m) j / n}.
-// Every thread of a warp reads the same entry at the same time, which the
-// constant cache serves as a broadcast.
-__constant__ float2 cEf64_16[16 * 64], cEi64_16[64 * 16], cEf64_8[8 * 64], cEi64_8[64 * 8];
-__constant__ float2 cEf32_16[16 * 32], cEi32_16[32 * 16], cEf32_8[8 * 32], cEi32_8[32 * 8];
-
-template <int N, int M, bool FWD>
-__device__ __forceinline__ float2 emat(int idx)
-{
-    if constexpr (FWD) {
-        if constexpr (N == 64 && M == 16) return cEf64_16[idx];
-        else if constexpr (N == 64) return cEf64_8[idx];
-        else if constexpr (M == 16) return cEf32_16[idx];
-        else return cEf32_8[idx];
-    } else {
-        if constexpr (N == 64 && M == 16) return cEi64_16[idx];
-        else if constexpr (N == 64) return cEi64_8[idx];
-        else if constexpr (M == 16) return cEi32_16[idx];
-        else return cEi32_8[idx];
-    }
-}
-
 constexpr int kAxisThreads = 256;
 constexpr int kAxisCols = 64;      // inner indices per block
 
-// out[o][m][i] = scale * sum_j Mat[m][j] in[o][j][i], Mat = Efwd (FWD: j < n,
-// m < M) or Einv (inverse: j < M, m < n).  A block stages in[o][0..NIN)[i0,
-// i0 + 64) in shared memory (each input read once) and its four thread groups
-// (whole warps) each produce a quarter of the outputs for the 64 columns.
+// out[o][m][i] = scale * sum_j Mat[m][j] in[o][j][i], Mat = Efwd [M][n] (FWD:
+// j < n, m < M) or Einv [n][M] (inverse: j < M, m < n).  A block stages
+// in[o][0..NIN)[i0, i0 + 64) and the whole matrix in shared memory (each input
+// read once from memory); its four thread groups (whole warps, so matrix
+// reads are broadcasts) each produce a quarter of the outputs.
 template <int N, int M, bool FWD>
 __global__ void __launch_bounds__(kAxisThreads) axis_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
-                                                           int I, float scale)
+                                                           const float2 *__restrict__ mat, int I, float scale)
 {
     constexpr int NIN = FWD ? N : M, MOUT = FWD ? M : N, MT = MOUT / 4;
     __shared__ float2 tile[NIN][kAxisCols];
+    __shared__ float2 ms[MOUT][NIN];
     const int o = blockIdx.y, i0 = blockIdx.x * kAxisCols;
     const float2 *src = in + (size_t)o * NIN * I + i0;
     for (int e = threadIdx.x; e < NIN * kAxisCols; e += kAxisThreads)
         tile[e / kAxisCols][e % kAxisCols] = src[(size_t)(e / kAxisCols) * I + e % kAxisCols];
+    for (int e = threadIdx.x; e < MOUT * NIN; e += kAxisThreads) ms[e / NIN][e % NIN] = mat[e];
     __syncthreads();
     const int il = threadIdx.x % kAxisCols, grp = threadIdx.x / kAxisCols;
     float2 acc[MT];
@@ -59,7 +39,7 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(const float2 *__rest
         const float2 x = tile[j][il];
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
-            const float2 m = emat<N, M, FWD>((grp * MT + t) * NIN + j);
+            const float2 m = ms[grp * MT + t][j];
             acc[t].x = fmaf(m.x, x.x, fmaf(-m.y, x.y, acc[t].x));
             acc[t].y = fmaf(m.x, x.y, fmaf(m.y, x.x, acc[t].y));
         }
@@ -70,13 +50,14 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(const float2 *__rest
 }
 
 template <int N, int M>
-cudaError_t axis_nm(bool fwd, const float2 *in, float2 *out, int O, int I, float scale, cudaStream_t st)
+cudaError_t axis_nm(bool fwd, const float2 *in, float2 *out, const float2 *mat, int O, int I, float scale,
+                    cudaStream_t st)
 {
     dim3 grid(I / kAxisCols, O);
     if (fwd)
-        axis_kernel<N, M, true><<<grid, kAxisThreads, 0, st>>>(in, out, I, scale);
+        axis_kernel<N, M, true><<<grid, kAxisThreads, 0, st>>>(in, out, mat, I, scale);
     else
-        axis_kernel<N, M, false><<<grid, kAxisThreads, 0, st>>>(in, out, I, scale);
+        axis_kernel<N, M, false><<<grid, kAxisThreads, 0, st>>>(in, out, mat, I, scale);
     return cudaGetLastError();
 }
 
@@ -172,16 +153,6 @@ __global__ void __launch_bounds__(256) zmix_fwd_kernel(float2 *__restrict__ A, f
         ei[e / M][e % M] = Einv[e];
     }
     const float inv_n = 1.f / N;
-    // this warp's modes kz = warp, warp + 8: column lane of R[k], loaded before the batch loop
-    constexpr int KW = (M + 7) / 8;
-    __nv_bfloat162 rr[KW][kC];
-#pragma unroll
-    for (int q = 0; q < KW; ++q) {
-        const int kz = warp + 8 * q;
-        const __nv_bfloat162 *Rk = R + ((size_t)(kz < M ? kz : 0) * COLS + col) * kC * kC;
-#pragma unroll
-        for (int i = 0; i < kC; ++i) rr[q][i] = Rk[i * kC + lane];
-    }
     for (int b = 0; b < B; ++b) {
         __syncthreads();
         for (int e = threadIdx.x; e < N * kC; e += 256) {
@@ -201,14 +172,12 @@ __global__ void __launch_bounds__(256) zmix_fwd_kernel(float2 *__restrict__ A, f
             if (Xsave) Xsave[((size_t)b * K + (size_t)kz * COLS + col) * kC + lane] = acc;
         }
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < KW; ++q) {
-            const int kz = warp + 8 * q;
-            if (kz >= M) break;
+        for (int kz = warp; kz < M; kz += 8) {
+            const __nv_bfloat162 *Rk = R + ((size_t)kz * COLS + col) * kC * kC;
             float2 y = make_float2(0.f, 0.f);
-#pragma unroll
+#pragma unroll 8
             for (int i = 0; i < kC; ++i) {
-                const float2 r = __bfloat1622float2(rr[q][i]);
+                const float2 r = __bfloat1622float2(Rk[i * kC + lane]);
                 const float2 x = xs[kz][i];
                 y.x = fmaf(r.x, x.x, fmaf(-r.y, x.y, y.x));
                 y.y = fmaf(r.x, x.y, fmaf(r.y, x.x, y.y));
@@ -280,29 +249,15 @@ __global__ void __launch_bounds__(256) diff_norms_kernel(const float2 *__restric
 
 }  // namespace
 
-cudaError_t launch_axis(const float2 *in, float2 *out, int n, int M, bool fwd, int O, int I, float scale,
-                        cudaStream_t st)
+cudaError_t launch_axis(const float2 *in, float2 *out, const float2 *mat, int n, int M, bool fwd, int O, int I,
+                        float scale, cudaStream_t st)
 {
     if (I % kAxisCols) return cudaErrorInvalidValue;
-    if (n == 64 && M == 16) return axis_nm<64, 16>(fwd, in, out, O, I, scale, st);
-    if (n == 64 && M == 8) return axis_nm<64, 8>(fwd, in, out, O, I, scale, st);
-    if (n == 32 && M == 16) return axis_nm<32, 16>(fwd, in, out, O, I, scale, st);
-    if (n == 32 && M == 8) return axis_nm<32, 8>(fwd, in, out, O, I, scale, st);
+    if (n == 64 && M == 16) return axis_nm<64, 16>(fwd, in, out, mat, O, I, scale, st);
+    if (n == 64 && M == 8) return axis_nm<64, 8>(fwd, in, out, mat, O, I, scale, st);
+    if (n == 32 && M == 16) return axis_nm<32, 16>(fwd, in, out, mat, O, I, scale, st);
+    if (n == 32 && M == 8) return axis_nm<32, 8>(fwd, in, out, mat, O, I, scale, st);
     return cudaErrorInvalidValue;
-}
-
-cudaError_t upload_axis_tables(int n, int M, const float2 *Efwd, const float2 *Einv)
-{
-    const size_t bytes = sizeof(float2) * (size_t)n * M;
-    const void *ef = nullptr, *ei = nullptr;
-    if (n == 64 && M == 16) { ef = cEf64_16; ei = cEi64_16; }
-    else if (n == 64 && M == 8) { ef = cEf64_8; ei = cEi64_8; }
-    else if (n == 32 && M == 16) { ef = cEf32_16; ei = cEi32_16; }
-    else if (n == 32 && M == 8) { ef = cEf32_8; ei = cEi32_8; }
-    else return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemcpyToSymbol(ef, Efwd, bytes);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(ei, Einv, bytes);
-    return e;
 }
 
 cudaError_t launch_zmix_fwd(int n, int M, float2 *A, float2 *Xsave, const __nv_bfloat16 *R, const float2 *Efwd,
