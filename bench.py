@@ -75,10 +75,11 @@ def dist_env():
 
 
 def source_hash() -> str:
+    """Hash of the solver's CUDA sources (the surrogate's fno* and surrogate.cu files excluded)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_25026_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
+        if f.endswith((".cu", ".cuh")) and not f.startswith(("fno", "surrogate")):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 

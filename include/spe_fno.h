@@ -57,6 +57,7 @@ extern "C" {
 /* flags of spe_fno_config */
 #define SPE_FNO_TRAIN     (1 << 0)  /* keep activations for spe_fno_backward */
 #define SPE_FNO_ACT_FP32  (1 << 1)  /* store activations in FP32 instead of BF16 */
+#define SPE_FNO_NO_GRAPH  (1 << 2)  /* never replay the inference forward as a CUDA graph */
 
 typedef struct spe_fno spe_fno;
 
@@ -91,7 +92,10 @@ SPE_API int spe_fno_get_grads(spe_fno *f, float *grads, size_t count, int where)
 /* psi_out[b] = the proposal for (psi[b], psi_b[b]), b < batch.  psi_out may be
  * psi_b (in place).  With SPE_FNO_TRAIN the activations are kept for
  * spe_fno_backward.  Asynchronous on the stream.  SPE_EINVAL if batch is out
- * of [1, max_batch]. */
+ * of [1, max_batch].  Without SPE_FNO_TRAIN a call that repeats the previous
+ * call's buffers, batch and stream is captured once as a CUDA graph and
+ * replayed (results are bitwise the same; parameter updates need no
+ * re-capture since the kernels read the weights in place). */
 SPE_API int spe_fno_forward(spe_fno *f, const void *psi, const void *psi_b, void *psi_out, int batch);
 
 /* Gradient of the batch loss of the last forward against psi_target

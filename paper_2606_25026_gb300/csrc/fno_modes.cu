@@ -9,55 +9,46 @@ namespace spe {
 namespace fno {
 namespace {
 
-constexpr int kAxisThreads = 256;
-constexpr int kAxisCols = 64;      // inner indices per block
+constexpr int kAxisThreads = 128;
 
-// out[o][m][i] = scale * sum_j Mat[m][j] in[o][j][i], Mat = Efwd [M][n] (FWD:
-// j < n, m < M) or Einv [n][M] (inverse: j < M, m < n).  A block stages
-// in[o][0..NIN)[i0, i0 + 64) and the whole matrix in shared memory (each input
-// read once from memory); its four thread groups (whole warps, so matrix
-// reads are broadcasts) each produce a quarter of the outputs.
-template <int N, int M, bool FWD>
+// out[o][m][i] = scale * sum_j mat[m][j] in[o][j][i] for m in this block's
+// MT outputs; threads run over i (contiguous), blocks over (i, o, m chunk).
+template <int NIN, int MT>
 __global__ void __launch_bounds__(kAxisThreads) axis_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
-                                                           const float2 *__restrict__ mat, int I, float scale)
+                                                           const float2 *__restrict__ mat, int I, int Mout,
+                                                           float scale)
 {
-    constexpr int NIN = FWD ? N : M, MOUT = FWD ? M : N, MT = MOUT / 4;
-    __shared__ float2 tile[NIN][kAxisCols];
-    __shared__ float2 ms[MOUT][NIN];
-    const int o = blockIdx.y, i0 = blockIdx.x * kAxisCols;
-    const float2 *src = in + (size_t)o * NIN * I + i0;
-    for (int e = threadIdx.x; e < NIN * kAxisCols; e += kAxisThreads)
-        tile[e / kAxisCols][e % kAxisCols] = src[(size_t)(e / kAxisCols) * I + e % kAxisCols];
-    for (int e = threadIdx.x; e < MOUT * NIN; e += kAxisThreads) ms[e / NIN][e % NIN] = mat[e];
+    __shared__ float2 ms[MT][NIN];
+    const int o = blockIdx.y, m0 = blockIdx.z * MT;
+    for (int e = threadIdx.x; e < MT * NIN; e += kAxisThreads) ms[e / NIN][e % NIN] = mat[(size_t)m0 * NIN + e];
     __syncthreads();
-    const int il = threadIdx.x % kAxisCols, grp = threadIdx.x / kAxisCols;
+    const int i = blockIdx.x * kAxisThreads + threadIdx.x;
+    if (i >= I) return;
     float2 acc[MT];
 #pragma unroll
     for (int t = 0; t < MT; ++t) acc[t] = make_float2(0.f, 0.f);
+    const float2 *src = in + (size_t)o * NIN * I + i;
 #pragma unroll 4
     for (int j = 0; j < NIN; ++j) {
-        const float2 x = tile[j][il];
+        const float2 x = src[(size_t)j * I];
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
-            const float2 m = ms[grp * MT + t][j];
+            const float2 m = ms[t][j];
             acc[t].x = fmaf(m.x, x.x, fmaf(-m.y, x.y, acc[t].x));
             acc[t].y = fmaf(m.x, x.y, fmaf(m.y, x.x, acc[t].y));
         }
     }
-    float2 *dst = out + ((size_t)o * MOUT + grp * MT) * I + i0 + il;
+    float2 *dst = out + ((size_t)o * Mout + m0) * I + i;
 #pragma unroll
     for (int t = 0; t < MT; ++t) dst[(size_t)t * I] = make_float2(acc[t].x * scale, acc[t].y * scale);
 }
 
-template <int N, int M>
-cudaError_t axis_nm(bool fwd, const float2 *in, float2 *out, const float2 *mat, int O, int I, float scale,
-                    cudaStream_t st)
+template <int NIN, int MT>
+cudaError_t axis_run(const float2 *in, float2 *out, const float2 *mat, int Mout, int O, int I, float scale,
+                     cudaStream_t st)
 {
-    dim3 grid(I / kAxisCols, O);
-    if (fwd)
-        axis_kernel<N, M, true><<<grid, kAxisThreads, 0, st>>>(in, out, mat, I, scale);
-    else
-        axis_kernel<N, M, false><<<grid, kAxisThreads, 0, st>>>(in, out, mat, I, scale);
+    dim3 grid((I + kAxisThreads - 1) / kAxisThreads, O, Mout / MT);
+    axis_kernel<NIN, MT><<<grid, kAxisThreads, 0, st>>>(in, out, mat, I, Mout, scale);
     return cudaGetLastError();
 }
 
@@ -249,15 +240,45 @@ __global__ void __launch_bounds__(256) diff_norms_kernel(const float2 *__restric
 
 }  // namespace
 
+template <int NIN>
+cudaError_t axis_nin(int MT, const float2 *in, float2 *out, const float2 *mat, int Mout, int O, int I, float scale,
+                     cudaStream_t st)
+{
+    switch (MT) {
+        case 1: return axis_run<NIN, 1>(in, out, mat, Mout, O, I, scale, st);
+        case 2: return axis_run<NIN, 2>(in, out, mat, Mout, O, I, scale, st);
+        case 4: return axis_run<NIN, 4>(in, out, mat, Mout, O, I, scale, st);
+        case 8: return axis_run<NIN, 8>(in, out, mat, Mout, O, I, scale, st);
+        default: return axis_run<NIN, 16>(in, out, mat, Mout, O, I, scale, st);
+    }
+}
+
+// Outputs per thread: as many as keep about 128 K threads in flight (the
+// contractions are short; latency, not arithmetic, bounds them), at most 16.
+int pick_mt(int Mout, long long OI)
+{
+    int mt = 16;
+    while (mt > 1 && (Mout % mt != 0 || OI * (Mout / mt) < (128ll << 10))) mt >>= 1;
+    return mt;
+}
+
+cudaError_t launch_axis_any(const float2 *in, float2 *out, const float2 *mat, int nin, int Mout, int O, int I,
+                            float scale, cudaStream_t st)
+{
+    const int mt = pick_mt(Mout, (long long)O * I);
+    switch (nin) {
+        case 64: return axis_nin<64>(mt, in, out, mat, Mout, O, I, scale, st);
+        case 32: return axis_nin<32>(mt, in, out, mat, Mout, O, I, scale, st);
+        case 16: return axis_nin<16>(mt, in, out, mat, Mout, O, I, scale, st);
+        case 8: return axis_nin<8>(mt, in, out, mat, Mout, O, I, scale, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_axis(const float2 *in, float2 *out, const float2 *mat, int n, int M, bool fwd, int O, int I,
                         float scale, cudaStream_t st)
 {
-    if (I % kAxisCols) return cudaErrorInvalidValue;
-    if (n == 64 && M == 16) return axis_nm<64, 16>(fwd, in, out, mat, O, I, scale, st);
-    if (n == 64 && M == 8) return axis_nm<64, 8>(fwd, in, out, mat, O, I, scale, st);
-    if (n == 32 && M == 16) return axis_nm<32, 16>(fwd, in, out, mat, O, I, scale, st);
-    if (n == 32 && M == 8) return axis_nm<32, 8>(fwd, in, out, mat, O, I, scale, st);
-    return cudaErrorInvalidValue;
+    return launch_axis_any(in, out, mat, fwd ? n : M, fwd ? M : n, O, I, scale, st);
 }
 
 cudaError_t launch_zmix_fwd(int n, int M, float2 *A, float2 *Xsave, const __nv_bfloat16 *R, const float2 *Efwd,

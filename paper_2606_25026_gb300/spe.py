@@ -46,6 +46,7 @@ EXPORTED = (
 SPE_FNO_WIDTH, SPE_FNO_HIDDEN = 32, 64
 SPE_FNO_TRAIN = 1 << 0
 SPE_FNO_ACT_FP32 = 1 << 1
+SPE_FNO_NO_GRAPH = 1 << 2
 
 
 class SpeError(RuntimeError):
@@ -454,14 +455,15 @@ class Fno:
     device, shaped (batch, n, n, n) or (n, n, n)."""
 
     def __init__(self, n=64, layers=4, modes=16, max_batch=1, train=False, act_fp32=False, inv_A=1.0,
-                 sigma=1.0, stream=None):
+                 sigma=1.0, stream=None, graph=True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libspe needs a CUDA device; there is no CPU fallback")
         self._lib = load_library()
         self.n, self.layers, self.modes, self.max_batch = int(n), int(layers), int(modes), int(max_batch)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        flags = (SPE_FNO_TRAIN if train else 0) | (SPE_FNO_ACT_FP32 if act_fp32 else 0)
+        flags = ((SPE_FNO_TRAIN if train else 0) | (SPE_FNO_ACT_FP32 if act_fp32 else 0)
+                 | (0 if graph else SPE_FNO_NO_GRAPH))
         self.cfg = spe_fno_config(self.n, self.layers, self.modes, self.max_batch, flags, float(inv_A),
                                   float(sigma), ctypes.c_void_p(self.stream.cuda_stream))
         cnt = ctypes.c_size_t()
