@@ -287,6 +287,19 @@ def fno_flops(n=64, C=32, M=16, H=64, L=4, fin=4):
     return 2.0 * (lift + (L - 1) * (spectral + row) + spectral + last_row)
 
 
+def fno_bytes(kind, n=64, C=32, M=16, batch=1):
+    """Algorithmic HBM bytes of one inference launch of an FNO kernel kind (BF16 activations,
+    complex64 spectral buffers, BF16 weights)."""
+    act = batch * n ** 3 * C * 2            # one BF16 activation tensor
+    xrow = batch * n * n * M * C * 8        # x-stage buffer
+    ystage = batch * n * M * M * C * 8      # y-stage buffer
+    field = batch * n ** 3 * 8              # one complex64 field
+    r = M ** 3 * C * C * 4                  # one layer's BF16 complex R
+    return {"fno_lift": 2 * field + act + xrow, "fno_layer": 2 * act + 2 * xrow, "fno_last_layer": 2 * act + xrow,
+            "fno_projection": act + 2 * field, "fno_y_dft": xrow + ystage, "fno_z_mix": 2 * ystage + r,
+            "fno_y_idft": ystage + xrow}[kind]
+
+
 def surrogate_arm(args, rank, world, local):
     """The FNO surrogate against the plain solver on 64^3 halos: train on solver trajectories,
     then advance held-out grids by K = 16 steps through the judge (proposal accepted when its mass
@@ -363,7 +376,7 @@ def surrogate_arm(args, rank, world, local):
     value = world * cells * K * steps / t_sur
     plain = world * cells * K * steps / t_plain
 
-    # the forward pass alone (batch 1), CUDA events on the network's stream
+    # the forward pass alone (batch 1, graph replay), CUDA events on the network's stream
     x1, b1 = test.psi[:1].contiguous(), test.psi_b[:1].contiguous()
     o1 = torch.empty_like(x1)
     for _ in range(3):
@@ -378,7 +391,20 @@ def surrogate_arm(args, rank, world, local):
     ev1.synchronize()
     fwd_s = ev0.elapsed_time(ev1) * 1e-3 / reps
     flops = fno_flops()
-    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    # per-kernel CUDA events (profile mode launches directly, without the graph)
+    pnet = spe.Fno(n=n, layers=4, modes=16, max_batch=1, inv_A=inv_A, sigma=sigma, profile=True)
+    pnet.set_params(params)
+    for _ in range(3):
+        pnet.forward(x1, b1, out=o1)
+    pnet.profile_read()
+    for _ in range(reps):
+        pnet.forward(x1, b1, out=o1)
+    prof = pnet.profile_read()
+    pnet.destroy()
+    dom = max(prof, key=lambda k: prof[k][1])
+    dom_launch_s = prof[dom][1] * 1e-3 / prof[dom][0]
+    peak, peak_kind = measured_peak()
+    dom_bytes = fno_bytes(dom)
 
     # e2e: the initial field from pinned host memory and the result back to it, every advance
     h_in = test.psi[:min(S, 16)].cpu().pin_memory()
@@ -413,10 +439,16 @@ def surrogate_arm(args, rank, world, local):
                   "energy_drift_max": float(max(v["energy_drift"] for v in verdicts))},
         "training": {"loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "seconds": t_train,
                      "pair_generation_s": t_gen, "sigma": sigma},
-        "roofline": {"bound": "alu", "kernel": "fno forward (all kernels, batch 1)", "achieved": flops / fwd_s / 1e12,
-                     "peak": alu_peak, "unit": "TFLOP/s", "frac": flops / fwd_s / 1e12 / alu_peak,
-                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz", "traffic": None,
-                     "flops_per_launch": flops, "avg_launch_ms": fwd_s * 1e3},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_bytes / dom_launch_s / 1e9, "peak": peak,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                     else "fallback 6800 GB/s", "unit": "GB/s",
+                     "frac": dom_bytes / dom_launch_s / 1e9 / peak, "traffic": None,
+                     "bytes_per_launch": dom_bytes, "avg_launch_ms": dom_launch_s * 1e3,
+                     "launches": prof[dom][0]},
+        "fno_forward": {"ms": fwd_s * 1e3, "flops": flops, "tflops_fp32_equivalent": flops / fwd_s / 1e12,
+                        "kernels": {k: {"launches": v[0], "ms_per_launch": round(v[1] / max(1, v[0]), 4),
+                                        "GBs": round(fno_bytes(k) / (v[1] * 1e-3 / max(1, v[0])) / 1e9, 1)}
+                                    for k, v in prof.items()}},
         "gpu_launches": int(fno_launches),
         "clocks": clk,
         "e2e": {"value": world * cells * K * ke / t_e2e, "unit": "cell-steps/s", "steps": ke,

@@ -58,6 +58,7 @@ extern "C" {
 #define SPE_FNO_TRAIN     (1 << 0)  /* keep activations for spe_fno_backward */
 #define SPE_FNO_ACT_FP32  (1 << 1)  /* store activations in FP32 instead of BF16 */
 #define SPE_FNO_NO_GRAPH  (1 << 2)  /* never replay the inference forward as a CUDA graph */
+#define SPE_FNO_PROFILE   (1 << 3)  /* CUDA events around every kernel (no graph replay) */
 
 typedef struct spe_fno spe_fno;
 
@@ -114,6 +115,12 @@ SPE_API int spe_fno_adam(spe_fno *f, double lr, double beta1, double beta2, doub
  * of a tensor-core kernel gave up since the last call (the affected results
  * are wrong; the flag is cleared). */
 SPE_API int spe_fno_sync(spe_fno *f);
+
+/* With SPE_FNO_PROFILE: per kernel kind, the launches and summed CUDA-event
+ * milliseconds since the last call (then reset).  Fills up to cap entries of
+ * names / launches / ms and returns the number of kinds (>= 0), or a negative
+ * status (SPE_ESTATE without the flag).  Synchronises the stream. */
+SPE_API int spe_fno_profile_read(spe_fno *f, const char **names, unsigned long long *launches, double *ms, int cap);
 
 /* Kernels launched by this network since creation (or the last reset). */
 SPE_API int spe_fno_launch_count(spe_fno *f, unsigned long long *count_out, int reset);

@@ -24,6 +24,16 @@
 
 using namespace spe::fno;
 
+// kernel kinds of the per-kernel event profile (SPE_FNO_PROFILE)
+enum FnoKind {
+    FK_LIFT, FK_LAYER, FK_LAST, FK_PROJ, FK_Y_FWD, FK_ZMIX, FK_Y_INV, FK_TOP_BWD, FK_START_BWD, FK_LAYER_BWD,
+    FK_LIFT_BWD, FK_AXIS_BWD, FK_MIX_BWD, FK_REDUCE, FK_ADAM, FK_COUNT
+};
+static const char *kFnoKindNames[FK_COUNT] = {
+    "fno_lift", "fno_layer", "fno_last_layer", "fno_projection", "fno_y_dft", "fno_z_mix", "fno_y_idft",
+    "fno_top_bwd", "fno_start_bwd", "fno_layer_bwd", "fno_lift_bwd", "fno_axis_bwd", "fno_mix_bwd",
+    "fno_reduce", "fno_adam"};
+
 struct spe_fno {
     spe_fno_config cfg;
     int n, L, M, B;
@@ -55,6 +65,12 @@ struct spe_fno {
     cudaStream_t key_st;
     int key_seen;
     unsigned long long graph_launches;
+    // per-kernel profile: event pairs recorded around each launch, read back by spe_fno_profile_read
+    bool profile;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
+    std::vector<cudaEvent_t> prof_free;
+    unsigned long long prof_launches[FK_COUNT];
+    double prof_ms[FK_COUNT];
 };
 
 namespace {
@@ -202,21 +218,50 @@ RowArgs base_args(spe_fno *f, int batch)
 
 int row_grid(int rows) { return rows < kRowBlocks ? rows : kRowBlocks; }
 
-#define SPE_TRY(expr)                              \
-    do {                                           \
-        cudaError_t _e = (expr);                   \
-        if (_e != cudaSuccess) return SPE_ECUDA;   \
-        ++f->launches;                             \
+cudaEvent_t prof_event(spe_fno *f)
+{
+    if (!f->prof_free.empty()) {
+        cudaEvent_t e = f->prof_free.back();
+        f->prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// one kernel launch of kind k: counted, and bracketed by events in profile mode
+template <typename F>
+cudaError_t run_kind(spe_fno *f, int k, F &&launch)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (f->profile) {
+        e0 = prof_event(f);
+        e1 = prof_event(f);
+        cudaEventRecord(e0, f->st);
+    }
+    const cudaError_t e = launch();
+    if (f->profile) {
+        cudaEventRecord(e1, f->st);
+        f->prof_pending.push_back({k, {e0, e1}});
+    }
+    ++f->launches;
+    return e;
+}
+
+#define SPE_TRY(kind, expr)                                                     \
+    do {                                                                        \
+        if (run_kind(f, kind, [&] { return (expr); }) != cudaSuccess) return SPE_ECUDA; \
     } while (0)
 
 // forward stages of layer l's spectral path: x-row buffer (x DFT of v_l) -> x-row buffer (y IDFT)
 int spectral_fwd(spe_fno *f, int l, int batch)
 {
     const int n = f->n, M = f->M;
-    SPE_TRY(launch_axis(f->xrow, f->ym, f->Efwd, n, M, true, batch * n, M * kC, 1.f, f->st));
-    SPE_TRY(launch_zmix_fwd(n, M, f->ym, f->train ? f->Xsave[l] : nullptr, f->w16 + f->off.R[l], f->Efwd, f->Einv,
+    SPE_TRY(FK_Y_FWD, launch_axis(f->xrow, f->ym, f->Efwd, n, M, true, batch * n, M * kC, 1.f, f->st));
+    SPE_TRY(FK_ZMIX, launch_zmix_fwd(n, M, f->ym, f->train ? f->Xsave[l] : nullptr, f->w16 + f->off.R[l], f->Efwd, f->Einv,
                             batch, f->st));
-    SPE_TRY(launch_axis(f->ym, f->xrow, f->Einv, n, M, false, batch * n, M * kC, 1.f / n, f->st));
+    SPE_TRY(FK_Y_INV, launch_axis(f->ym, f->xrow, f->Einv, n, M, false, batch * n, M * kC, 1.f / n, f->st));
     return SPE_OK;
 }
 
@@ -224,18 +269,18 @@ int spectral_fwd(spe_fno *f, int l, int batch)
 int spectral_bwd(spe_fno *f, int l, int batch)
 {
     const int n = f->n, M = f->M;
-    SPE_TRY(launch_axis(f->xrow, f->ym, f->Efwd, n, M, true, batch * n, M * kC, 1.f / n, f->st));
-    SPE_TRY(launch_axis(f->ym, f->Ybuf, f->Efwd, n, M, true, batch, M * M * kC, 1.f / n, f->st));
-    SPE_TRY(launch_mix_bwd(M, f->Ybuf, f->Xsave[l], f->Xbbuf, f->w16 + f->off.R[l], f->grad + f->off.R[l], batch,
+    SPE_TRY(FK_AXIS_BWD, launch_axis(f->xrow, f->ym, f->Efwd, n, M, true, batch * n, M * kC, 1.f / n, f->st));
+    SPE_TRY(FK_AXIS_BWD, launch_axis(f->ym, f->Ybuf, f->Efwd, n, M, true, batch, M * M * kC, 1.f / n, f->st));
+    SPE_TRY(FK_MIX_BWD, launch_mix_bwd(M, f->Ybuf, f->Xsave[l], f->Xbbuf, f->w16 + f->off.R[l], f->grad + f->off.R[l], batch,
                            f->st));
-    SPE_TRY(launch_axis(f->Xbbuf, f->ym, f->Einv, n, M, false, batch, M * M * kC, 1.f, f->st));
-    SPE_TRY(launch_axis(f->ym, f->xrow, f->Einv, n, M, false, batch * n, M * kC, 1.f, f->st));
+    SPE_TRY(FK_AXIS_BWD, launch_axis(f->Xbbuf, f->ym, f->Einv, n, M, false, batch, M * M * kC, 1.f, f->st));
+    SPE_TRY(FK_AXIS_BWD, launch_axis(f->ym, f->xrow, f->Einv, n, M, false, batch * n, M * kC, 1.f, f->st));
     return SPE_OK;
 }
 
 int reduce_into(spe_fno *f, int seg, int nblk, float *dst, int ndst, double *extra)
 {
-    SPE_TRY(launch_reduce_partials(f->partials, seg, nblk, dst, ndst, extra, f->st));
+    SPE_TRY(FK_REDUCE, launch_reduce_partials(f->partials, seg, nblk, dst, ndst, extra, f->st));
     return SPE_OK;
 }
 
@@ -283,6 +328,7 @@ SPE_API int spe_fno_create(const spe_fno_config *cfg, spe_fno **out)
     f->train = (cfg->flags & SPE_FNO_TRAIN) != 0;
     f->fp32 = (cfg->flags & SPE_FNO_ACT_FP32) != 0;
     f->st = (cudaStream_t)cfg->cuda_stream;
+    f->profile = (cfg->flags & SPE_FNO_PROFILE) != 0;
     f->off = make_offsets(f->L, f->M);
     f->nparams = f->off.total;
     const size_t n = f->n, M = f->M, B = f->B, cells = n * n * n;
@@ -351,6 +397,11 @@ SPE_API int spe_fno_destroy(spe_fno *f)
     cudaStreamSynchronize(f->st);
     if (f->fwd_exec) cudaGraphExecDestroy(f->fwd_exec);
     if (f->cap_st) cudaStreamDestroy(f->cap_st);
+    for (auto &p : f->prof_pending) {
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    for (auto e : f->prof_free) cudaEventDestroy(e);
     free_all(f);
     delete f;
     return SPE_OK;
@@ -401,9 +452,9 @@ static int issue_forward(spe_fno *f, const void *psi, const void *psi_b, void *p
     const bool tc = !f->fp32;
     const int tiles = rows / kTcTile, tgrid = tiles < kTcBlocks ? tiles : kTcBlocks;
     if (tc)
-        SPE_TRY(launch_layer_fwd_tc(n, M, 2, a, tgrid, f->st));
+        SPE_TRY(FK_LIFT, launch_layer_fwd_tc(n, M, 2, a, tgrid, f->st));
     else
-        SPE_TRY(launch_lift_fwd(n, M, f->fp32, a, grid, f->st));
+        SPE_TRY(FK_LIFT, launch_lift_fwd(n, M, f->fp32, a, grid, f->st));
     for (int l = 0; l < L; ++l) {
         int rc = spectral_fwd(f, l, batch);
         if (rc) return rc;
@@ -417,9 +468,9 @@ static int issue_forward(spe_fno *f, const void *psi, const void *psi_b, void *p
         b.oW = f->off.W[l];
         b.ob = f->off.b[l];
         if (tc) {
-            SPE_TRY(launch_layer_fwd_tc(n, M, l == L - 1 ? 1 : 0, b, tgrid, f->st));
+            SPE_TRY(l == L - 1 ? FK_LAST : FK_LAYER, launch_layer_fwd_tc(n, M, l == L - 1 ? 1 : 0, b, tgrid, f->st));
         } else {
-            SPE_TRY(launch_layer_fwd(n, M, f->fp32, l == L - 1, b, grid, f->st));
+            SPE_TRY(l == L - 1 ? FK_LAST : FK_LAYER, launch_layer_fwd(n, M, f->fp32, l == L - 1, b, grid, f->st));
         }
     }
     if (tc) {
@@ -428,7 +479,7 @@ static int issue_forward(spe_fno *f, const void *psi, const void *psi_b, void *p
         p.psib = (const float2 *)psi_b;
         p.out = (float2 *)psi_out;
         const int cells = rows * n, ptiles = cells / 128;
-        SPE_TRY(launch_proj_tc(p, cells, ptiles < kProjBlocks ? ptiles : kProjBlocks, f->st));
+        SPE_TRY(FK_PROJ, launch_proj_tc(p, cells, ptiles < kProjBlocks ? ptiles : kProjBlocks, f->st));
     }
     return SPE_OK;
 }
@@ -472,7 +523,7 @@ SPE_API int spe_fno_forward(spe_fno *f, const void *psi, const void *psi_b, void
     int rc;
     const bool same = f->key_psi == psi && f->key_psib == psi_b && f->key_out == psi_out &&
                       f->key_batch == batch && f->key_st == f->st;
-    if (f->train || (f->cfg.flags & SPE_FNO_NO_GRAPH)) {
+    if (f->train || f->profile || (f->cfg.flags & SPE_FNO_NO_GRAPH)) {
         if ((rc = issue_forward(f, psi, psi_b, psi_out, batch))) return rc;
     } else if (same && f->key_seen >= 1) {
         // a repeated call: replay (capturing it on its second occurrence)
@@ -510,11 +561,11 @@ SPE_API int spe_fno_backward(spe_fno *f, const void *psi_target, double *loss_ou
     a.target = (const float2 *)psi_target;
     a.vin = v_buf(f, L);
     a.loss_scale = (float)(2.0 / (f->cfg.sigma * (double)batch * (double)n * n * n));
-    SPE_TRY(launch_top_bwd(n, f->fp32, a, grid, f->st));
+    SPE_TRY(FK_TOP_BWD, launch_top_bwd(n, f->fp32, a, grid, f->st));
     int rc = reduce_into(f, kTopSeg, grid, f->grad + f->off.Q1, kTopSeg - 1, f->dres);
     if (rc) return rc;
     a.vin = v_buf(f, L - 1);
-    SPE_TRY(launch_grad_start(n, M, f->fp32, a, grid, f->st));
+    SPE_TRY(FK_START_BWD, launch_grad_start(n, M, f->fp32, a, grid, f->st));
     if ((rc = reduce_into(f, kLayerSeg, grid, f->grad + f->off.W[L - 1], kLayerSeg, nullptr))) return rc;
     for (int l = L - 1; l >= 0; --l) {
         if ((rc = spectral_bwd(f, l, batch))) return rc;
@@ -525,10 +576,10 @@ SPE_API int spe_fno_backward(spe_fno *f, const void *psi_target, double *loss_ou
         if (l >= 1) {
             b.vin = v_buf(f, l - 1);
             b.upre = u_buf(f, l - 1);
-            SPE_TRY(launch_layer_bwd(n, M, f->fp32, b, grid, f->st));
+            SPE_TRY(FK_LAYER_BWD, launch_layer_bwd(n, M, f->fp32, b, grid, f->st));
             if ((rc = reduce_into(f, kLayerSeg, grid, f->grad + f->off.W[l - 1], kLayerSeg, nullptr))) return rc;
         } else {
-            SPE_TRY(launch_lift_bwd(n, M, f->fp32, b, grid, f->st));
+            SPE_TRY(FK_LIFT_BWD, launch_lift_bwd(n, M, f->fp32, b, grid, f->st));
             if ((rc = reduce_into(f, kLiftSeg, grid, f->grad + f->off.P, kLiftSeg, nullptr))) return rc;
         }
     }
@@ -550,7 +601,7 @@ SPE_API int spe_fno_adam(spe_fno *f, double lr, double beta1, double beta2, doub
     f->adam_t++;
     const double c1 = 1.0 / (1.0 - std::pow(beta1, (double)f->adam_t));
     const double c2 = 1.0 / (1.0 - std::pow(beta2, (double)f->adam_t));
-    SPE_TRY(launch_adam(f->master, f->am, f->av, f->grad, f->w16, f->nparams, (float)lr, (float)beta1,
+    SPE_TRY(FK_ADAM, launch_adam(f->master, f->am, f->av, f->grad, f->w16, f->nparams, (float)lr, (float)beta1,
                         (float)beta2, (float)eps, (float)c1, (float)c2, f->st));
     return SPE_OK;
 }
@@ -567,6 +618,31 @@ SPE_API int spe_fno_sync(spe_fno *f)
         return SPE_ETIMEOUT;
     }
     return SPE_OK;
+}
+
+SPE_API int spe_fno_profile_read(spe_fno *f, const char **names, unsigned long long *launches, double *ms, int cap)
+{
+    if (!f || cap < 0 || (cap && (!names || !launches || !ms))) return SPE_EINVAL;
+    if (!f->profile) return SPE_ESTATE;
+    if (cudaStreamSynchronize(f->st) != cudaSuccess) return SPE_ECUDA;
+    for (auto &p : f->prof_pending) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, p.second.first, p.second.second);
+        f->prof_ms[p.first] += t;
+        f->prof_launches[p.first] += 1;
+        f->prof_free.push_back(p.second.first);
+        f->prof_free.push_back(p.second.second);
+    }
+    f->prof_pending.clear();
+    const int n = cap < FK_COUNT ? cap : FK_COUNT;
+    for (int k = 0; k < n; ++k) {
+        names[k] = kFnoKindNames[k];
+        launches[k] = f->prof_launches[k];
+        ms[k] = f->prof_ms[k];
+        f->prof_launches[k] = 0;
+        f->prof_ms[k] = 0.0;
+    }
+    return FK_COUNT;
 }
 
 SPE_API int spe_fno_launch_count(spe_fno *f, unsigned long long *count_out, int reset)

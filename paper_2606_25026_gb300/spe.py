@@ -38,7 +38,7 @@ EXPORTED = (
     # include/spe_fno.h
     "spe_fno_param_count", "spe_fno_create", "spe_fno_destroy", "spe_fno_set_params", "spe_fno_get_params",
     "spe_fno_get_grads", "spe_fno_forward", "spe_fno_backward", "spe_fno_adam", "spe_fno_sync",
-    "spe_fno_launch_count",
+    "spe_fno_profile_read", "spe_fno_launch_count",
     "spe_surrogate_create", "spe_surrogate_destroy", "spe_surrogate_advance",
 )
 
@@ -47,6 +47,7 @@ SPE_FNO_WIDTH, SPE_FNO_HIDDEN = 32, 64
 SPE_FNO_TRAIN = 1 << 0
 SPE_FNO_ACT_FP32 = 1 << 1
 SPE_FNO_NO_GRAPH = 1 << 2
+SPE_FNO_PROFILE = 1 << 3
 
 
 class SpeError(RuntimeError):
@@ -143,6 +144,8 @@ def load_library(path: str = LIB_PATH):
         "spe_fno_backward": (I, [P, P, ctypes.POINTER(D)]),
         "spe_fno_adam": (I, [P, D, D, D, D]),
         "spe_fno_sync": (I, [P]),
+        "spe_fno_profile_read": (I, [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_ulonglong),
+                                     ctypes.POINTER(D), I]),
         "spe_fno_launch_count": (I, [P, ctypes.POINTER(ctypes.c_ulonglong), I]),
         "spe_surrogate_create": (I, [ctypes.POINTER(spe_config), P, ctypes.POINTER(spe_judge_config),
                                      ctypes.POINTER(P)]),
@@ -455,7 +458,7 @@ class Fno:
     device, shaped (batch, n, n, n) or (n, n, n)."""
 
     def __init__(self, n=64, layers=4, modes=16, max_batch=1, train=False, act_fp32=False, inv_A=1.0,
-                 sigma=1.0, stream=None, graph=True):
+                 sigma=1.0, stream=None, graph=True, profile=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libspe needs a CUDA device; there is no CPU fallback")
@@ -463,7 +466,7 @@ class Fno:
         self.n, self.layers, self.modes, self.max_batch = int(n), int(layers), int(modes), int(max_batch)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         flags = ((SPE_FNO_TRAIN if train else 0) | (SPE_FNO_ACT_FP32 if act_fp32 else 0)
-                 | (0 if graph else SPE_FNO_NO_GRAPH))
+                 | (0 if graph else SPE_FNO_NO_GRAPH) | (SPE_FNO_PROFILE if profile else 0))
         self.cfg = spe_fno_config(self.n, self.layers, self.modes, self.max_batch, flags, float(inv_A),
                                   float(sigma), ctypes.c_void_p(self.stream.cuda_stream))
         cnt = ctypes.c_size_t()
@@ -541,6 +544,17 @@ class Fno:
 
     def sync(self):
         _check(self._lib.spe_fno_sync(self._h), "spe_fno_sync")
+
+    def profile_read(self) -> dict:
+        """{kernel kind: (launches, summed CUDA-event ms)} since the last read (profile mode)."""
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        launches = (ctypes.c_ulonglong * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = self._lib.spe_fno_profile_read(self._h, names, launches, ms, cap)
+        if n < 0:
+            _check(n, "spe_fno_profile_read")
+        return {names[i].decode(): (launches[i], ms[i]) for i in range(min(n, cap)) if launches[i]}
 
     def launch_count(self, reset=False) -> int:
         out = ctypes.c_ulonglong()

@@ -242,3 +242,21 @@ def test_graph_replay_matches_direct_forward(spe):
     assert np.array_equal(outs["direct"], outs["graphed"])
     assert np.array_equal(outs["direct2"], outs["graphed2"])
     assert not np.array_equal(outs["direct"], outs["direct2"])
+
+
+def test_profile_mode_counts_kernels(spe):
+    import torch
+    shape = fo.FnoShape(n=32, modes=16, layers=2)
+    net = spe.Fno(n=32, layers=2, modes=16, sigma=0.05, profile=True)
+    net.set_params(params_for(shape, seed=3))
+    psis, pbs, _ = problem(32, 1, seed=4)
+    P, B = to_dev(psis), to_dev(pbs)
+    o = torch.empty_like(B)
+    for _ in range(3):
+        net.forward(P, B, out=o)
+    prof = net.profile_read()
+    assert prof["fno_layer"][0] == 3 and prof["fno_last_layer"][0] == 3 and prof["fno_z_mix"][0] == 6
+    assert all(ms > 0 for _, ms in prof.values())
+    assert net.profile_read() == {}
+    with pytest.raises(spe.SpeError):
+        spe.Fno(n=32, layers=1, modes=8, sigma=0.1).profile_read()
