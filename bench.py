@@ -508,6 +508,7 @@ def main():
     g.set_ic(torch.from_numpy(psi).cuda())
     if nstar:
         g.add_particles(torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda(), torch.from_numpy(mass).cuda())
+    tiles = g.autotune() if not args.no_autotune else None
     g.step(args.warmup, dt)
     g.sync()
     g.profile_read()
@@ -551,7 +552,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": [nx, ny, nz], "n_star": nstar, "dt": dt,
-                   "precision": args.prec,
+                   "precision": args.prec, "strided_tile_widths_yz": tiles,
                    "l2": f"working set {g.workspace.numel() / 2**20:.0f} MiB > 129 MB L2 (no flush needed)",
                    "parallelism": f"{world} independent replica(s)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -579,6 +580,8 @@ def main():
         o_psi = torch.empty(psi.shape, dtype=torch.complex64).pin_memory()
         o_pos = np.empty((nstar, 3), np.float32)
         ge = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, flags=prec_flag, stream=stream)
+        if not args.no_autotune:
+            ge.autotune()
         ke = max(1, min(args.steps, 200))
         # warm the path once
         ge.set_ic(h_psi)

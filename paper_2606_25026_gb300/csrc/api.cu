@@ -1221,13 +1221,17 @@ int autotune_grid(spe_grid *g, float2 *scratch)
                 continue;
             }
         }
-        float t16 = 0.f, t32 = 0.f;
-        int rc = time_tile(g, axis, 16, scratch, &t16);
-        if (rc) return rc;
-        int best = 16;
-        if ((size_t)g->n[axis] * 32 * sizeof(float2) <= 227 * 1024) {
-            if ((rc = time_tile(g, axis, 32, scratch, &t32))) return rc;
-            if (t32 < t16) best = 32;
+        // candidate widths 8, 16, 32 columns (32 only where the tile fits in shared memory)
+        float best_ms = 0.f;
+        int best = 16, rc;
+        for (int tile : {16, 8, 32}) {
+            if (tile == 32 && (size_t)g->n[axis] * 32 * sizeof(float2) > 227 * 1024) continue;
+            float ms = 0.f;
+            if ((rc = time_tile(g, axis, tile, scratch, &ms))) return rc;
+            if (tile == 16 || ms < best_ms) {
+                best = tile;
+                best_ms = ms;
+            }
         }
         g->stile[axis] = best;
         std::lock_guard<std::mutex> lock(g_tune_mu);

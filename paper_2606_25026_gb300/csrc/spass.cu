@@ -4,8 +4,10 @@
 
 namespace spe {
 
+cudaError_t launch_spass_t8(int n, const SParams &p, cudaStream_t st, int *blocks_out);
 cudaError_t launch_spass_t16(int n, const SParams &p, cudaStream_t st, int *blocks_out);
 cudaError_t launch_spass_t32(int n, const SParams &p, cudaStream_t st, int *blocks_out);
+cudaError_t setup_spass_attributes_t8();
 cudaError_t setup_spass_attributes_t16();
 cudaError_t setup_spass_attributes_t32();
 cudaError_t launch_spass_tc(int n, const SParams &p, cudaStream_t st, int *blocks_out);
@@ -13,19 +15,24 @@ cudaError_t setup_tc_attributes();
 
 int spass_default_tile(int n) { return n >= 256 ? 16 : 32; }
 
-bool spass_tile_ok(int n, int tile) { return tile == 16 || (tile == 32 && (size_t)n * 32 * 8 <= 227 * 1024); }
+bool spass_tile_ok(int n, int tile)
+{
+    return tile == 8 || tile == 16 || (tile == 32 && (size_t)n * 32 * 8 <= 227 * 1024);
+}
 
 cudaError_t launch_spass(int n, const SParams &p, cudaStream_t st, int *blocks_out)
 {
     if (p.tc && (n == 256 || n == 512)) return launch_spass_tc(n, p, st, blocks_out);
     int tw = p.tile ? p.tile : spass_default_tile(n);
     if (!spass_tile_ok(n, tw)) tw = 16;
+    if (tw == 8) return launch_spass_t8(n, p, st, blocks_out);
     return tw == 16 ? launch_spass_t16(n, p, st, blocks_out) : launch_spass_t32(n, p, st, blocks_out);
 }
 
 cudaError_t setup_spass_attributes()
 {
-    cudaError_t e = setup_spass_attributes_t16();
+    cudaError_t e = setup_spass_attributes_t8();
+    if (e == cudaSuccess) e = setup_spass_attributes_t16();
     if (e == cudaSuccess) e = setup_spass_attributes_t32();
     if (e == cudaSuccess) e = setup_tc_attributes();
     return e;
