@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--fno-train", type=int, default=2000, help="fno64: training trajectories")
     ap.add_argument("--fno-test", type=int, default=200, help="fno64: held-out trajectories")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--grid", default=None,
+                    help="NXxNYxNZ: run the workload's initial-condition family on this grid instead "
+                         "(profiling cases; the stars keep their count)")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "split16"],
                     help="split16: radix-16 DFT stages of 256/512-point axes on the tensor cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -157,9 +160,10 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def make_inputs(workload):
+def make_inputs(workload, grid=None):
     from paper_2606_25026_gb300 import inputs
-    psi, pos, vel, mass, dt, _ = inputs.make_workload(workload)
+    n = tuple(int(v) for v in grid.lower().split("x")) if grid else None
+    psi, pos, vel, mass, dt, _ = inputs.make_workload(workload, n=n)
     return (psi.astype(np.complex64), pos.astype(np.float32), vel.astype(np.float32), mass.astype(np.float32),
             float(dt))
 
@@ -489,7 +493,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_2606_25026_gb300 import spe
 
-    psi, pos, vel, mass, dt = make_inputs(args.workload)
+    psi, pos, vel, mass, dt = make_inputs(args.workload, args.grid)
     nz, ny, nx = psi.shape
     ncells = psi.size
     nstar = len(mass)

@@ -23,9 +23,7 @@
 namespace spe {
 
 template <int N, bool TC = false> struct XCfg {
-    // rows per tile: 8 for lines of 512 and more keeps the tile and its staging area near 53 KB, so
-    // four CTAs share an SM and overlap each other's load, transform and store phases
-    static constexpr int T = (N >= 512 && !TC) ? 8 : 16;
+    static constexpr int T = 16;
     static constexpr int TP = T + 1;
     static constexpr int NT = (N * T / 8 >= 256) ? 256 : ((N * T / 8 >= 128) ? 128 : 64);
     // tile + aux; aux holds T real rows, or T half-spectrum rows of N/2 + 1 complex while staging
