@@ -24,7 +24,11 @@ cudaError_t setup_spass_attributes_t32()
     if constexpr (tile_fits<n>(32))                                                                   \
         if (e == cudaSuccess)                                                                            \
             e = cudaFuncSetAttribute(spass_kernel<n, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)SCfg<n, 32>::smem);
+                                     (int)SCfg<n, 32>::smem);                                     \
+    if constexpr (pipe_fits<n, 32>())                                                                 \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaFuncSetAttribute(spass_pipe_kernel<n, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     (int)(2 * SCfg<n, 32>::base));
     SPE_FOR_EACH_N(X)
 #undef X
     return e;
