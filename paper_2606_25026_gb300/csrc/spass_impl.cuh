@@ -147,112 +147,13 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC>::NT) spass_kernel(SParams p)
     if constexpr (TC) tc_teardown(*tcs);
 }
 
-// Persistent, double-buffered form of the FP32 strided pass (all flag sets but
-// the kinetic diagnostic): each CTA walks tiles blockIdx.x, blockIdx.x +
-// gridDim.x, ...; the asynchronous loads of its next tile are in flight while
-// the current one is transformed and stored, so memory traffic continues
-// through the shared-memory FFT phase of every CTA.
-template <int N, int TW>
-__global__ void __launch_bounds__(SCfg<N, TW>::NT) spass_pipe_kernel(SParams p, int ntx)
-{
-    constexpr int T = SCfg<N, TW>::T, TP = SCfg<N, TW>::TP, NT = SCfg<N, TW>::NT, HT = T / 2;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float2 *buf0 = reinterpret_cast<float2 *>(smem_raw);
-    float2 *buf1 = buf0 + N * TP;
-    __shared__ float4 colfac[T];
-    __shared__ float colk2[T];
-    const int tid = threadIdx.x;
-    const int flags = p.flags;
-    const int total = ntx * p.batches;
-
-    auto issue = [&](int t, float2 *tile) {
-        const int c0 = (t % ntx) * T, b = t / ntx;
-        const float2 *base = p.data + (size_t)b * p.bstride + c0;
-        for (int idx = tid; idx < N * HT; idx += NT) {
-            const int n = idx / HT, q = idx % HT;
-            if (c0 + 2 * q < p.W) cp_async16(&tile[n * TP + 2 * q], base + (size_t)n * p.S + 2 * q);
-            else *reinterpret_cast<float4 *>(&tile[n * TP + 2 * q]) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        cp_async_commit();
-    };
-
-    int t = blockIdx.x;
-    if (t < total) issue(t, buf0);
-    float2 *cur = buf0, *nxt = buf1;
-    for (; t < total; t += gridDim.x) {
-        const int c0 = (t % ntx) * T, b = t / ntx;
-        const int tn = t + gridDim.x;
-        if (tn < total) issue(tn, nxt);
-        if (tid < T) {
-            const int c = c0 + tid;
-            if (flags & S_DRIFT)
-                colfac[tid] = (c < p.W) ? __ldg(&p.dxy[(size_t)b * p.dxy_pitch + c]) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (flags & S_POISSON) colk2[tid] = (c < p.W) ? __ldg(&p.colk2[c]) + __ldg(&p.batchk2[b]) : 0.f;
-        }
-        if (tn < total) cp_async_wait_group<1>();
-        else cp_async_wait_group<0>();
-        __syncthreads();
-        if ((flags & (S_FWD | S_INV)) == (S_FWD | S_INV) && (flags & (S_DRIFT | S_POISSON))) {
-            if (flags & S_DRIFT) tile_fft_fwd_op_inv<N, T, TP, NT>(cur, p.tw, DriftOp{colfac, p.ez});
-            else tile_fft_fwd_op_inv<N, T, TP, NT>(cur, p.tw, PoissonOp{colk2, p.linek2, p.poisson * p.norm});
-        } else {
-            if (flags & S_FWD) tile_fft<N, T, TP, NT, -1>(cur, p.tw);
-            if (flags & S_INV) tile_fft<N, T, TP, NT, +1>(cur, p.tw);
-        }
-        float2 *base = p.data + (size_t)b * p.bstride + c0;
-        for (int idx = tid; idx < N * HT; idx += NT) {
-            const int n = idx / HT, q = idx % HT;
-            if (c0 + 2 * q < p.W)
-                *reinterpret_cast<float4 *>(base + (size_t)n * p.S + 2 * q) =
-                    *reinterpret_cast<const float4 *>(&cur[n * TP + 2 * q]);
-        }
-        // every thread is done with cur (and with colfac / colk2) before the next iteration
-        // issues loads into it
-        __syncthreads();
-        float2 *tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-    }
-}
-
 // widths that fit in shared memory for length N
 template <int N> constexpr bool tile_fits(int tw) { return (size_t)N * tw * sizeof(float2) <= 227 * 1024; }
-
-template <int N, int TW> constexpr bool pipe_fits() { return 2 * SCfg<N, TW>::base <= 227 * 1024; }
-
-// resident CTAs per SM of the double-buffered kernel (queried once per instance)
-template <int N, int TW>
-static int pipe_blocks_per_sm()
-{
-    static int cached = -1;
-    if (cached < 0) {
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spass_pipe_kernel<N, TW>, SCfg<N, TW>::NT,
-                                                          2 * SCfg<N, TW>::base) != cudaSuccess || nb < 1)
-            nb = 1;
-        cached = nb;
-    }
-    return cached;
-}
 
 template <int N, int TW, bool TC = false>
 static cudaError_t launch_s_nt(const SParams &p, cudaStream_t st, int *blocks_out)
 {
-    const int ntx = (p.W + TW - 1) / TW;
-    if constexpr (!TC && pipe_fits<N, TW>()) {
-        if (!(p.flags & S_KIN)) {
-            int dev = 0, sms = 152;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int total = ntx * p.batches;
-            int grid = pipe_blocks_per_sm<N, TW>() * sms;
-            if (grid > total) grid = total;
-            if (blocks_out) *blocks_out = grid;
-            spass_pipe_kernel<N, TW><<<grid, SCfg<N, TW>::NT, 2 * SCfg<N, TW>::base, st>>>(p, ntx);
-            return cudaGetLastError();
-        }
-    }
-    dim3 grid(ntx, p.batches);
+    dim3 grid((p.W + TW - 1) / TW, p.batches);
     if (blocks_out) *blocks_out = grid.x * grid.y;
     spass_kernel<N, TW, TC><<<grid, SCfg<N, TW, TC>::NT, SCfg<N, TW, TC>::smem, st>>>(p);
     return cudaGetLastError();

@@ -24,11 +24,7 @@ cudaError_t setup_spass_attributes_t16()
     if constexpr (tile_fits<n>(16))                                                                   \
         if (e == cudaSuccess)                                                                            \
             e = cudaFuncSetAttribute(spass_kernel<n, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)SCfg<n, 16>::smem);                                     \
-    if constexpr (pipe_fits<n, 16>())                                                                 \
-        if (e == cudaSuccess)                                                                            \
-            e = cudaFuncSetAttribute(spass_pipe_kernel<n, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)(2 * SCfg<n, 16>::base));
+                                     (int)SCfg<n, 16>::smem);
     SPE_FOR_EACH_N(X)
 #undef X
     return e;

@@ -24,11 +24,7 @@ cudaError_t setup_spass_attributes_t32()
     if constexpr (tile_fits<n>(32))                                                                   \
         if (e == cudaSuccess)                                                                            \
             e = cudaFuncSetAttribute(spass_kernel<n, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)SCfg<n, 32>::smem);                                     \
-    if constexpr (pipe_fits<n, 32>())                                                                 \
-        if (e == cudaSuccess)                                                                            \
-            e = cudaFuncSetAttribute(spass_pipe_kernel<n, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)(2 * SCfg<n, 32>::base));
+                                     (int)SCfg<n, 32>::smem);
     SPE_FOR_EACH_N(X)
 #undef X
     return e;

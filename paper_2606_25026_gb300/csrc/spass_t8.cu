@@ -24,11 +24,7 @@ cudaError_t setup_spass_attributes_t8()
     if constexpr (tile_fits<n>(8))                                                                   \
         if (e == cudaSuccess)                                                                            \
             e = cudaFuncSetAttribute(spass_kernel<n, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)SCfg<n, 8>::smem);                                     \
-    if constexpr (pipe_fits<n, 8>())                                                                 \
-        if (e == cudaSuccess)                                                                            \
-            e = cudaFuncSetAttribute(spass_pipe_kernel<n, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)(2 * SCfg<n, 8>::base));
+                                     (int)SCfg<n, 8>::smem);
     SPE_FOR_EACH_N(X)
 #undef X
     return e;
