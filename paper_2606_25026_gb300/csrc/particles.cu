@@ -15,6 +15,8 @@
 // which threads run: the step stays bitwise reproducible.
 #include "spe_internal.cuh"
 
+#include <climits>
+
 namespace spe {
 
 struct Cic {
@@ -44,51 +46,128 @@ __device__ __forceinline__ float wrap_pos(float x, float L)
     return x - L * floorf((x + 0.5f * L) / L);
 }
 
-__global__ void particles_kernel(PParams p)
+// Shared-memory boxes of the tiled path: the Phi nodes the block's kick
+// stencils touch, or the deposit nodes of its stars.  Stars are kept sorted by
+// 4^3 cell blocks, so a block of 256 consecutive stars usually covers one or
+// two cell blocks and its box is small; a block whose box does not fit (stars
+// spread out, or on both sides of the periodic boundary) uses global memory.
+constexpr int kPartThreads = 256;
+constexpr int kBoxBytes = 16384;
+constexpr int kBoxPhi = kBoxBytes / 4;     // floats
+constexpr int kBoxDep = kBoxBytes / 8;     // 64-bit counters
+
+// Block-wide min and max of three integers over the live threads; results
+// in out[0..2] (min) and out[3..5] (max).  All threads of the block call it.
+__device__ __forceinline__ void block_minmax3(int a, int b, int c, bool live, int (*red)[kPartThreads / 32],
+                                              int *out)
 {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int v[6] = {live ? a : INT_MAX, live ? b : INT_MAX, live ? c : INT_MAX,
+                live ? a : INT_MIN, live ? b : INT_MIN, live ? c : INT_MIN};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        v[q] = __reduce_min_sync(0xffffffffu, v[q]);
+        v[q + 3] = __reduce_max_sync(0xffffffffu, v[q + 3]);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) red[q][warp] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int q = threadIdx.x;
+        int r = red[q][0];
+        for (int w = 1; w < kPartThreads / 32; ++w) r = q < 3 ? min(r, red[q][w]) : max(r, red[q][w]);
+        out[q] = r;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPartThreads) particles_kernel(PParams p)
+{
+    __shared__ __align__(16) unsigned char box_raw[kBoxBytes];
+    __shared__ int red[6][kPartThreads / 32];
+    __shared__ int bb[6];
+    float *sphi = reinterpret_cast<float *>(box_raw);
+    unsigned long long *sdep = reinterpret_cast<unsigned long long *>(box_raw);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.n) return;
-    float x = p.x[i], y = p.y[i], z = p.z[i];
-    float vx = p.vx[i], vy = p.vy[i], vz = p.vz[i];
+    const bool live = i < p.n;
+    float x = 0.f, y = 0.f, z = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+    if (live) {
+        x = p.x[i];
+        y = p.y[i];
+        z = p.z[i];
+        vx = p.vx[i];
+        vy = p.vy[i];
+        vz = p.vz[i];
+    }
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     if (p.flags & PK_KICK) {
         const Cic cx = cic_axis(x, 0.5f * p.Lx, p.inv_dx, nx);
         const Cic cy = cic_axis(y, 0.5f * p.Ly, p.inv_dy, ny);
         const Cic cz = cic_axis(z, 0.5f * p.Lz, p.inv_dz, nz);
+        // the stencil of a star spans nodes i0 - 1 .. i0 + 2 on each axis
+        block_minmax3(cx.i0, cy.i0, cz.i0, live, red, bb);
+        const int ox = bb[0] - 1, oy = bb[1] - 1, oz = bb[2] - 1;
+        const int ex = bb[3] - bb[0] + 4, ey = bb[4] - bb[1] + 4, ez = bb[5] - bb[2] + 4;
+        const bool tiled = (long long)ex * ey * ez <= kBoxPhi;
+        if (tiled) {
+            for (int v = threadIdx.x; v < ex * ey * ez; v += kPartThreads) {
+                const int a = v % ex, b = (v / ex) % ey, c = v / (ex * ey);
+                sphi[v] = __ldg(&p.phi[((size_t)wrapi(oz + c, nz) * ny + wrapi(oy + b, ny)) * nx + wrapi(ox + a, nx)]);
+            }
+            __syncthreads();
+        }
         float gx = 0.f, gy = 0.f, gz = 0.f;
+        if (live) {
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int k = c ? cz.i1 : cz.i0;
-            const float wz = c ? cz.w1 : cz.w0;
+            for (int c = 0; c < 2; ++c) {
+                const int k = c ? cz.i1 : cz.i0;
+                const int ku = cz.i0 + c;     // unwrapped
+                const float wz = c ? cz.w1 : cz.w0;
 #pragma unroll
-            for (int bb = 0; bb < 2; ++bb) {
-                const int j = bb ? cy.i1 : cy.i0;
-                const float wy = bb ? cy.w1 : cy.w0;
+                for (int b2 = 0; b2 < 2; ++b2) {
+                    const int j = b2 ? cy.i1 : cy.i0;
+                    const int ju = cy.i0 + b2;
+                    const float wy = b2 ? cy.w1 : cy.w0;
 #pragma unroll
-                for (int a = 0; a < 2; ++a) {
-                    const int ii = a ? cx.i1 : cx.i0;
-                    const float w = (a ? cx.w1 : cx.w0) * wy * wz;
-                    const size_t plane = (size_t)k * ny;
-                    const float *row = p.phi + (plane + j) * nx;
-                    const float dphix = __ldg(&row[wrapi(ii + 1, nx)]) - __ldg(&row[wrapi(ii - 1, nx)]);
-                    const float dphiy = __ldg(&p.phi[(plane + wrapi(j + 1, ny)) * nx + ii]) -
-                                        __ldg(&p.phi[(plane + wrapi(j - 1, ny)) * nx + ii]);
-                    const float dphiz = __ldg(&p.phi[((size_t)wrapi(k + 1, nz) * ny + j) * nx + ii]) -
-                                        __ldg(&p.phi[((size_t)wrapi(k - 1, nz) * ny + j) * nx + ii]);
-                    gx -= w * dphix;
-                    gy -= w * dphiy;
-                    gz -= w * dphiz;
+                    for (int a = 0; a < 2; ++a) {
+                        const int ii = a ? cx.i1 : cx.i0;
+                        const int iu = cx.i0 + a;
+                        const float w = (a ? cx.w1 : cx.w0) * wy * wz;
+                        float dphix, dphiy, dphiz;
+                        if (tiled) {
+                            auto at = [&](int uu, int vv, int ww) {
+                                return sphi[((ww - oz) * ey + (vv - oy)) * ex + (uu - ox)];
+                            };
+                            dphix = at(iu + 1, ju, ku) - at(iu - 1, ju, ku);
+                            dphiy = at(iu, ju + 1, ku) - at(iu, ju - 1, ku);
+                            dphiz = at(iu, ju, ku + 1) - at(iu, ju, ku - 1);
+                        } else {
+                            const size_t plane = (size_t)k * ny;
+                            const float *row = p.phi + (plane + j) * nx;
+                            dphix = __ldg(&row[wrapi(ii + 1, nx)]) - __ldg(&row[wrapi(ii - 1, nx)]);
+                            dphiy = __ldg(&p.phi[(plane + wrapi(j + 1, ny)) * nx + ii]) -
+                                    __ldg(&p.phi[(plane + wrapi(j - 1, ny)) * nx + ii]);
+                            dphiz = __ldg(&p.phi[((size_t)wrapi(k + 1, nz) * ny + j) * nx + ii]) -
+                                    __ldg(&p.phi[((size_t)wrapi(k - 1, nz) * ny + j) * nx + ii]);
+                        }
+                        gx -= w * dphix;
+                        gy -= w * dphiy;
+                        gz -= w * dphiz;
+                    }
                 }
             }
+            vx += p.kick * gx * p.gx_scale;
+            vy += p.kick * gy * p.gy_scale;
+            vz += p.kick * gz * p.gz_scale;
+            p.vx[i] = vx;
+            p.vy[i] = vy;
+            p.vz[i] = vz;
         }
-        vx += p.kick * gx * p.gx_scale;
-        vy += p.kick * gy * p.gy_scale;
-        vz += p.kick * gz * p.gz_scale;
-        p.vx[i] = vx;
-        p.vy[i] = vy;
-        p.vz[i] = vz;
+        __syncthreads();   // the box is reused below
     }
-    if (p.flags & PK_DRIFT) {
+    if ((p.flags & PK_DRIFT) && live) {
         x = wrap_pos(x + vx * p.drift, p.Lx);
         y = wrap_pos(y + vy * p.drift, p.Ly);
         z = wrap_pos(z + vz * p.drift, p.Lz);
@@ -100,21 +179,51 @@ __global__ void particles_kernel(PParams p)
         const Cic cx = cic_axis(x, 0.5f * p.Lx, p.inv_dx, nx);
         const Cic cy = cic_axis(y, 0.5f * p.Ly, p.inv_dy, ny);
         const Cic cz = cic_axis(z, 0.5f * p.Lz, p.inv_dz, nz);
-        const float mq = p.m[i] * p.inv_quantum;
+        // a star deposits to nodes i0 .. i0 + 1 on each axis
+        block_minmax3(cx.i0, cy.i0, cz.i0, live, red, bb);
+        const int ox = bb[0], oy = bb[1], oz = bb[2];
+        const int ex = bb[3] - bb[0] + 2, ey = bb[4] - bb[1] + 2, ez = bb[5] - bb[2] + 2;
+        const int vol = ex * ey * ez;
+        const bool tiled = (long long)ex * ey * ez <= kBoxDep;
+        if (tiled) {
+            for (int v = threadIdx.x; v < vol; v += kPartThreads) sdep[v] = 0ull;
+            __syncthreads();
+        }
+        if (live) {
+            const float mq = p.m[i] * p.inv_quantum;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int k = c ? cz.i1 : cz.i0;
-            const float wz = c ? cz.w1 : cz.w0;
+            for (int c = 0; c < 2; ++c) {
+                const int k = c ? cz.i1 : cz.i0;
+                const float wz = c ? cz.w1 : cz.w0;
 #pragma unroll
-            for (int bb = 0; bb < 2; ++bb) {
-                const int j = bb ? cy.i1 : cy.i0;
-                const float wyz = (bb ? cy.w1 : cy.w0) * wz;
-                unsigned long long *row =
-                    reinterpret_cast<unsigned long long *>(p.dep) + ((size_t)k * ny + j) * nx;
-                const long long q0 = llrintf(mq * cx.w0 * wyz);
-                const long long q1 = llrintf(mq * cx.w1 * wyz);
-                if (q0) atomicAdd(&row[cx.i0], (unsigned long long)q0);
-                if (q1) atomicAdd(&row[cx.i1], (unsigned long long)q1);
+                for (int b2 = 0; b2 < 2; ++b2) {
+                    const int j = b2 ? cy.i1 : cy.i0;
+                    const float wyz = (b2 ? cy.w1 : cy.w0) * wz;
+                    const long long q0 = llrintf(mq * cx.w0 * wyz);
+                    const long long q1 = llrintf(mq * cx.w1 * wyz);
+                    if (tiled) {
+                        unsigned long long *srow =
+                            sdep + ((cz.i0 + c - oz) * ey + (cy.i0 + b2 - oy)) * ex + (cx.i0 - ox);
+                        if (q0) atomicAdd(&srow[0], (unsigned long long)q0);
+                        if (q1) atomicAdd(&srow[1], (unsigned long long)q1);
+                    } else {
+                        unsigned long long *row =
+                            reinterpret_cast<unsigned long long *>(p.dep) + ((size_t)k * ny + j) * nx;
+                        if (q0) atomicAdd(&row[cx.i0], (unsigned long long)q0);
+                        if (q1) atomicAdd(&row[cx.i1], (unsigned long long)q1);
+                    }
+                }
+            }
+        }
+        if (tiled) {
+            __syncthreads();
+            unsigned long long *dep = reinterpret_cast<unsigned long long *>(p.dep);
+            for (int v = threadIdx.x; v < vol; v += kPartThreads) {
+                const unsigned long long q = sdep[v];
+                if (q) {
+                    const int a = v % ex, b = (v / ex) % ey, c = v / (ex * ey);
+                    atomicAdd(&dep[((size_t)wrapi(oz + c, nz) * ny + wrapi(oy + b, ny)) * nx + wrapi(ox + a, nx)], q);
+                }
             }
         }
     }
@@ -123,8 +232,7 @@ __global__ void particles_kernel(PParams p)
 cudaError_t launch_particles(const PParams &p, cudaStream_t st)
 {
     if (p.n <= 0) return cudaSuccess;
-    const int nt = 256;
-    particles_kernel<<<(p.n + nt - 1) / nt, nt, 0, st>>>(p);
+    particles_kernel<<<(p.n + kPartThreads - 1) / kPartThreads, kPartThreads, 0, st>>>(p);
     return cudaGetLastError();
 }
 
