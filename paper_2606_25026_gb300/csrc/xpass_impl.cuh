@@ -22,12 +22,18 @@
 
 namespace spe {
 
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+
 template <int N, bool TC = false> struct XCfg {
     static constexpr int T = 16;
     static constexpr int TP = T + 1;
+    static constexpr int HP = T / 2 + 1;   // pitch of the packed Phi lines
     static constexpr int NT = (N * T / 8 >= 256) ? 256 : ((N * T / 8 >= 128) ? 128 : 64);
-    // tile + aux; aux holds T real rows, or T half-spectrum rows of N/2 + 1 complex while staging
-    static constexpr size_t base = sizeof(float2) * N * TP + sizeof(float2) * T * (N / 2 + 1);
+    // tile + aux; aux holds T real rows, the T half-spectrum rows of N/2 + 1 complex while staging,
+    // or the T/2 packed complex Phi lines (pitch HP) while they are transformed
+    static constexpr size_t aux_bytes = cmax(cmax(sizeof(float2) * T * (N / 2 + 1), sizeof(float2) * N * HP),
+                                             sizeof(float) * T * N);
+    static constexpr size_t base = sizeof(float2) * N * TP + aux_bytes;
     static constexpr size_t tc_off = (base + 127) & ~(size_t)127;
     static constexpr size_t smem = TC ? tc_off + sizeof(TcSmem) : base;
 };
@@ -46,7 +52,7 @@ __global__ void __launch_bounds__(XCfg<N, TC>::NT) xpass_kernel(XParams p)
     constexpr int T = XCfg<N, TC>::T, TP = XCfg<N, TC>::TP, NT = XCfg<N, TC>::NT, H = N / 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
-    float *aux = reinterpret_cast<float *>(tile + N * TP);  // aux[t * N + n]: real row t
+    float *aux = reinterpret_cast<float *>(tile + N * TP);  // aux[t * N + n]: real row t (or Phi work area)
     const int row0 = blockIdx.x * T;
     const int tid = threadIdx.x;
     const int flags = p.flags;
@@ -56,37 +62,75 @@ __global__ void __launch_bounds__(XCfg<N, TC>::NT) xpass_kernel(XParams p)
         tc_setup(*tcs, static_cast<const __half *>(p.tcw), NT);
     }
 
-    // ---- Phi rows from the half spectrum: rows (2m, 2m+1) as one complex line
+    // psi rows of a kick pass stream into the tile from the start; the Phi work below runs in aux
+    const bool psi_early = (flags & X_HAS_PHI) && (flags & (X_KICK | X_FFT));
+
+    // ---- Phi rows from the half spectrum: rows (2m, 2m+1) as one complex line, all in aux
     if (flags & X_HAS_PHI) {
-        // stage the T half-spectrum rows in aux with asynchronous copies, then build the packed
-        // lines Z = A + iB (Hermitian extension of both rows) from shared memory
+        constexpr int HP = XCfg<N, TC>::HP;
+        constexpr int PV = (T / 2) * N;               // packed values of the tile
+        constexpr int PB = (PV + NT - 1) / NT;        // per thread
         float2 *stage = reinterpret_cast<float2 *>(aux);
+        float2 *pk = reinterpret_cast<float2 *>(aux);   // packed lines [n][HP]
         for (int idx = tid; idx < T * (H + 1); idx += NT) {
             const int t = idx / (H + 1), k = idx % (H + 1);
             const int row = row0 + t;
             if (row < p.rows) cp_async8(&stage[idx], &p.phik[(size_t)row * p.P + k]);
             else stage[idx] = make_float2(0.f, 0.f);
         }
-        cp_async_wait_all();
+        cp_async_commit();
+        if (psi_early) {
+            for (int idx = tid; idx < T * N; idx += NT) {
+                const int n = idx % N, t = idx / N;
+                const int row = row0 + t;
+                if (row < p.rows) cp_async8(&tile[n * TP + t], &p.psi[(size_t)row * N + n]);
+                else tile[n * TP + t] = make_float2(0.f, 0.f);
+            }
+            cp_async_commit();
+            cp_async_wait_group<1>();   // the half-spectrum rows; psi may still be in flight
+        } else {
+            cp_async_wait_group<0>();
+        }
         __syncthreads();
-        for (int idx = tid; idx < (T / 2) * N; idx += NT) {
+        // build the packed lines Z = A + iB (Hermitian extension of both rows) through registers,
+        // since they overwrite the staged rows
+        float2 z[PB];
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            const int idx = tid + q * NT;
+            if (idx >= PV) break;
             const int n = idx % N, m = idx / N;
             const int kk = (n <= H) ? n : N - n;
             float2 A = stage[(2 * m) * (H + 1) + kk], B = stage[(2 * m + 1) * (H + 1) + kk];
             if (n > H) { A.y = -A.y; B.y = -B.y; }
             if (n == 0 || n == H) { A.y = 0.f; B.y = 0.f; }
-            tile[n * TP + m] = make_float2(A.x - B.y, A.y + B.x);
+            z[q] = make_float2(A.x - B.y, A.y + B.x);
         }
         __syncthreads();
-        tfft<N, T / 2, TP, NT, +1, TC>(tile, p.tw, tcs, p.status);
-        for (int idx = tid; idx < (T / 2) * N; idx += NT) {
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            const int idx = tid + q * NT;
+            if (idx < PV) pk[(idx % N) * HP + idx / N] = z[q];
+        }
+        __syncthreads();
+        tfft<N, T / 2, HP, NT, +1, TC>(pk, p.tw, tcs, p.status);
+        // real rows into aux (again through registers: they overwrite the packed lines)
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            const int idx = tid + q * NT;
+            if (idx < PV) z[q] = pk[(idx % N) * HP + idx / N];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < PB; ++q) {
+            const int idx = tid + q * NT;
+            if (idx >= PV) break;
             const int n = idx % N, m = idx / N;
-            const float2 z = tile[n * TP + m];
-            aux[(2 * m) * N + n] = z.x;
-            aux[(2 * m + 1) * N + n] = z.y;
+            aux[(2 * m) * N + n] = z[q].x;
+            aux[(2 * m + 1) * N + n] = z[q].y;
             const int ra = row0 + 2 * m;
             if ((flags & X_WRITE_PHI) && ra + 1 < p.rows) {
-                float za = z.x, zb = z.y;
+                float za = z[q].x, zb = z[q].y;
                 if (flags & X_STATIC) {
                     za += __ldg(&p.phib[(size_t)ra * N + n]);
                     zb += __ldg(&p.phib[(size_t)(ra + 1) * N + n]);
@@ -101,11 +145,13 @@ __global__ void __launch_bounds__(XCfg<N, TC>::NT) xpass_kernel(XParams p)
     // ---- kick and forward x transform of psi
     if (flags & (X_KICK | X_FFT)) {
         const bool fft = flags & X_FFT;
-        for (int idx = tid; idx < T * N; idx += NT) {
-            const int n = idx % N, t = idx / N;
-            const int row = row0 + t;
-            if (row < p.rows) cp_async8(&tile[n * TP + t], &p.psi[(size_t)row * N + n]);
-            else tile[n * TP + t] = make_float2(0.f, 0.f);
+        if (!psi_early) {
+            for (int idx = tid; idx < T * N; idx += NT) {
+                const int n = idx % N, t = idx / N;
+                const int row = row0 + t;
+                if (row < p.rows) cp_async8(&tile[n * TP + t], &p.psi[(size_t)row * N + n]);
+                else tile[n * TP + t] = make_float2(0.f, 0.f);
+            }
         }
         cp_async_wait_all();
         __syncthreads();
