@@ -165,6 +165,7 @@ struct spe_grid {
     float *absorb;    // absorbing-layer factors per axis: nx, ny, nz floats (dt dependent)
     bool absorbing;
     int stile[3];     // strided-pass tile width per axis (0 = default; set by the autotuner)
+    int splan[3];     // strided-pass radix schedule per axis (0 default, 1 alternative)
     int tc;           // SPE_PREC_SPLIT16
     __half *tcw;      // 32 x 32 DFT operands for the tensor stages: [dir][hi, lo][core layout]
     int *status;      // device status word
@@ -265,6 +266,7 @@ SParams base_y(spe_grid *g, float2 *data, int W, int P)
     memset(&p, 0, sizeof(p));
     p.data = data;
     p.tile = g->stile[1];
+    p.plan = g->splan[1];
     p.tc = g->tc;
     p.tcw = g->tcw;
     p.status = g->status;
@@ -287,6 +289,7 @@ SParams base_z(spe_grid *g, float2 *data, int W, int P)
     memset(&p, 0, sizeof(p));
     p.data = data;
     p.tile = g->stile[2];
+    p.plan = g->splan[2];
     p.tc = g->tc;
     p.tcw = g->tcw;
     p.status = g->status;
@@ -525,6 +528,12 @@ int step_body(spe_grid *g, double dtk, double dt, bool absorb_prev)
     return SPE_OK;
 }
 
+// everything about the strided passes' launch shapes that a captured graph bakes in
+int schedule_key(const spe_grid *g)
+{
+    return ((g->stile[1] * 64 + g->stile[2]) * 2 + g->splan[1]) * 2 + g->splan[2];
+}
+
 bool graphs_enabled(spe_grid *g) { return !(g->cfg.flags & (SPE_NO_GRAPH | SPE_PROFILE)); }
 
 // One full step (dt_k = dt, the previous step's absorbing layer applied) as an
@@ -532,7 +541,7 @@ bool graphs_enabled(spe_grid *g) { return !(g->cfg.flags & (SPE_NO_GRAPH | SPE_P
 // the caller's.  Re-captured when anything baked into the launches changes.
 int ensure_step_graph(spe_grid *g, double dt)
 {
-    const int tiles = g->stile[1] * 64 + g->stile[2];
+    const int tiles = schedule_key(g);
     if (g->step_exec && g->graph_dt == dt && g->graph_np == g->np && g->graph_static == g->static_set &&
         g->graph_tiles == tiles)
         return SPE_OK;
@@ -1189,13 +1198,14 @@ int spe_profile_read(spe_grid *g, const char **names, unsigned long long *launch
 namespace {
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tuned;  // (axis, n, nx) -> tile
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;  // (axis, n, nx) -> (tile, plan)
 
-int time_tile(spe_grid *g, int axis, int tile, float2 *scratch, float *ms_out)
+int time_tile(spe_grid *g, int axis, int tile, int plan, float2 *scratch, float *ms_out)
 {
     SParams p = axis == 1 ? base_y(g, scratch, g->n[0], g->n[0]) : base_z(g, scratch, g->n[0], g->n[0]);
     p.flags = S_FWD | S_INV;
     p.tile = tile;
+    p.plan = plan;
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return SPE_ECUDA;
     cudaError_t e = launch_spass(g->n[axis], p, g->st, nullptr);  // warm-up
@@ -1217,25 +1227,33 @@ int autotune_grid(spe_grid *g, float2 *scratch)
             std::lock_guard<std::mutex> lock(g_tune_mu);
             auto it = g_tuned.find(key);
             if (it != g_tuned.end()) {
-                g->stile[axis] = it->second;
+                g->stile[axis] = it->second.first;
+                g->splan[axis] = it->second.second;
                 continue;
             }
         }
-        // candidate widths 8, 16, 32 columns (32 only where the tile fits in shared memory)
+        // candidates: tile widths 16, 8, 32 (32 only where it fits in shared memory) x the default
+        // and the alternative radix schedule (lengths that have one)
         float best_ms = 0.f;
-        int best = 16, rc;
-        for (int tile : {16, 8, 32}) {
-            if (tile == 32 && (size_t)g->n[axis] * 32 * sizeof(float2) > 227 * 1024) continue;
-            float ms = 0.f;
-            if ((rc = time_tile(g, axis, tile, scratch, &ms))) return rc;
-            if (tile == 16 || ms < best_ms) {
-                best = tile;
-                best_ms = ms;
+        int best_tile = 16, best_plan = 0, rc;
+        bool first = true;
+        for (int plan = 0; plan <= (has_alt_plan_n(g->n[axis]) ? 1 : 0); ++plan) {
+            for (int tile : {16, 8, 32}) {
+                if (!spass_tile_ok(g->n[axis], tile)) continue;
+                float ms = 0.f;
+                if ((rc = time_tile(g, axis, tile, plan, scratch, &ms))) return rc;
+                if (first || ms < best_ms) {
+                    best_tile = tile;
+                    best_plan = plan;
+                    best_ms = ms;
+                    first = false;
+                }
             }
         }
-        g->stile[axis] = best;
+        g->stile[axis] = best_tile;
+        g->splan[axis] = best_plan;
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tuned[key] = best;
+        g_tuned[key] = std::make_pair(best_tile, best_plan);
     }
     return SPE_OK;
 }
@@ -1259,6 +1277,31 @@ extern "C" int spe_autotune(spe_grid *g, int *tiles_out)
         tiles_out[1] = g->stile[2];
     }
     return rc;
+}
+
+extern "C" int spe_set_schedule(spe_grid *g, const int *tiles, const int *plans)
+{
+    if (!g || !tiles || !plans) return SPE_EINVAL;
+    for (int a = 0; a < 2; ++a) {
+        const int n = g->n[a + 1];
+        if (tiles[a] != 0 && !spass_tile_ok(n, tiles[a])) return SPE_EINVAL;
+        if (plans[a] != 0 && (plans[a] != 1 || !has_alt_plan_n(n))) return SPE_EINVAL;
+    }
+    for (int a = 0; a < 2; ++a) {
+        g->stile[a + 1] = tiles[a];
+        g->splan[a + 1] = plans[a];
+    }
+    return SPE_OK;
+}
+
+extern "C" int spe_get_schedule(spe_grid *g, int *tiles, int *plans)
+{
+    if (!g || !tiles || !plans) return SPE_EINVAL;
+    for (int a = 0; a < 2; ++a) {
+        tiles[a] = g->stile[a + 1] ? g->stile[a + 1] : spass_default_tile(g->n[a + 1]);
+        plans[a] = g->splan[a + 1];
+    }
+    return SPE_OK;
 }
 
 // ======================================================================== batches
@@ -1308,7 +1351,7 @@ int batch_graph(spe_batch *b, const double *dts)
     bool same = b->exec && b->key_dt.size() == n;
     for (size_t i = 0; same && i < n; ++i)
         same = b->key_dt[i] == dts[i] && b->key_np[i] == b->g[i]->np &&
-               b->key_tiles[i] == b->g[i]->stile[1] * 64 + b->g[i]->stile[2] && !b->g[i]->static_set;
+               b->key_tiles[i] == schedule_key(b->g[i]) && !b->g[i]->static_set;
     if (same) return SPE_OK;
     if (b->exec) {
         cudaGraphExecDestroy(b->exec);
@@ -1354,7 +1397,7 @@ int batch_graph(spe_batch *b, const double *dts)
     b->key_tiles.resize(n);
     for (size_t i = 0; i < n; ++i) {
         b->key_np[i] = b->g[i]->np;
-        b->key_tiles[i] = b->g[i]->stile[1] * 64 + b->g[i]->stile[2];
+        b->key_tiles[i] = schedule_key(b->g[i]);
     }
     return SPE_OK;
 }

@@ -226,6 +226,26 @@ template <> struct Plan<512> { using type = RList<8, 8, 8>; };
 template <> struct Plan<768> { using type = RList<3, 4, 8, 8>; };
 template <> struct Plan<1024> { using type = RList<4, 16, 16>; };
 
+// Alternative radix schedules the autotuner may pick for the strided passes
+// (PL = 1); lengths without one use the default plan.
+template <int N, int PL> struct PlanSel { using type = typename Plan<N>::type; };
+template <> struct PlanSel<32, 1> { using type = RList<2, 16>; };
+template <> struct PlanSel<48, 1> { using type = RList<3, 16>; };
+template <> struct PlanSel<64, 1> { using type = RList<4, 16>; };
+template <> struct PlanSel<96, 1> { using type = RList<3, 2, 16>; };
+template <> struct PlanSel<128, 1> { using type = RList<16, 8>; };
+template <> struct PlanSel<192, 1> { using type = RList<3, 4, 16>; };
+template <> struct PlanSel<256, 1> { using type = RList<4, 8, 8>; };
+template <> struct PlanSel<384, 1> { using type = RList<3, 8, 16>; };
+template <> struct PlanSel<512, 1> { using type = RList<16, 16, 2>; };
+template <> struct PlanSel<768, 1> { using type = RList<3, 16, 16>; };
+template <> struct PlanSel<1024, 1> { using type = RList<8, 8, 16>; };
+template <int N> constexpr bool has_alt_plan()
+{
+    return N == 32 || N == 48 || N == 64 || N == 96 || N == 128 || N == 192 || N == 256 || N == 384 || N == 512 ||
+           N == 768 || N == 1024;
+}
+
 // One Stockham stage over all T lines of the tile, in place through registers.
 template <int N, int T, int TP, int NT, int DIR, int Ns, int R>
 __device__ __forceinline__ void fft_stage(float2 *s, const float4 *__restrict__ tw)
@@ -280,10 +300,10 @@ __device__ __forceinline__ void fft_stages(float2 *s, const float4 *tw, RList<R,
 
 // Transform all T lines of the tile.  Callers __syncthreads() before (the
 // tile must be complete); the last stage ends with a barrier.
-template <int N, int T, int TP, int NT, int DIR>
+template <int N, int T, int TP, int NT, int DIR, int PL = 0>
 __device__ __forceinline__ void tile_fft(float2 *s, const float4 *tw)
 {
-    fft_stages<N, T, TP, NT, DIR, 1>(s, tw, typename Plan<N>::type{});
+    fft_stages<N, T, TP, NT, DIR, 1>(s, tw, typename PlanSel<N, PL>::type{});
 }
 
 // ---- plan utilities: the last radix, the plan without it, a reversed plan
@@ -311,10 +331,10 @@ template <int R, int... Rs, int... As> struct Reverse<RList<R, Rs...>, RList<As.
 // first inverse stage of radix R_m (Ns = 1, no twiddles); the inverse then
 // continues with R_{m-1}..R_1.  op(v, n, t) gets the value of frequency n of
 // line t and returns it multiplied.
-template <int N, int T, int TP, int NT, class Op>
+template <int N, int T, int TP, int NT, class Op, int PL = 0>
 __device__ __forceinline__ void tile_fft_fwd_op_inv(float2 *s, const float4 *tw, const Op &op)
 {
-    using Full = typename Plan<N>::type;
+    using Full = typename PlanSel<N, PL>::type;
     constexpr int R = SplitLast<Full>::last;
     using Init = typename SplitLast<Full>::init;
     constexpr int B = N / R;

@@ -1,6 +1,7 @@
 // Strided-pass dispatch: picks the tile width (the per-length default, or the
 // width the autotuner chose in SParams::tile) and the kernel instance.
 #include "spe_internal.cuh"
+#include "fft_tile.cuh"
 
 namespace spe {
 
@@ -14,6 +15,17 @@ cudaError_t launch_spass_tc(int n, const SParams &p, cudaStream_t st, int *block
 cudaError_t setup_tc_attributes();
 
 int spass_default_tile(int n) { return n >= 256 ? 16 : 32; }
+
+bool has_alt_plan_n(int n)
+{
+    switch (n) {
+#define X(n) \
+    case n: return has_alt_plan<n>();
+        SPE_FOR_EACH_N(X)
+#undef X
+    default: return false;
+    }
+}
 
 bool spass_tile_ok(int n, int tile)
 {

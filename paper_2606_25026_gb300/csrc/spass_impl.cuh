@@ -40,10 +40,10 @@ template <int R0, int R1, int... Rs> struct MaxRadix<RList<R0, R1, Rs...>> {
 // the other width is the autotuner's alternative (SParams::tile).
 template <int N> constexpr int default_tile() { return N >= 256 ? 16 : 32; }
 
-template <int N, int TW, bool TC = false> struct SCfg {
+template <int N, int TW, bool TC = false, int PL = 0> struct SCfg {
     static constexpr int T = TW;
     static constexpr int TP = T;
-    static constexpr int W = N * T / MaxRadix<typename Plan<N>::type>::value;  // butterflies per stage
+    static constexpr int W = N * T / MaxRadix<typename PlanSel<N, PL>::type>::value;  // butterflies per stage
     static constexpr int NT = W >= 512 ? 512 : (W >= 256 ? 256 : (W >= 128 ? 128 : 64));
     static constexpr size_t base = sizeof(float2) * N * TP;
     static constexpr size_t tc_off = (base + 127) & ~(size_t)127;
@@ -71,10 +71,11 @@ struct PoissonOp {
     }
 };
 
-template <int N, int TW, bool TC = false>
-__global__ void __launch_bounds__(SCfg<N, TW, TC>::NT) spass_kernel(SParams p)
+template <int N, int TW, bool TC = false, int PL = 0>
+__global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams p)
 {
-    constexpr int T = SCfg<N, TW, TC>::T, TP = SCfg<N, TW, TC>::TP, NT = SCfg<N, TW, TC>::NT, HT = T / 2;
+    constexpr int T = SCfg<N, TW, TC, PL>::T, TP = SCfg<N, TW, TC, PL>::TP, NT = SCfg<N, TW, TC, PL>::NT,
+                  HT = T / 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TcSmem *tcs = nullptr;
     if constexpr (TC) {
@@ -112,15 +113,17 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC>::NT) spass_kernel(SParams p)
                 tile_fft_fwd_op_inv_tc<N, T, TP, NT>(tile, p.tw, PoissonOp{colk2, p.linek2, p.poisson * p.norm},
                                                      *tcs, p.status);
         } else {
-            if (flags & S_DRIFT) tile_fft_fwd_op_inv<N, T, TP, NT>(tile, p.tw, DriftOp{colfac, p.ez});
-            else tile_fft_fwd_op_inv<N, T, TP, NT>(tile, p.tw, PoissonOp{colk2, p.linek2, p.poisson * p.norm});
+            if (flags & S_DRIFT) tile_fft_fwd_op_inv<N, T, TP, NT, DriftOp, PL>(tile, p.tw, DriftOp{colfac, p.ez});
+            else
+                tile_fft_fwd_op_inv<N, T, TP, NT, PoissonOp, PL>(tile, p.tw,
+                                                                 PoissonOp{colk2, p.linek2, p.poisson * p.norm});
         }
     } else if constexpr (TC) {
         if (flags & S_FWD) tile_fft_tc<N, T, TP, NT, -1>(tile, p.tw, *tcs, p.status);
         if (flags & S_INV) tile_fft_tc<N, T, TP, NT, +1>(tile, p.tw, *tcs, p.status);
     } else {
-        if (flags & S_FWD) tile_fft<N, T, TP, NT, -1>(tile, p.tw);
-        if (flags & S_INV) tile_fft<N, T, TP, NT, +1>(tile, p.tw);
+        if (flags & S_FWD) tile_fft<N, T, TP, NT, -1, PL>(tile, p.tw);
+        if (flags & S_INV) tile_fft<N, T, TP, NT, +1, PL>(tile, p.tw);
     }
 
     if (flags & S_KIN) {
@@ -150,13 +153,48 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC>::NT) spass_kernel(SParams p)
 // widths that fit in shared memory for length N
 template <int N> constexpr bool tile_fits(int tw) { return (size_t)N * tw * sizeof(float2) <= 227 * 1024; }
 
-template <int N, int TW, bool TC = false>
+template <int N, int TW, bool TC = false, int PL = 0>
 static cudaError_t launch_s_nt(const SParams &p, cudaStream_t st, int *blocks_out)
 {
     dim3 grid((p.W + TW - 1) / TW, p.batches);
     if (blocks_out) *blocks_out = grid.x * grid.y;
-    spass_kernel<N, TW, TC><<<grid, SCfg<N, TW, TC>::NT, SCfg<N, TW, TC>::smem, st>>>(p);
+    spass_kernel<N, TW, TC, PL><<<grid, SCfg<N, TW, TC, PL>::NT, SCfg<N, TW, TC, PL>::smem, st>>>(p);
     return cudaGetLastError();
+}
+
+}  // namespace spe
+
+namespace spe {
+
+// Launch / attribute set-up of width W at length n, for the per-width translation units; inside
+// templates the discarded branches instantiate nothing.
+template <int n, int W>
+cudaError_t spass_launch_w(const SParams &p, cudaStream_t st, int *blocks_out)
+{
+    if constexpr (tile_fits<n>(W)) {
+        if constexpr (has_alt_plan<n>()) {
+            if (p.plan) return launch_s_nt<n, W, false, 1>(p, st, blocks_out);
+        }
+        return launch_s_nt<n, W>(p, st, blocks_out);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <int n, int W>
+cudaError_t spass_attr_w()
+{
+    cudaError_t e = cudaSuccess;
+    if constexpr (tile_fits<n>(W)) {
+        e = cudaFuncSetAttribute(spass_kernel<n, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SCfg<n, W>::smem);
+        if constexpr (has_alt_plan<n>()) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(spass_kernel<n, W, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SCfg<n, W, false, 1>::smem);
+        }
+    }
+    return e;
 }
 
 }  // namespace spe

@@ -7,10 +7,8 @@ namespace spe {
 cudaError_t launch_spass_t32(int n, const SParams &p, cudaStream_t st, int *blocks_out)
 {
     switch (n) {
-#define X(n)                                                                               \
-    case n:                                                                                \
-        if constexpr (tile_fits<n>(32)) return launch_s_nt<n, 32>(p, st, blocks_out);   \
-        return cudaErrorInvalidValue;
+#define X(n) \
+    case n: return spass_launch_w<n, 32>(p, st, blocks_out);
         SPE_FOR_EACH_N(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -20,11 +18,8 @@ cudaError_t launch_spass_t32(int n, const SParams &p, cudaStream_t st, int *bloc
 cudaError_t setup_spass_attributes_t32()
 {
     cudaError_t e = cudaSuccess;
-#define X(n)                                                                                            \
-    if constexpr (tile_fits<n>(32))                                                                   \
-        if (e == cudaSuccess)                                                                            \
-            e = cudaFuncSetAttribute(spass_kernel<n, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)SCfg<n, 32>::smem);
+#define X(n) \
+    if (e == cudaSuccess) e = spass_attr_w<n, 32>();
     SPE_FOR_EACH_N(X)
 #undef X
     return e;

@@ -10,6 +10,9 @@ namespace spe {
     X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
 
 bool supported_n(int n);
+bool spass_tile_ok(int n, int tile);      // strided-pass tile width 8, 16 or 32 usable at length n
+int spass_default_tile(int n);            // the width used when none is chosen
+bool has_alt_plan_n(int n);               // length n has an alternative radix schedule
 
 // ---------------------------------------------------------------- x passes
 // Lines along x are contiguous rows of nx complex values; rows = ny * nz.
@@ -82,7 +85,8 @@ struct SParams {
     double *partials;
     unsigned int *counter;
     double *result;
-    int tile;             // columns per CTA: 16 or 32 (0 = the per-length default)
+    int tile;             // columns per CTA: 8, 16 or 32 (0 = the per-length default)
+    int plan;             // radix schedule: 0 default, 1 the alternative (lengths that have one)
     int tc;               // radix-16 stages on the tensor cores (split FP16), N = 256 and 512
     const void *tcw;
     int *status;          // device status word (tensor-stage timeouts)

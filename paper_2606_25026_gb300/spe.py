@@ -33,7 +33,8 @@ EXPORTED = (
     "spe_clear_particles", "spe_step", "spe_suggest_dt", "spe_density", "spe_potential", "spe_energy",
     "spe_last_mass", "spe_get_psi", "spe_get_particles", "spe_particle_count", "spe_sync",
     "spe_launch_count", "spe_profile_read", "spe_strerror", "spe_field_energy_noalloc",
-    "spe_set_static_potential", "spe_virial", "spe_autotune", "spe_batch_create", "spe_batch_grid",
+    "spe_set_static_potential", "spe_virial", "spe_autotune", "spe_set_schedule", "spe_get_schedule",
+    "spe_batch_create", "spe_batch_grid",
     "spe_batch_autotune", "spe_batch_step", "spe_batch_launch_count", "spe_batch_destroy",
     # include/spe_fno.h
     "spe_fno_param_count", "spe_fno_create", "spe_fno_destroy", "spe_fno_set_params", "spe_fno_get_params",
@@ -128,6 +129,8 @@ def load_library(path: str = LIB_PATH):
         "spe_set_static_potential": (I, [P, fp, I]),
         "spe_virial": (I, [P, ctypes.POINTER(spe_virial_t)]),
         "spe_autotune": (I, [P, ctypes.POINTER(I)]),
+        "spe_set_schedule": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "spe_get_schedule": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "spe_batch_create": (I, [ctypes.POINTER(spe_config), I, ctypes.POINTER(P)]),
         "spe_batch_grid": (I, [P, I, ctypes.POINTER(P)]),
         "spe_batch_autotune": (I, [P]),
@@ -318,10 +321,24 @@ class Grid:
         _check(self._lib.spe_set_static_potential(self._h, ctypes.c_void_p(ptr), where), "spe_set_static_potential")
 
     def autotune(self):
-        """Pick the strided passes' tile widths by timing (see spe_autotune); returns (y, z) widths."""
+        """Pick the strided passes' tile widths and radix schedules by timing (see spe_autotune);
+        returns the (y, z) widths."""
         out = (ctypes.c_int * 2)()
         _check(self._lib.spe_autotune(self._h, out), "spe_autotune")
         return out[0], out[1]
+
+    def set_schedule(self, tiles=(0, 0), plans=(0, 0)):
+        """Pin the y and z passes' tile widths (0 = default) and radix schedules (0/1)."""
+        t = (ctypes.c_int * 2)(*[int(v) for v in tiles])
+        p = (ctypes.c_int * 2)(*[int(v) for v in plans])
+        _check(self._lib.spe_set_schedule(self._h, t, p), "spe_set_schedule")
+
+    def schedule(self):
+        """((y tile, z tile), (y plan, z plan)) in use."""
+        t = (ctypes.c_int * 2)()
+        p = (ctypes.c_int * 2)()
+        _check(self._lib.spe_get_schedule(self._h, t, p), "spe_get_schedule")
+        return (t[0], t[1]), (p[0], p[1])
 
     def virial(self) -> dict:
         v = spe_virial_t()

@@ -90,14 +90,47 @@ def test_graph_replay_equals_direct_launches(spe, members):
     assert np.array_equal(a[0], d[0]) and np.array_equal(a[1], d[1])
 
 
-def test_autotune_keeps_results_bitwise(spe, members):
+def test_autotune_stays_within_parity(spe, members):
+    """Tile widths regroup independent lines; the radix schedule the tuner may pick changes only
+    the FP32 rounding: the tuned grid stays within 1e-6 of the default one."""
     m = members[0]
     g = spe.Grid(m["n"], G=1.0)
     tiles = g.autotune()
     assert all(t in (8, 16, 32) for t in tiles)
+    (ty, tz), (py, pz) = g.schedule()
+    assert (ty, tz) == tuple(tiles) and py in (0, 1) and pz in (0, 1)
     g.set_ic(m["psi"])
     g.step(6, m["dt"])
     h = spe.Grid(m["n"], G=1.0)
     h.set_ic(m["psi"])
     h.step(6, m["dt"])
-    assert np.array_equal(g.get_psi(), h.get_psi())
+    a, b = g.get_psi(), h.get_psi()
+    assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
+    if (py, pz) == (0, 0):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n", [64, 96, 128, 256])
+def test_every_schedule_matches_oracle(spe, n):
+    """Each tile width and radix schedule of the strided passes against the FP64 oracle."""
+    import oracle
+    oracle.build()
+    psi = inputs.soliton_halo((n, n, 16) if n == 256 else n, seed=n).astype(np.complex64)
+    shape = psi.shape
+    nz, ny, nx = shape
+    dt = inputs.kinetic_dt((nx, ny, nz))
+    o = oracle.Oracle(nx, ny, nz, 1.0, G=1.0)
+    o.set_ic(psi.astype(np.complex128))
+    o.step(4, dt)
+    ref = o.get_psi()
+    for plan in (0, 1):
+        for tile in (8, 16, 32):
+            g = spe.Grid(nx, ny, nz, G=1.0)
+            try:
+                g.set_schedule((tile, tile), (plan, plan))
+            except spe.SpeError:
+                continue          # width not usable at this length
+            g.set_ic(psi)
+            g.step(4, dt)
+            err = np.linalg.norm(g.get_psi() - ref) / np.linalg.norm(ref)
+            assert err <= 1e-5, (n, tile, plan, err)
