@@ -513,6 +513,7 @@ def main():
     if nstar:
         g.add_particles(torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda(), torch.from_numpy(mass).cuda())
     tiles = g.autotune() if not args.no_autotune else None
+    schedule = g.schedule()
     g.step(args.warmup, dt)
     g.sync()
     g.profile_read()
@@ -556,7 +557,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": [nx, ny, nz], "n_star": nstar, "dt": dt,
-                   "precision": args.prec, "strided_tile_widths_yz": tiles,
+                   "precision": args.prec, "strided_schedule_yz": {"tiles": list(schedule[0]),
+                                                                   "alt_radix_plan": list(schedule[1]),
+                                                                   "autotuned": tiles is not None},
                    "l2": f"working set {g.workspace.numel() / 2**20:.0f} MiB > 129 MB L2 (no flush needed)",
                    "parallelism": f"{world} independent replica(s)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,

@@ -28,7 +28,7 @@ template <int N, bool TC = false> struct XCfg {
     static constexpr int T = 16;
     static constexpr int TP = T + 1;
     static constexpr int HP = T / 2 + 1;   // pitch of the packed Phi lines
-    static constexpr int NT = (N * T / 8 >= 256) ? 256 : ((N * T / 8 >= 128) ? 128 : 64);
+    static constexpr int NT = (N >= 512 && !TC) ? 512 : ((N * T / 8 >= 256) ? 256 : ((N * T / 8 >= 128) ? 128 : 64));
     // tile + aux; aux holds T real rows, the T half-spectrum rows of N/2 + 1 complex while staging,
     // or the T/2 packed complex Phi lines (pitch HP) while they are transformed
     static constexpr size_t aux_bytes = cmax(cmax(sizeof(float2) * T * (N / 2 + 1), sizeof(float2) * N * HP),
