@@ -1,5 +1,5 @@
-// Warp-per-line x passes for lines of 256 and 512 points (FP32, no block-wide
-// barriers).  One warp owns a pair of rows (2m, 2m+1).
+// Warp-per-line x passes for lines of 256 and 512 points (FP32, no shared
+// memory, no block-wide barriers).  One warp owns a pair of rows (2m, 2m+1).
 // A line of N = 32 R points lives in the warp's registers, R per lane, in one
 // of two layouts:
 //   layout A: lane a holds points a + 32 r,          r = 0..R-1
@@ -12,17 +12,16 @@
 // (decimation-in-time across lanes from bit-reversed input, twiddle, register
 // DFT).  The inverse transforms go A -> B, the forward ones B -> A, so that
 //   kick pass   : Phi (the inverse of the packed half-spectrum rows) comes out
-//                 in layout B, psi is brought into layout B, kicked, transformed
-//                 forward into layout A and stored coalesced;
+//                 in layout B, psi is loaded in layout B (R contiguous points
+//                 per lane), kicked, transformed forward into layout A and
+//                 stored coalesced;
 //   density pass: psi-hat is loaded in layout A (coalesced), transformed back
 //                 into layout B and stored, |psi|^2 (+ the star deposit) packed
 //                 as one complex line per row pair, transformed forward into
 //                 layout A and separated into the two rows' half spectra with
 //                 the mirror value of each point fetched across lanes.
-// Global rows move between natural order and layout B through a per-warp
-// shared-memory staging buffer (only __syncwarp), so every global access is
-// coalesced.  Twiddles come from the grid's FP64-built (hi, lo) table with the
-// same compensated multiply as the shared-memory passes.
+// Twiddles come from the grid's FP64-built (hi, lo) table with the same
+// compensated multiply as the shared-memory passes.
 #include "fft_tile.cuh"
 #include "reduce.cuh"
 #include "spe_internal.cuh"
@@ -114,50 +113,6 @@ __device__ __forceinline__ void fft_ba(float2 (&v)[N / 32], const float4 *__rest
     Dft<R, DIR>::run(v);
 }
 
-// Per-warp staging between natural order (coalesced global access: lane i
-// touches points i + 32 j) and layout B.  Point e sits at e + e / (2R), which
-// keeps both the natural-order and the layout-B accesses free of bank
-// conflicts for 8-byte elements.
-template <int N> struct Stage {
-    static constexpr int R = N / 32;
-    static constexpr int SIZE = N + N / (2 * R);
-    __device__ __forceinline__ static int at(int e) { return e + e / (2 * R); }
-};
-
-// global row (natural order, 8-byte elements) -> layout B registers
-template <int N, typename T>
-__device__ __forceinline__ void load_b(const T *__restrict__ g, T (&v)[N / 32], T *buf)
-{
-    constexpr int R = N / 32;
-    const int lane = threadIdx.x & 31, nb = R * brev5(lane);
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-        const int e = lane + 32 * j;
-        buf[Stage<N>::at(e)] = g[e];
-    }
-    __syncwarp();
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = buf[Stage<N>::at(nb + r)];
-    __syncwarp();
-}
-
-// layout B registers -> global row (natural order)
-template <int N, typename T>
-__device__ __forceinline__ void store_b(T *__restrict__ g, const T (&v)[N / 32], T *buf)
-{
-    constexpr int R = N / 32;
-    const int lane = threadIdx.x & 31, nb = R * brev5(lane);
-#pragma unroll
-    for (int r = 0; r < R; ++r) buf[Stage<N>::at(nb + r)] = v[r];
-    __syncwarp();
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-        const int e = lane + 32 * j;
-        g[e] = buf[Stage<N>::at(e)];
-    }
-    __syncwarp();
-}
-
 constexpr int kKickFlags = X_HAS_PHI | X_WRITE_PHI | X_KICK | X_FFT | X_STATIC | X_ABSORB;
 constexpr int kDensityFlags = X_IFFT | X_MASS | X_R2C | X_DEP;
 
@@ -165,9 +120,7 @@ template <int N>
 __global__ void __launch_bounds__(kXwThreads) xwarp_kick_kernel(XParams p)
 {
     constexpr int R = N / 32, H = N / 2;
-    __shared__ __align__(16) float2 stage_all[kXwThreads / 32][Stage<N>::SIZE];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2 *buf = stage_all[warp];
     const int ra = 2 * (blockIdx.x * (kXwThreads / 32) + warp);
     if (ra >= p.rows) return;    // whole warps; this kernel has no block-level synchronisation
     const int flags = p.flags;
@@ -203,23 +156,16 @@ __global__ void __launch_bounds__(kXwThreads) xwarp_kick_kernel(XParams p)
             pb[r] = z[r].y;
         }
         if ((flags & X_WRITE_PHI) && has_b) {
-            // both rows' Phi as (row 2m, row 2m+1) pairs through the staging buffer
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[Stage<N>::at(nb + r)] = make_float2(pa[r], pb[r]);
-            __syncwarp();
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const int e = lane + 32 * j;
-                const float2 z = buf[Stage<N>::at(e)];
-                float za = z.x, zb = z.y;
+            for (int r = 0; r < R; ++r) {
+                float za = pa[r], zb = pb[r];
                 if (flags & X_STATIC) {
-                    za += __ldg(&p.phib[(size_t)ra * N + e]);
-                    zb += __ldg(&p.phib[(size_t)(ra + 1) * N + e]);
+                    za += __ldg(&p.phib[(size_t)ra * N + nb + r]);
+                    zb += __ldg(&p.phib[(size_t)(ra + 1) * N + nb + r]);
                 }
-                p.phi_out[(size_t)ra * N + e] = za;
-                p.phi_out[(size_t)(ra + 1) * N + e] = zb;
+                p.phi_out[(size_t)ra * N + nb + r] = za;
+                p.phi_out[(size_t)(ra + 1) * N + nb + r] = zb;
             }
-            __syncwarp();
         }
     }
 
@@ -229,28 +175,12 @@ __global__ void __launch_bounds__(kXwThreads) xwarp_kick_kernel(XParams p)
             const int row = ra + h;
             if (row >= p.rows) break;
             float2 v[R];
-            load_b<N>(p.psi + (size_t)row * N, v, buf);
-            float sb[R];   // static potential of the row, layout B
-            if (flags & X_STATIC) {
-                float2 t[R];
+            const float4 *src = reinterpret_cast<const float4 *>(p.psi + (size_t)row * N + nb);
 #pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const int e = lane + 32 * j;
-                    buf[Stage<N>::at(e)] = make_float2(__ldg(&p.phib[(size_t)row * N + e]), 0.f);
-                }
-                __syncwarp();
-#pragma unroll
-                for (int r = 0; r < R; ++r) t[r] = buf[Stage<N>::at(nb + r)];
-                __syncwarp();
-#pragma unroll
-                for (int r = 0; r < R; ++r) sb[r] = t[r].x;
-                if ((flags & X_WRITE_PHI) && !(flags & X_HAS_PHI)) {
-#pragma unroll
-                    for (int j = 0; j < R; ++j) {
-                        const int e = lane + 32 * j;
-                        p.phi_out[(size_t)row * N + e] = __ldg(&p.phib[(size_t)row * N + e]);
-                    }
-                }
+            for (int q = 0; q < R / 2; ++q) {
+                const float4 w = src[q];
+                v[2 * q] = make_float2(w.x, w.y);
+                v[2 * q + 1] = make_float2(w.z, w.w);
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -258,7 +188,11 @@ __global__ void __launch_bounds__(kXwThreads) xwarp_kick_kernel(XParams p)
                 if (flags & X_KICK) {
                     const float a2 = v[r].x * v[r].x + v[r].y * v[r].y;
                     float phi = (flags & X_HAS_PHI) ? (h ? pb[r] : pa[r]) : 0.f;
-                    if (flags & X_STATIC) phi += sb[r];
+                    if (flags & X_STATIC) {
+                        const float pbv = __ldg(&p.phib[(size_t)row * N + n]);
+                        phi += pbv;
+                        if ((flags & X_WRITE_PHI) && !(flags & X_HAS_PHI)) p.phi_out[(size_t)row * N + n] = pbv;
+                    }
                     // v * exp(-i ph) = v + v (cos ph - 1 - i sin ph), cos ph - 1 = -2 sin^2(ph/2)
                     float sh, ch;
                     sincosf(0.5f * ((phi + p.kappa * a2) * p.kick_scale), &sh, &ch);
@@ -277,7 +211,10 @@ __global__ void __launch_bounds__(kXwThreads) xwarp_kick_kernel(XParams p)
 #pragma unroll
                 for (int r = 0; r < R; ++r) p.psi[(size_t)row * N + lane + 32 * r] = v[r];
             } else {
-                store_b<N>(p.psi + (size_t)row * N, v, buf);
+                float4 *dst = reinterpret_cast<float4 *>(p.psi + (size_t)row * N + nb);
+#pragma unroll
+                for (int q = 0; q < R / 2; ++q)
+                    dst[q] = make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
             }
         }
     }
@@ -287,9 +224,7 @@ template <int N>
 __global__ void __launch_bounds__(kXwThreads) xwarp_density_kernel(XParams p)
 {
     constexpr int R = N / 32, H = N / 2;
-    __shared__ __align__(16) float2 stage_all[kXwThreads / 32][Stage<N>::SIZE];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float2 *buf = stage_all[warp];
     const int ra = 2 * (blockIdx.x * (kXwThreads / 32) + warp);
     const bool live = ra < p.rows;       // every thread reaches the grid reduction
     const int flags = p.flags;
@@ -306,13 +241,19 @@ __global__ void __launch_bounds__(kXwThreads) xwarp_density_kernel(XParams p)
             for (int r = 0; r < R; ++r)
                 v[r] = ok ? p.psi[(size_t)row * N + lane + 32 * r] : make_float2(0.f, 0.f);
             fft_ab<N, +1>(v, p.tw);
-            if (ok) store_b<N>(p.psi + (size_t)row * N, v, buf);
-        } else {
             if (ok) {
-                load_b<N>(p.psi + (size_t)row * N, v, buf);
-            } else {
+                float4 *dst = reinterpret_cast<float4 *>(p.psi + (size_t)row * N + nb);
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[r] = make_float2(0.f, 0.f);
+                for (int q = 0; q < R / 2; ++q)
+                    dst[q] = make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
+            }
+        } else {
+            const float4 *src = reinterpret_cast<const float4 *>(p.psi + (size_t)row * N + nb);
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) {
+                const float4 w = ok ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[2 * q] = make_float2(w.x, w.y);
+                v[2 * q + 1] = make_float2(w.z, w.w);
             }
         }
 #pragma unroll
@@ -322,23 +263,15 @@ __global__ void __launch_bounds__(kXwThreads) xwarp_density_kernel(XParams p)
             rho[h][r] = a2;
         }
         if ((flags & X_DEP) && ok) {
-            long long *dep = p.dep + (size_t)row * N;
-            long long *lbuf = reinterpret_cast<long long *>(buf);
+            long long *dep = p.dep + (size_t)row * N + nb;
             long long d[R];
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const int e = lane + 32 * j;
-                lbuf[Stage<N>::at(e)] = __ldcs(&dep[e]);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int r = 0; r < R; ++r) d[r] = lbuf[Stage<N>::at(nb + r)];
-            __syncwarp();
+            for (int r = 0; r < R; ++r) d[r] = __ldcs(&dep[r]);
 #pragma unroll
             for (int r = 0; r < R; ++r) rho[h][r] += (float)d[r] * p.dep_scale;
-            // every value of the row has been read (into the staging buffer): clear it for the next step
+            // every value of this lane's run has been read: clear it for the next step
 #pragma unroll
-            for (int j = 0; j < R; ++j) __stcs(&dep[lane + 32 * j], 0ll);
+            for (int r = 0; r < R; ++r) __stcs(&dep[r], 0ll);
         }
     }
     if (flags & X_R2C) {
