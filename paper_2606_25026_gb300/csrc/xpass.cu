@@ -13,15 +13,10 @@ static cudaError_t launch_x_n(const XParams &p, cudaStream_t st, int *blocks_out
 }
 
 cudaError_t launch_xpass_tc(int nx, const XParams &p, cudaStream_t st, int *blocks_out);
-cudaError_t launch_xwarp(int nx, const XParams &p, cudaStream_t st, int *blocks_out);
 
 cudaError_t launch_xpass(int nx, const XParams &p, cudaStream_t st, int *blocks_out)
 {
     if (p.tc && (nx == 256 || nx == 512)) return launch_xpass_tc(nx, p, st, blocks_out);
-    if (nx == 256 || nx == 512) {
-        const cudaError_t e = launch_xwarp(nx, p, st, blocks_out);
-        if (e != cudaErrorNotSupported) return e;
-    }
     switch (nx) {
 #define X(n) \
     case n: return launch_x_n<n>(p, st, blocks_out);
