@@ -30,6 +30,7 @@
 #include <cuda_fp16.h>
 
 #include "spe.h"
+#include "fno_internal.cuh"
 #include "spe_internal.cuh"
 
 namespace spe {
@@ -663,6 +664,78 @@ void update_quantum(spe_grid *g)
 
 }  // namespace
 
+namespace spe {
+
+// Launch every kernel of spe_energy on the grid's stream; the raw sums land in
+// diag[8 .. 8 + kEnergyRaw).  With host_raw they are also copied there
+// asynchronously (a pinned buffer; nothing waits).
+int energy_issue(spe_grid *g, double *host_raw, bool copy_to_host)
+{
+    int rc;
+    if ((rc = potential_to_phi(g))) return rc;
+    if ((rc = deposit_only(g))) return rc;
+    if ((rc = launch(g, KIND_DIAG, [&] {
+             return launch_grid_diag(g->psi, g->phi, g->np ? g->dep : nullptr, (float)(g->quantum / g->dv),
+                                     (float)g->cfg.kappa, g->dv, g->ncells, g->partials, g->counter, g->diag + 8,
+                                     g->st);
+         })))
+        return rc;
+    if (g->static_set) {
+        // the static potential counts once, not halved: 1/2 sum (|psi|^2 + rho_*) Phi_b dV lands in diag[25]
+        if ((rc = deposit_only(g))) return rc;
+        if ((rc = launch(g, KIND_DIAG, [&] {
+                 return launch_grid_diag(g->psi, g->phib, g->np ? g->dep : nullptr, (float)(g->quantum / g->dv),
+                                         0.f, g->dv, g->ncells, g->partials, g->counter, g->diag + 24, g->st);
+             })))
+            return rc;
+    }
+    // kinetic: sum over axes of (1/N_a) sum_lines sum_k k_a^2 |F_a line|^2
+    XParams xp = base_x(g);
+    xp.flags = X_KIN;
+    xp.result = g->diag + 16;
+    if ((rc = run_x(g, KIND_DIAG, xp))) return rc;
+    SParams y = base_y(g, g->psi, g->n[0], g->n[0]);
+    y.flags = S_FWD | S_KIN;
+    y.result = g->diag + 17;
+    if ((rc = run_s(g, KIND_DIAG, g->n[1], y))) return rc;
+    SParams z = base_z(g, g->psi, g->n[0], g->n[0]);
+    z.flags = S_FWD | S_KIN;
+    z.result = g->diag + 18;
+    if ((rc = run_s(g, KIND_DIAG, g->n[2], z))) return rc;
+    if (g->np) {
+        if ((rc = launch(g, KIND_DIAG, [&] {
+                 return launch_particle_ke(g->vx, g->vy, g->vz, g->pm, (int)g->np, g->partials, g->counter,
+                                           g->diag + 19, g->st);
+             })))
+            return rc;
+    }
+    if (copy_to_host && host_raw &&
+        cudaMemcpyAsync(host_raw, g->diag + 8, kEnergyRaw * sizeof(double), cudaMemcpyDeviceToHost, g->st) !=
+            cudaSuccess)
+        return SPE_ECUDA;
+    return SPE_OK;
+}
+
+int energy_from_raw(spe_grid *g, const double *raw, spe_energy_t *out)
+{
+    const double static_raw = g->static_set ? raw[17] : 0.0;
+    const double eta = g->cfg.hbar_over_m;
+    out->mass = raw[0] * g->dv;
+    const bool has_phi = g->gravity || g->static_set;
+    out->potential = has_phi ? 0.5 * (raw[1] + static_raw) * g->dv : 0.0;
+    out->interaction = 0.5 * g->cfg.kappa * raw[2] * g->dv;
+    out->max_abs_phi = has_phi ? raw[3] : 0.0;
+    out->kinetic = 0.5 * eta * eta * g->dv * (raw[8] / g->n[0] + raw[9] / g->n[1] + raw[10] / g->n[2]);
+    out->star_kinetic = g->np ? raw[11] : 0.0;
+    out->total = out->kinetic + out->potential + out->interaction + out->star_kinetic;
+    return SPE_OK;
+}
+
+float2 *grid_psi(spe_grid *g) { return g->psi; }
+cudaStream_t grid_stream(spe_grid *g) { return g->st; }
+
+}  // namespace spe
+
 extern "C" {
 
 const char *spe_strerror(int s)
@@ -1008,60 +1081,11 @@ int spe_potential(spe_grid *g, float *out, int where)
 int spe_energy(spe_grid *g, spe_energy_t *out)
 {
     if (!g || !out) return SPE_EINVAL;
+    double raw[spe::kEnergyRaw];
     int rc;
-    if ((rc = potential_to_phi(g))) return rc;
-    if ((rc = deposit_only(g))) return rc;
-    if ((rc = launch(g, KIND_DIAG, [&] {
-             return launch_grid_diag(g->psi, g->phi, g->np ? g->dep : nullptr, (float)(g->quantum / g->dv),
-                                     (float)g->cfg.kappa, g->dv, g->ncells, g->partials, g->counter, g->diag + 8,
-                                     g->st);
-         })))
-        return rc;
-    double static_raw = 0.0;
-    if (g->static_set) {
-        // the static potential counts once, not halved: add 1/2 sum (|psi|^2 + rho_*) Phi_b dV
-        if ((rc = deposit_only(g))) return rc;
-        if ((rc = launch(g, KIND_DIAG, [&] {
-                 return launch_grid_diag(g->psi, g->phib, g->np ? g->dep : nullptr, (float)(g->quantum / g->dv),
-                                         0.f, g->dv, g->ncells, g->partials, g->counter, g->diag + 24, g->st);
-             })))
-            return rc;
-        if ((rc = copy_out(g, &static_raw, g->diag + 25, sizeof(double), SPE_HOST))) return rc;
-    }
-    // kinetic: sum over axes of (1/N_a) sum_lines sum_k k_a^2 |F_a line|^2
-    XParams xp = base_x(g);
-    xp.flags = X_KIN;
-    xp.result = g->diag + 16;
-    if ((rc = run_x(g, KIND_DIAG, xp))) return rc;
-    SParams y = base_y(g, g->psi, g->n[0], g->n[0]);
-    y.flags = S_FWD | S_KIN;
-    y.result = g->diag + 17;
-    if ((rc = run_s(g, KIND_DIAG, g->n[1], y))) return rc;
-    SParams z = base_z(g, g->psi, g->n[0], g->n[0]);
-    z.flags = S_FWD | S_KIN;
-    z.result = g->diag + 18;
-    if ((rc = run_s(g, KIND_DIAG, g->n[2], z))) return rc;
-    double skin = 0.0;
-    if (g->np) {
-        if ((rc = launch(g, KIND_DIAG, [&] {
-                 return launch_particle_ke(g->vx, g->vy, g->vz, g->pm, (int)g->np, g->partials, g->counter,
-                                           g->diag + 19, g->st);
-             })))
-            return rc;
-    }
-    double raw[12];
+    if ((rc = spe::energy_issue(g, raw, false))) return rc;
     if ((rc = copy_out(g, raw, g->diag + 8, sizeof(raw), SPE_HOST))) return rc;
-    if (g->np) skin = raw[11];
-    const double eta = g->cfg.hbar_over_m;
-    out->mass = raw[0] * g->dv;
-    const bool has_phi = g->gravity || g->static_set;
-    out->potential = has_phi ? 0.5 * (raw[1] + static_raw) * g->dv : 0.0;
-    out->interaction = 0.5 * g->cfg.kappa * raw[2] * g->dv;
-    out->max_abs_phi = has_phi ? raw[3] : 0.0;
-    out->kinetic = 0.5 * eta * eta * g->dv * (raw[8] / g->n[0] + raw[9] / g->n[1] + raw[10] / g->n[2]);
-    out->star_kinetic = skin;
-    out->total = out->kinetic + out->potential + out->interaction + out->star_kinetic;
-    return SPE_OK;
+    return spe::energy_from_raw(g, raw, out);
 }
 
 int spe_set_static_potential(spe_grid *g, const float *phi_b, int where)

@@ -292,8 +292,23 @@ void free_all(spe_fno *f)
 
 }  // namespace
 
+extern "C" {
+static int issue_forward(spe_fno *f, const void *psi, const void *psi_b, void *psi_out, int batch);
+}
+
 int spe::fno::net_n(const spe_fno *f) { return f->n; }
 cudaStream_t spe::fno::net_stream(const spe_fno *f) { return f->st; }
+
+int spe::fno::forward_direct(spe_fno *f, cudaStream_t st, const void *psi, const void *psi_b, void *psi_out,
+                             int batch)
+{
+    if (!f || !psi || !psi_b || !psi_out || batch < 1 || batch > f->B) return SPE_EINVAL;
+    const cudaStream_t keep = f->st;
+    f->st = st;
+    const int rc = issue_forward(f, psi, psi_b, psi_out, batch);
+    f->st = keep;
+    return rc;
+}
 
 int spe::fno::forward_on_stream(spe_fno *f, cudaStream_t st, const void *psi, const void *psi_b, void *psi_out,
                                 int batch)

@@ -17,6 +17,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "spe.h"
+
 #include <cstddef>
 
 namespace spe {
@@ -110,6 +112,10 @@ struct spe_fno;
 namespace spe {
 namespace fno {
 
+// spe_fno_forward issued as direct launches on another stream, never as a graph
+// replay (for use inside a stream capture)
+int forward_direct(spe_fno *f, cudaStream_t st, const void *psi, const void *psi_b, void *psi_out, int batch);
+
 // grid points per axis and stream of a network (fno.cu)
 int net_n(const spe_fno *f);
 cudaStream_t net_stream(const spe_fno *f);
@@ -117,4 +123,15 @@ cudaStream_t net_stream(const spe_fno *f);
 int forward_on_stream(spe_fno *f, cudaStream_t st, const void *psi, const void *psi_b, void *psi_out, int batch);
 
 }  // namespace fno
+}  // namespace spe
+
+namespace spe {
+
+// solver internals the judge uses (api.cu)
+constexpr int kEnergyRaw = 18;   // raw energy sums copied per spe_energy
+int energy_issue(spe_grid *g, double *host_raw, bool copy_to_host);
+int energy_from_raw(spe_grid *g, const double *raw, spe_energy_t *out);
+float2 *grid_psi(spe_grid *g);
+cudaStream_t grid_stream(spe_grid *g);
+
 }  // namespace spe

@@ -5,7 +5,11 @@
 //
 // The coarse step, the network and the proposal's energy run on a private
 // stream (the coarse grid's), so the energy of the current state, computed on
-// the grid's stream, overlaps them; the coarse grid steps without host syncs.
+// the grid's stream, overlaps them.  That private-stream work is captured as
+// one CUDA graph the second time an advance repeats K dt, and replayed after
+// (the coarse grid's tables are built by the first, direct advance); the
+// proposal's raw energy sums come back through a pinned buffer, so an advance
+// has one wait for the private stream.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,6 +32,11 @@ struct spe_surrogate {
     cudaStream_t st;      // the grids' stream (grid_cfg.cuda_stream)
     cudaStream_t own;     // private stream of the coarse grid and the network
     cudaEvent_t ready;
+    double *h_raw;        // pinned: the proposal's raw energy sums
+    cudaGraphExec_t exec; // the private-stream work of an advance, for key_dt
+    double key_dt;
+    int seen;
+    bool graph_ok;
 };
 
 namespace {
@@ -42,7 +51,45 @@ void release(spe_surrogate *s)
     cudaFree(s->out);
     cudaFree(s->counter);
     if (s->ready) cudaEventDestroy(s->ready);
+    if (s->exec) cudaGraphExecDestroy(s->exec);
     if (s->own) cudaStreamDestroy(s->own);
+    if (s->h_raw) cudaFreeHost(s->h_raw);
+}
+
+// coarse step of K dt from psi0, the proposal, the proposal's energy kernels and
+// the copy of its raw sums to the pinned buffer: all on the private stream, no
+// host synchronisation (capturable)
+int issue_private(spe_surrogate *s, double kdt)
+{
+    int rc;
+    if ((rc = spe_set_ic(s->coarse, s->psi0, s->ncells, SPE_DEVICE))) return rc;
+    if ((rc = spe_step(s->coarse, 1, kdt))) return rc;
+    if (cudaMemcpyAsync(s->psib, spe::grid_psi(s->coarse), s->ncells * sizeof(float2), cudaMemcpyDeviceToDevice,
+                        s->own) != cudaSuccess)
+        return SPE_ECUDA;
+    if ((rc = forward_direct(s->f, s->own, s->psi0, s->psib, s->prop, 1))) return rc;
+    if ((rc = spe_set_ic(s->coarse, s->prop, s->ncells, SPE_DEVICE))) return rc;
+    return spe::energy_issue(s->coarse, s->h_raw, true);
+}
+
+int capture_private(spe_surrogate *s, double kdt)
+{
+    if (s->exec) {
+        cudaGraphExecDestroy(s->exec);
+        s->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SPE_ECUDA;
+    int rc = issue_private(s, kdt);
+    const cudaError_t ec = cudaStreamEndCapture(s->own, &graph);
+    if (rc == SPE_OK && ec != cudaSuccess) rc = SPE_ECUDA;
+    if (rc == SPE_OK && cudaGraphInstantiate(&s->exec, graph, 0) != cudaSuccess) {
+        s->exec = nullptr;
+        rc = SPE_ECUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc;
 }
 
 }  // namespace
@@ -69,6 +116,7 @@ SPE_API int spe_surrogate_create(const spe_config *grid_cfg, spe_fno *f, const s
         rc = SPE_ECUDA;
     spe_config cc = *grid_cfg;
     cc.flags |= SPE_NO_CFL_CHECK | SPE_ASYNC;
+    cc.flags &= ~SPE_PROFILE;
     cc.max_particles = 0;
     cc.cuda_stream = s->own;
     if (rc == SPE_OK) rc = spe_create_grid(&cc, nullptr, 0, &s->coarse);
@@ -81,6 +129,8 @@ SPE_API int spe_surrogate_create(const spe_config *grid_cfg, spe_fno *f, const s
         if (e == cudaSuccess) e = cudaMalloc(&s->out, 2 * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc(&s->counter, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemset(s->counter, 0, sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMallocHost(&s->h_raw, spe::kEnergyRaw * sizeof(double));
+        s->graph_ok = true;
         if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? SPE_ENOMEM : SPE_ECUDA;
     }
     if (rc != SPE_OK) {
@@ -112,19 +162,35 @@ SPE_API int spe_surrogate_advance(spe_surrogate *s, spe_grid *g, int K, double d
     spe_judge_result r{};
     r.rel_l2 = -1.0;
     // 1. the state, handed to the private stream
-    if ((rc = spe_get_psi(g, s->psi0, SPE_DEVICE))) return rc;
-    if (cudaEventRecord(s->ready, s->st) != cudaSuccess || cudaStreamWaitEvent(s->own, s->ready, 0) != cudaSuccess)
+    if (cudaMemcpyAsync(s->psi0, spe::grid_psi(g), s->ncells * sizeof(float2), cudaMemcpyDeviceToDevice,
+                        spe::grid_stream(g)) != cudaSuccess)
         return SPE_ECUDA;
-    // 2. the coarse step and the proposal (private stream, no host sync)
-    if ((rc = spe_set_ic(s->coarse, s->psi0, s->ncells, SPE_DEVICE))) return rc;
-    if ((rc = spe_step(s->coarse, 1, K * dt))) return rc;
-    if ((rc = spe_get_psi(s->coarse, s->psib, SPE_DEVICE))) return rc;
-    if ((rc = forward_on_stream(s->f, s->own, s->psi0, s->psib, s->prop, 1))) return rc;
-    if ((rc = spe_set_ic(s->coarse, s->prop, s->ncells, SPE_DEVICE))) return rc;
+    if (cudaEventRecord(s->ready, spe::grid_stream(g)) != cudaSuccess ||
+        cudaStreamWaitEvent(s->own, s->ready, 0) != cudaSuccess)
+        return SPE_ECUDA;
+    // 2. coarse step, proposal, the proposal's energy (private stream; a graph replay once K dt repeats)
+    const double kdt = K * dt;
+    if (s->graph_ok && s->seen >= 1 && s->key_dt == kdt) {
+        if (!s->exec && (rc = capture_private(s, kdt))) {
+            s->graph_ok = false;          // capture unavailable: stay on direct launches
+            if ((rc = issue_private(s, kdt))) return rc;
+        } else if (cudaGraphLaunch(s->exec, s->own) != cudaSuccess) {
+            return SPE_ECUDA;
+        }
+    } else {
+        if (s->exec) {
+            cudaGraphExecDestroy(s->exec);
+            s->exec = nullptr;
+        }
+        if ((rc = issue_private(s, kdt))) return rc;
+        s->key_dt = kdt;
+        s->seen = 1;
+    }
     // 3. the state's energy on the grid's stream meanwhile, then the proposal's
     spe_energy_t e0{}, e1{};
     if ((rc = spe_energy(g, &e0))) return rc;
-    if ((rc = spe_energy(s->coarse, &e1))) return rc;
+    if (cudaStreamSynchronize(s->own) != cudaSuccess) return SPE_ECUDA;
+    if ((rc = spe::energy_from_raw(s->coarse, s->h_raw, &e1))) return rc;
     if ((rc = spe_fno_sync(s->f))) return rc;
     r.mass_drift = std::fabs(e1.mass - e0.mass) / std::fabs(e0.mass);
     r.energy_drift = std::fabs(e1.total - e0.total) / std::fabs(e0.total);
