@@ -33,6 +33,7 @@ struct spe_surrogate {
     cudaStream_t own;     // private stream of the coarse grid and the network
     cudaEvent_t ready;
     double *h_raw;        // pinned: the proposal's raw energy sums
+    double *h_raw0;       // pinned: the state's raw energy sums
     cudaGraphExec_t exec; // the private-stream work of an advance, for key_dt
     double key_dt;
     int seen;
@@ -54,6 +55,7 @@ void release(spe_surrogate *s)
     if (s->exec) cudaGraphExecDestroy(s->exec);
     if (s->own) cudaStreamDestroy(s->own);
     if (s->h_raw) cudaFreeHost(s->h_raw);
+    if (s->h_raw0) cudaFreeHost(s->h_raw0);
 }
 
 // coarse step of K dt from psi0, the proposal, the proposal's energy kernels and
@@ -130,6 +132,7 @@ SPE_API int spe_surrogate_create(const spe_config *grid_cfg, spe_fno *f, const s
         if (e == cudaSuccess) e = cudaMalloc(&s->counter, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemset(s->counter, 0, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMallocHost(&s->h_raw, spe::kEnergyRaw * sizeof(double));
+        if (e == cudaSuccess) e = cudaMallocHost(&s->h_raw0, spe::kEnergyRaw * sizeof(double));
         s->graph_ok = true;
         if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? SPE_ENOMEM : SPE_ECUDA;
     }
@@ -186,10 +189,12 @@ SPE_API int spe_surrogate_advance(spe_surrogate *s, spe_grid *g, int K, double d
         s->key_dt = kdt;
         s->seen = 1;
     }
-    // 3. the state's energy on the grid's stream meanwhile, then the proposal's
+    // 3. the state's energy on the grid's stream meanwhile; then both sets of raw sums
     spe_energy_t e0{}, e1{};
-    if ((rc = spe_energy(g, &e0))) return rc;
-    if (cudaStreamSynchronize(s->own) != cudaSuccess) return SPE_ECUDA;
+    if ((rc = spe::energy_issue(g, s->h_raw0, true))) return rc;
+    if (cudaStreamSynchronize(spe::grid_stream(g)) != cudaSuccess || cudaStreamSynchronize(s->own) != cudaSuccess)
+        return SPE_ECUDA;
+    if ((rc = spe::energy_from_raw(g, s->h_raw0, &e0))) return rc;
     if ((rc = spe::energy_from_raw(s->coarse, s->h_raw, &e1))) return rc;
     if ((rc = spe_fno_sync(s->f))) return rc;
     r.mass_drift = std::fabs(e1.mass - e0.mass) / std::fabs(e0.mass);
