@@ -372,9 +372,9 @@ def surrogate_arm(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     t_plain = sg.timed(lambda: run_plain(steps), reps=1)
-    l0 = inf.launch_count()
+    sur.launch_count(reset=True)
     t_sur = sg.timed(lambda: run_surrogate(steps), reps=1)
-    fno_launches = inf.launch_count() - l0
+    sur_launches = sur.launch_count()
     clk = clocks.stop()
     cells = n ** 3
     value = world * cells * K * steps / t_sur
@@ -453,7 +453,7 @@ def surrogate_arm(args, rank, world, local):
                         "kernels": {k: {"launches": v[0], "ms_per_launch": round(v[1] / max(1, v[0]), 4),
                                         "GBs": round(fno_bytes(k) / (v[1] * 1e-3 / max(1, v[0])) / 1e9, 1)}
                                     for k, v in prof.items()}},
-        "gpu_launches": int(fno_launches),
+        "gpu_launches": int(sur_launches),
         "clocks": clk,
         "e2e": {"value": world * cells * K * ke / t_e2e, "unit": "cell-steps/s", "steps": ke,
                 "h2d_bytes_per_step": cells * 8, "d2h_bytes_per_step": cells * 8,

@@ -165,6 +165,11 @@ SPE_API int spe_surrogate_destroy(spe_surrogate *s);
 SPE_API int spe_surrogate_advance(spe_surrogate *s, spe_grid *g, int K, double dt, int spot_check,
                                   spe_judge_result *out);
 
+/* Kernels the surrogate's advances ran (the network's, the coarse grid's and
+ * the kernels they launched on the caller's grid; CUDA-graph nodes counted per
+ * replay) since creation or the last reset. */
+SPE_API int spe_surrogate_launch_count(spe_surrogate *s, unsigned long long *count_out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@
 
 #include <cmath>
 #include <new>
+#include <vector>
 
 #include "fno_internal.cuh"
 #include "spe_fno.h"
@@ -38,6 +39,8 @@ struct spe_surrogate {
     double key_dt;
     int seen;
     bool graph_ok;
+    unsigned long long graph_kernels;  // kernel nodes of exec
+    unsigned long long launches;       // kernels this surrogate ran (graph nodes included)
 };
 
 namespace {
@@ -89,7 +92,20 @@ int capture_private(spe_surrogate *s, double kdt)
         s->exec = nullptr;
         rc = SPE_ECUDA;
     }
-    if (graph) cudaGraphDestroy(graph);
+    s->graph_kernels = 0;
+    if (graph) {
+        size_t n = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &n) == cudaSuccess && n) {
+            std::vector<cudaGraphNode_t> nodes(n);
+            if (cudaGraphGetNodes(graph, nodes.data(), &n) == cudaSuccess)
+                for (size_t i = 0; i < n; ++i) {
+                    cudaGraphNodeType t;
+                    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                        ++s->graph_kernels;
+                }
+        }
+        cudaGraphDestroy(graph);
+    }
     cudaGetLastError();
     return rc;
 }
@@ -164,6 +180,11 @@ SPE_API int spe_surrogate_advance(spe_surrogate *s, spe_grid *g, int K, double d
     if (np) return SPE_EINVAL;
     spe_judge_result r{};
     r.rel_l2 = -1.0;
+    unsigned long long g0 = 0, c0 = 0, f0 = 0;
+    spe_launch_count(g, &g0, 0);
+    spe_launch_count(s->coarse, &c0, 0);
+    spe_fno_launch_count(s->f, &f0, 0);
+    bool replayed = false;
     // 1. the state, handed to the private stream
     if (cudaMemcpyAsync(s->psi0, spe::grid_psi(g), s->ncells * sizeof(float2), cudaMemcpyDeviceToDevice,
                         spe::grid_stream(g)) != cudaSuccess)
@@ -179,6 +200,8 @@ SPE_API int spe_surrogate_advance(spe_surrogate *s, spe_grid *g, int K, double d
             if ((rc = issue_private(s, kdt))) return rc;
         } else if (cudaGraphLaunch(s->exec, s->own) != cudaSuccess) {
             return SPE_ECUDA;
+        } else {
+            replayed = true;
         }
     } else {
         if (s->exec) {
@@ -224,7 +247,22 @@ SPE_API int spe_surrogate_advance(spe_surrogate *s, spe_grid *g, int K, double d
         if ((rc = spe_step(g, K, dt))) return rc;
         r.accepted = 0;
     }
+    unsigned long long g1 = 0, c1 = 0, f1 = 0;
+    spe_launch_count(g, &g1, 0);
+    spe_launch_count(s->coarse, &c1, 0);
+    spe_fno_launch_count(s->f, &f1, 0);
+    // the counters also moved while a graph was captured (its kernels did not run then)
+    if (!replayed) s->launches += (g1 - g0) + (c1 - c0) + (f1 - f0);
+    else s->launches += (g1 - g0) + s->graph_kernels;
     *out = r;
+    return SPE_OK;
+}
+
+SPE_API int spe_surrogate_launch_count(spe_surrogate *s, unsigned long long *count_out, int reset)
+{
+    if (!s || !count_out) return SPE_EINVAL;
+    *count_out = s->launches;
+    if (reset) s->launches = 0;
     return SPE_OK;
 }
 

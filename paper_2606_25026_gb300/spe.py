@@ -40,7 +40,7 @@ EXPORTED = (
     "spe_fno_param_count", "spe_fno_create", "spe_fno_destroy", "spe_fno_set_params", "spe_fno_get_params",
     "spe_fno_get_grads", "spe_fno_forward", "spe_fno_backward", "spe_fno_adam", "spe_fno_sync",
     "spe_fno_profile_read", "spe_fno_launch_count",
-    "spe_surrogate_create", "spe_surrogate_destroy", "spe_surrogate_advance",
+    "spe_surrogate_create", "spe_surrogate_destroy", "spe_surrogate_advance", "spe_surrogate_launch_count",
 )
 
 # include/spe_fno.h
@@ -154,6 +154,7 @@ def load_library(path: str = LIB_PATH):
                                      ctypes.POINTER(P)]),
         "spe_surrogate_destroy": (I, [P]),
         "spe_surrogate_advance": (I, [P, P, I, D, I, ctypes.POINTER(spe_judge_result)]),
+        "spe_surrogate_launch_count": (I, [P, ctypes.POINTER(ctypes.c_ulonglong), I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -603,6 +604,12 @@ class Surrogate:
             self.destroy()
         except Exception:
             pass
+
+    def launch_count(self, reset=False) -> int:
+        out = ctypes.c_ulonglong()
+        _check(self._lib.spe_surrogate_launch_count(self._h, ctypes.byref(out), int(bool(reset))),
+               "spe_surrogate_launch_count")
+        return out.value
 
     def advance(self, grid: Grid, K: int, dt: float, spot_check=False) -> dict:
         r = spe_judge_result()

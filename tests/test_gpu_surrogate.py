@@ -126,3 +126,8 @@ def test_graph_replayed_advance_matches_direct(spe):
     for o, v in zip(outs[1:], verdicts[1:]):
         assert np.array_equal(o, outs[0])
         assert v == verdicts[0]
+    # every advance ran kernels, replays included
+    s.launch_count(reset=True)
+    g.set_ic(psi)
+    s.advance(g, K, dt)
+    assert s.launch_count() >= 40
