@@ -32,6 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_2606_25026_gb300 import replicas  # noqa: E402
+
 # Algorithmic HBM bytes per grid cell for one launch of each kernel kind, with stars (the
 # fused axis-pass schedule): reads + writes that the step cannot avoid at that pass.
 #   x_kick_fwd        : R psi 8 + R Phi_hat 4 + W psi 8 + W Phi 4           = 24
@@ -68,13 +70,6 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
-
-
-def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
 
 
 def source_hash() -> str:
@@ -227,14 +222,12 @@ def reference_arm(args, rank, world):
     return 0
 
 
-def ensemble_arm(args, rank, world, local):
+def ensemble_arm(args, r):
     """64 independent halos of uneven sizes stepped as one batch (a CUDA graph with a branch per
     member); value = sum over members of cells x steps / time."""
     import torch
-    import torch.distributed as dist
-    from paper_2606_25026_gb300 import build as spe_build, inputs, spe
-    spe_build.build()
-    torch.cuda.set_device(local)
+    from paper_2606_25026_gb300 import inputs, spe
+    rank, world, local = r.rank, r.world, r.local
     members = inputs.ensemble()
     stream = torch.cuda.Stream()
     b = spe.Batch([dict(nx=m["n"], G=1.0, max_particles=len(m["mass"])) for m in members], stream=stream)
@@ -249,7 +242,7 @@ def ensemble_arm(args, rank, world, local):
     cells = sum(m["n"] ** 3 for m in members)
     stars = sum(len(m["mass"]) for m in members)
     l0 = b.launch_count()
-    torch.cuda.synchronize()
+    replicas.barrier(r)
     clocks = ClockSampler(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -257,12 +250,13 @@ def ensemble_arm(args, rank, world, local):
     b.step(args.steps, dts)
     ev1.record(stream)
     ev1.synchronize()
+    replicas.barrier(r)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms = replicas.max_over_ranks(r, ev0.elapsed_time(ev1), device="cuda")
     bytes_step = sum((132.0 if len(m["mass"]) else 112.0) * m["n"] ** 3 for m in members)
     peak, kind = measured_peak()
     ach = bytes_step * args.steps / (ms * 1e-3) / 1e9
-    line = {"metric": "grid_cell_steps_per_s", "value": world * cells * args.steps / (ms * 1e-3),
+    line = {"metric": "grid_cell_steps_per_s", "value": replicas.job_rate(r, cells * args.steps, ms * 1e-3),
             "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64", "data": "synthetic",
@@ -304,18 +298,17 @@ def fno_bytes(kind, n=64, C=32, M=16, batch=1):
             "fno_y_idft": ystage + xrow}[kind]
 
 
-def surrogate_arm(args, rank, world, local):
+def surrogate_arm(args, r):
     """The FNO surrogate against the plain solver on 64^3 halos: train on solver trajectories,
     then advance held-out grids by K = 16 steps through the judge (proposal accepted when its mass
     and energy drifts pass, spot-checked against the solver every 8th advance) and by the solver
     alone.  value = cell-steps/s of the surrogate path; plain.value the solver's."""
     import torch
-    from paper_2606_25026_gb300 import build as spe_build, inputs, spe, surrogate as sg
+    from paper_2606_25026_gb300 import inputs, spe, surrogate as sg
+    rank, world, local = r.rank, r.world, r.local
     n, K = 64, 16
     specs = sg.ic_specs(args.fno_train + args.fno_test, seed=2026)
     ics = sg.make_ics(n, specs)
-    spe_build.build()
-    torch.cuda.set_device(local)
     dt = inputs.kinetic_dt(n)
     t0 = time.perf_counter()
     train = sg.generate_pairs(ics[:args.fno_train], n, K, dt, pairs_per_ic=2, warmup_steps=16)
@@ -368,17 +361,21 @@ def surrogate_arm(args, rank, world, local):
     warm = max(args.warmup, 3)
     run_plain(warm)
     run_surrogate(warm)
-    torch.cuda.synchronize()
+    replicas.barrier(r)
     clocks = ClockSampler(local)
     clocks.start()
     t_plain = sg.timed(lambda: run_plain(steps), reps=1)
+    replicas.barrier(r)
     sur.launch_count(reset=True)
     t_sur = sg.timed(lambda: run_surrogate(steps), reps=1)
     sur_launches = sur.launch_count()
+    replicas.barrier(r)
     clk = clocks.stop()
+    t_plain = replicas.max_over_ranks(r, t_plain, device="cuda")
+    t_sur = replicas.max_over_ranks(r, t_sur, device="cuda")
     cells = n ** 3
-    value = world * cells * K * steps / t_sur
-    plain = world * cells * K * steps / t_plain
+    value = replicas.job_rate(r, cells * K * steps, t_sur)
+    plain = replicas.job_rate(r, cells * K * steps, t_plain)
 
     # the forward pass alone (batch 1, graph replay), CUDA events on the network's stream
     x1, b1 = test.psi[:1].contiguous(), test.psi_b[:1].contiguous()
@@ -414,14 +411,14 @@ def surrogate_arm(args, rank, world, local):
     h_in = test.psi[:min(S, 16)].cpu().pin_memory()
     h_out = torch.empty_like(h_in).pin_memory()
     ke = min(steps, 16)
-    torch.cuda.synchronize()
+    replicas.barrier(r)
     t0 = time.perf_counter()
     for i in range(ke):
         g.set_ic(h_in[i % len(h_in)])
         sur.advance(g, K, dt, spot_check=(i % spot_every == 0))
         g.get_psi(out=h_out[i % len(h_out)])
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
+    replicas.barrier(r)
+    t_e2e = replicas.max_over_ranks(r, time.perf_counter() - t0, device="cuda")
 
     line = {
         "metric": "grid_cell_steps_per_s", "value": value, "unit": "cell-steps/s", "n_gpus": world,
@@ -455,7 +452,7 @@ def surrogate_arm(args, rank, world, local):
                                     for k, v in prof.items()}},
         "gpu_launches": int(sur_launches),
         "clocks": clk,
-        "e2e": {"value": world * cells * K * ke / t_e2e, "unit": "cell-steps/s", "steps": ke,
+        "e2e": {"value": replicas.job_rate(r, cells * K * ke, t_e2e), "unit": "cell-steps/s", "steps": ke,
                 "h2d_bytes_per_step": cells * 8, "d2h_bytes_per_step": cells * 8,
                 "what": "pinned-host upload of each held-out field, the judged advance, download of the result"},
     }
@@ -473,25 +470,32 @@ def surrogate_arm(args, rank, world, local):
 
 def main():
     args = parse()
-    rank, world, local = dist_env()
+    r = replicas.from_env()
     if args.impl == "reference":
-        return reference_arm(args, rank, world)
-    if args.workload == "ensemble64":
-        return ensemble_arm(args, rank, world, local)
-    if args.workload == "fno64":
-        return surrogate_arm(args, rank, world, local)
+        return reference_arm(args, r.rank, r.world)
 
     import torch
-    import torch.distributed as dist
     from paper_2606_25026_gb300 import build as spe_build
-    if rank == 0 or world == 1:
+    # the leader compiles; the other ranks find the library up to date after the first barrier
+    if r.leader:
         spe_build.build()
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-        dist.barrier()
-        spe_build.build()
-    torch.cuda.set_device(local)
+    replicas.init(r, "nccl", torch.device("cuda", r.local))
+    spe_build.build()
+    torch.cuda.set_device(r.local)
+    try:
+        if args.workload == "ensemble64":
+            return ensemble_arm(args, r)
+        if args.workload == "fno64":
+            return surrogate_arm(args, r)
+        return grid_arm(args, r)
+    finally:
+        replicas.finish(r)
+
+
+def grid_arm(args, r):
+    import torch
     from paper_2606_25026_gb300 import spe
+    rank, world, local = r.rank, r.world, r.local
 
     psi, pos, vel, mass, dt = make_inputs(args.workload, args.grid)
     nz, ny, nx = psi.shape
@@ -500,10 +504,7 @@ def main():
     stream = torch.cuda.Stream()
 
     def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-            torch.cuda.synchronize()
+        replicas.barrier(r)
 
     # ---------------- device-resident timed region
     prec_flag = spe.SPE_PREC_SPLIT16 if args.prec == "split16" else 0
@@ -531,11 +532,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     launches = g.launch_count()
     prof = g.profile_read()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * ncells * args.steps / (ms * 1e-3)
+    ms = replicas.max_over_ranks(r, ms, device="cuda")
+    value = replicas.job_rate(r, ncells * args.steps, ms * 1e-3)
 
     # roofline of the dominant kernel
     bpc = BYTES_PER_CELL if nstar else BYTES_PER_CELL_NO_STARS
@@ -610,13 +608,10 @@ def main():
             ge.get_particles()
         barrier()
         sec = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([sec], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            sec = float(t.item())
+        sec = replicas.max_over_ranks(r, sec, device="cuda")
         h2d = psi.nbytes + pos.nbytes + vel.nbytes + mass.nbytes
         d2h = ke * 8 + psi.nbytes + pos.nbytes + vel.nbytes
-        line["e2e"] = {"value": world * ncells * ke / sec, "unit": "cell-steps/s", "steps": ke,
+        line["e2e"] = {"value": replicas.job_rate(r, ncells * ke, sec), "unit": "cell-steps/s", "steps": ke,
                        "h2d_bytes_per_step": h2d / ke, "d2h_bytes_per_step": d2h / ke,
                        "what": "pinned-host upload of psi and stars, single-step spe_step calls each followed "
                                "by a device->host read of the step's mass, final download of psi and stars"}
@@ -645,9 +640,6 @@ def main():
 
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
     return 0
 
 
