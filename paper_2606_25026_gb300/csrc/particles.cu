@@ -29,8 +29,10 @@ __device__ __forceinline__ Cic cic_axis(float x, float halfL, float inv_dx, int 
     const float u = (x + halfL) * inv_dx;
     const float fl = floorf(u);
     int i = (int)fl;
-    i %= n;
-    if (i < 0) i += n;
+    if ((unsigned)i >= (unsigned)n) {   // positions are kept in the box: only u = n after rounding lands here
+        i %= n;
+        if (i < 0) i += n;
+    }
     Cic c;
     c.i0 = i;
     c.i1 = (i + 1 == n) ? 0 : i + 1;
@@ -55,6 +57,11 @@ constexpr int kPartThreads = 256;
 constexpr int kBoxBytes = 16384;
 constexpr int kBoxPhi = kBoxBytes / 4;     // floats
 constexpr int kBoxDep = kBoxBytes / 8;     // 64-bit counters
+
+// Exact v / d for 0 <= v, d < 2^16, d >= 2, with m = div_magic(d): the product's error v (m - 2^32/d)
+// / 2^32 < v / 2^32 < 1/d cannot carry v/d past the next integer.
+__device__ __forceinline__ unsigned div_magic(unsigned d) { return 0xffffffffu / d + 1u; }
+__device__ __forceinline__ int div_small(int v, unsigned m) { return (int)__umulhi((unsigned)v, m); }
 
 // Block-wide min and max of three integers over the live threads; results
 // in out[0..2] (min) and out[3..5] (max).  All threads of the block call it.
@@ -83,7 +90,7 @@ __device__ __forceinline__ void block_minmax3(int a, int b, int c, bool live, in
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kPartThreads) particles_kernel(PParams p)
+__global__ void __launch_bounds__(kPartThreads, 4) particles_kernel(PParams p)
 {
     __shared__ __align__(16) unsigned char box_raw[kBoxBytes];
     __shared__ int red[6][kPartThreads / 32];
@@ -112,8 +119,10 @@ __global__ void __launch_bounds__(kPartThreads) particles_kernel(PParams p)
         const int ex = bb[3] - bb[0] + 4, ey = bb[4] - bb[1] + 4, ez = bb[5] - bb[2] + 4;
         const bool tiled = (long long)ex * ey * ez <= kBoxPhi;
         if (tiled) {
+            const unsigned mx = div_magic(ex), my = div_magic(ey);
             for (int v = threadIdx.x; v < ex * ey * ez; v += kPartThreads) {
-                const int a = v % ex, b = (v / ex) % ey, c = v / (ex * ey);
+                const int r = div_small(v, mx), c = div_small(r, my);
+                const int a = v - r * ex, b = r - c * ey;
                 sphi[v] = __ldg(&p.phi[((size_t)wrapi(oz + c, nz) * ny + wrapi(oy + b, ny)) * nx + wrapi(ox + a, nx)]);
             }
             __syncthreads();
@@ -137,12 +146,11 @@ __global__ void __launch_bounds__(kPartThreads) particles_kernel(PParams p)
                         const float w = (a ? cx.w1 : cx.w0) * wy * wz;
                         float dphix, dphiy, dphiz;
                         if (tiled) {
-                            auto at = [&](int uu, int vv, int ww) {
-                                return sphi[((ww - oz) * ey + (vv - oy)) * ex + (uu - ox)];
-                            };
-                            dphix = at(iu + 1, ju, ku) - at(iu - 1, ju, ku);
-                            dphiy = at(iu, ju + 1, ku) - at(iu, ju - 1, ku);
-                            dphiz = at(iu, ju, ku + 1) - at(iu, ju, ku - 1);
+                            const float *q = sphi + ((ku - oz) * ey + (ju - oy)) * ex + (iu - ox);
+                            const int sz = ex * ey;
+                            dphix = q[1] - q[-1];
+                            dphiy = q[ex] - q[-ex];
+                            dphiz = q[sz] - q[-sz];
                         } else {
                             const size_t plane = (size_t)k * ny;
                             const float *row = p.phi + (plane + j) * nx;
@@ -218,10 +226,12 @@ __global__ void __launch_bounds__(kPartThreads) particles_kernel(PParams p)
         if (tiled) {
             __syncthreads();
             unsigned long long *dep = reinterpret_cast<unsigned long long *>(p.dep);
+            const unsigned mx = div_magic(ex), my = div_magic(ey);
             for (int v = threadIdx.x; v < vol; v += kPartThreads) {
                 const unsigned long long q = sdep[v];
                 if (q) {
-                    const int a = v % ex, b = (v / ex) % ey, c = v / (ex * ey);
+                    const int r = div_small(v, mx), c = div_small(r, my);
+                    const int a = v - r * ex, b = r - c * ey;
                     atomicAdd(&dep[((size_t)wrapi(oz + c, nz) * ny + wrapi(oy + b, ny)) * nx + wrapi(ox + a, nx)], q);
                 }
             }

@@ -24,6 +24,31 @@ namespace spe {
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 
+// sin h and cos h of a kick half-angle.  A kick turns the phase by a small angle (|h| well below
+// 1/2 at any stable time step), where the Maclaurin series of sine to h^11 and of cosine to h^10
+// are exact to under 1e-12 relative (the first omitted terms are h^13/13! and h^12/12!), so the
+// only error is the FP32 rounding of the Horner evaluation; larger angles take sincosf.
+__device__ __forceinline__ void half_angle_sincos(float h, float &sh, float &ch)
+{
+    if (fabsf(h) <= 0.5f) {
+        const float s2 = h * h;
+        float ps = -1.f / 39916800.f;
+        ps = fmaf(ps, s2, 1.f / 362880.f);
+        ps = fmaf(ps, s2, -1.f / 5040.f);
+        ps = fmaf(ps, s2, 1.f / 120.f);
+        ps = fmaf(ps, s2, -1.f / 6.f);
+        sh = fmaf(h * s2, ps, h);
+        float pc = -1.f / 3628800.f;
+        pc = fmaf(pc, s2, 1.f / 40320.f);
+        pc = fmaf(pc, s2, -1.f / 720.f);
+        pc = fmaf(pc, s2, 1.f / 24.f);
+        pc = fmaf(pc, s2, -0.5f);
+        ch = fmaf(s2, pc, 1.f);
+    } else {
+        sincosf(h, &sh, &ch);
+    }
+}
+
 template <int N, bool TC = false> struct XCfg {
     static constexpr int T = 16;
     static constexpr int TP = T + 1;
@@ -171,7 +196,7 @@ __global__ void __launch_bounds__(XCfg<N, TC>::NT) xpass_kernel(XParams p)
                     if ((flags & X_WRITE_PHI) && !(flags & X_HAS_PHI)) p.phi_out[(size_t)row * N + n] = pb;
                 }
                 float sh, ch;
-                sincosf(0.5f * ((phi + p.kappa * a2) * p.kick_scale), &sh, &ch);
+                half_angle_sincos(0.5f * ((phi + p.kappa * a2) * p.kick_scale), sh, ch);
                 const float cm1 = -2.f * sh * sh, sn = 2.f * sh * ch;
                 v = make_float2(fmaf(v.x, cm1, fmaf(v.y, sn, v.x)), fmaf(v.y, cm1, fmaf(-v.x, sn, v.y)));
             }
