@@ -248,6 +248,7 @@ def ensemble_arm(args, r):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     b.step(args.steps, dts)
+    b.settle()          # the members' closing half kicks, inside the timed region
     ev1.record(stream)
     ev1.synchronize()
     replicas.barrier(r)
@@ -525,6 +526,7 @@ def grid_arm(args, r):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     g.step(args.steps, dt)
+    g.settle()          # the closing half kick of the last step, inside the timed region
     ev1.record(stream)
     ev1.synchronize()
     barrier()

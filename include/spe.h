@@ -134,12 +134,21 @@ SPE_API int spe_add_particles(spe_grid *g, size_t n, const float *pos3, const fl
 SPE_API int spe_clear_particles(spe_grid *g);
 
 /* Advance nsteps kick-drift-kick steps of size dt (dt may be negative).
- * The half kicks of consecutive steps inside one call are applied as one
- * full kick; the call starts and ends with a half kick so that psi and the
- * particles are synchronised at return.  Unless SPE_ASYNC is set, the call
- * waits for the work and returns SPE_ENONFINITE if the field's mass stopped
- * being finite. */
+ * The half kicks of consecutive steps are applied as one full kick, also
+ * across calls: the closing half kick of a call is deferred, and the next
+ * spe_step with the same dt applies it together with its own leading half
+ * kick, so that a run of single-step calls does the work of one call.  Every
+ * function that reads or changes the state (spe_get_psi, spe_get_particles,
+ * spe_energy, spe_set_ic, ..., spe_sync, spe_settle) applies a deferred kick
+ * first, so psi and the particles are always observed synchronised;
+ * spe_last_mass needs no kick (the mass is measured inside the step).
+ * Unless SPE_ASYNC is set, the call waits for the work and returns
+ * SPE_ENONFINITE if the field's mass stopped being finite. */
 SPE_API int spe_step(spe_grid *g, int nsteps, double dt);
+
+/* Apply a deferred closing half kick now (queued on the grid's stream, no
+ * wait).  A no-op when none is owed. */
+SPE_API int spe_settle(spe_grid *g);
 
 /* Sec. 3.5: dt = safety * 0.5 * min{4/(3 pi) dx^2/eta, 2 pi eta/max|Phi|,
  * 2 pi eta/(|kappa| max|psi|^2)}, dx the smallest cell edge. */
@@ -176,7 +185,8 @@ SPE_API int spe_get_particles(spe_grid *g, float *pos3, float *vel3, int where);
 /* Number of particles currently held. */
 SPE_API int spe_particle_count(spe_grid *g, size_t *n_out);
 
-/* Wait for all work queued on the grid's stream. */
+/* Apply a deferred closing half kick (spe_settle), then wait for all work
+ * queued on the grid's stream. */
 SPE_API int spe_sync(spe_grid *g);
 
 /* Kernel launches issued by this grid since creation (or the last reset). */
@@ -248,8 +258,12 @@ SPE_API int spe_batch_create(const spe_config *cfgs, int count, spe_batch **out)
 SPE_API int spe_batch_grid(spe_batch *b, int index, spe_grid **out);
 /* spe_autotune for every member */
 SPE_API int spe_batch_autotune(spe_batch *b);
-/* nsteps KDK steps of every member, dts[i] for member i; returns after the work completes */
+/* nsteps KDK steps of every member, dts[i] for member i; returns after the work
+ * completes.  Each member's closing half kick is deferred as in spe_step. */
 SPE_API int spe_batch_step(spe_batch *b, int nsteps, const double *dts);
+/* Apply every member's deferred closing half kick: queued on the member
+ * streams and joined into the batch stream (no wait). */
+SPE_API int spe_batch_settle(spe_batch *b);
 /* kernel launches of all members since creation (graph replays counted per node) */
 SPE_API int spe_batch_launch_count(spe_batch *b, unsigned long long *count_out);
 SPE_API int spe_batch_destroy(spe_batch *b);

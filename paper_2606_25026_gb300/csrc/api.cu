@@ -183,6 +183,11 @@ struct spe_grid {
     double mstar;
     double quantum;
     bool phi_valid;
+    // the closing half kick of the last spe_step, not yet applied: the next spe_step with the same
+    // dt merges it into its leading kick, anything that reads or changes the state applies it first
+    bool kick_pending;
+    double pending_h;
+    double pending_dt;
     bool tables_valid;
     double table_dt;
     unsigned long long launches;
@@ -626,6 +631,24 @@ int final_half_kick(spe_grid *g, double h)
     return SPE_OK;
 }
 
+}  // namespace
+
+namespace spe {
+
+// Apply the deferred closing half kick, if any (asynchronously, on the grid's stream).
+int settle(spe_grid *g)
+{
+    if (!g->kick_pending) return SPE_OK;
+    g->kick_pending = false;
+    return final_half_kick(g, g->pending_h);
+}
+
+}  // namespace spe
+
+namespace {
+
+using spe::settle;
+
 // Real-space Phi into g->phi.
 int potential_to_phi(spe_grid *g)
 {
@@ -672,6 +695,7 @@ namespace spe {
 int energy_issue(spe_grid *g, double *host_raw, bool copy_to_host)
 {
     int rc;
+    if ((rc = settle(g))) return rc;
     if ((rc = potential_to_phi(g))) return rc;
     if ((rc = deposit_only(g))) return rc;
     if ((rc = launch(g, KIND_DIAG, [&] {
@@ -916,6 +940,8 @@ int spe_destroy(spe_grid *g)
 int spe_set_ic(spe_grid *g, const void *psi, size_t n, int where)
 {
     if (!g || !psi || n != g->ncells || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
+    const int rc = settle(g);   // the stars still owe the half kick
+    if (rc) return rc;
     cudaError_t e = cudaMemcpyAsync(g->psi, psi, n * sizeof(float2),
                                     where == SPE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->st);
     if (e == cudaSuccess && where == SPE_HOST) e = cudaStreamSynchronize(g->st);
@@ -928,6 +954,7 @@ int spe_add_particles(spe_grid *g, size_t n, const float *pos3, const float *vel
     if (!g || (n && (!pos3 || !vel3 || !mass)) || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
     if (n == 0) return SPE_OK;
     if (g->np + n > g->cfg.max_particles) return SPE_ENOMEM;
+    if (const int rc = settle(g)) return rc;   // before the new stars join
     const size_t o = g->np;
     cudaError_t e = cudaSuccess;
     double msum = 0.0;
@@ -973,6 +1000,7 @@ int spe_add_particles(spe_grid *g, size_t n, const float *pos3, const float *vel
 int spe_clear_particles(spe_grid *g)
 {
     if (!g) return SPE_EINVAL;
+    if (const int rc = settle(g)) return rc;
     g->np = 0;
     g->mstar = 0.0;
     update_quantum(g);
@@ -992,12 +1020,21 @@ int spe_step(spe_grid *g, int nsteps, double dt)
         if (fabs(dt) > bound * (1.0 + 1e-12)) return SPE_ECFL;
     }
     int rc;
+    // a closing half kick still owed by the previous call joins this call's leading kick (as
+    // between the steps of one call) when the step size is the same; otherwise it goes first,
+    // with the tables of its own step
+    if (g->kick_pending && g->pending_dt != dt && (rc = settle(g))) return rc;
     if ((rc = ensure_drift_tables(g, dt))) return rc;
     if (!g->phi_valid && (rc = compute_phi(g))) return rc;
-    if ((rc = step_body(g, 0.5 * dt, dt, false))) return rc;
+    const bool merge = g->kick_pending;
+    const double lead = merge ? g->pending_h + 0.5 * dt : 0.5 * dt;
+    g->kick_pending = false;
+    if ((rc = step_body(g, lead, dt, merge))) return rc;
     g->steps_done++;
     if ((rc = run_full_steps(g, nsteps - 1, dt))) return rc;
-    if ((rc = final_half_kick(g, 0.5 * dt))) return rc;
+    g->kick_pending = true;
+    g->pending_h = 0.5 * dt;
+    g->pending_dt = dt;
     if (g->cfg.flags & SPE_ASYNC) return SPE_OK;
     double mass = 0.0;
     cudaError_t e = cudaMemcpyAsync(&mass, g->diag, sizeof(double), cudaMemcpyDeviceToHost, g->st);
@@ -1032,6 +1069,7 @@ int spe_suggest_dt(spe_grid *g, double safety, double *dt_out)
 {
     if (!g || !dt_out || !(safety > 0)) return SPE_EINVAL;
     int rc;
+    if ((rc = settle(g))) return rc;
     if ((rc = potential_to_phi(g))) return rc;
     if ((rc = launch(g, KIND_DIAG, [&] {
              return launch_grid_diag(g->psi, g->phi, nullptr, 0.f, (float)g->cfg.kappa, g->dv, g->ncells,
@@ -1059,6 +1097,7 @@ int spe_density(spe_grid *g, float *out, int where)
 {
     if (!g || !out || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
     int rc;
+    if ((rc = settle(g))) return rc;
     if ((rc = deposit_only(g))) return rc;
     float *dst = (where == SPE_DEVICE) ? out : g->phi;
     if ((rc = launch(g, KIND_DIAG, [&] {
@@ -1074,6 +1113,7 @@ int spe_potential(spe_grid *g, float *out, int where)
 {
     if (!g || !out || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
     int rc;
+    if ((rc = settle(g))) return rc;
     if ((rc = potential_to_phi(g))) return rc;
     return copy_out(g, out, g->phi, g->ncells * sizeof(float), where);
 }
@@ -1092,6 +1132,7 @@ int spe_set_static_potential(spe_grid *g, const float *phi_b, int where)
 {
     if (!g || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
     if (!g->phib) return SPE_ESTATE;
+    if (const int rc = settle(g)) return rc;   // the owed half kick feels the old potential
     if (!phi_b) {
         g->static_set = false;
         return SPE_OK;
@@ -1108,6 +1149,7 @@ int spe_virial(spe_grid *g, spe_virial_t *out)
 {
     if (!g || !out) return SPE_EINVAL;
     int rc;
+    if ((rc = settle(g))) return rc;
     if ((rc = potential_to_phi(g))) return rc;
     if ((rc = launch(g, KIND_DIAG, [&] {
              return launch_virial(g->psi, g->phi, g->n[0], g->n[1], g->n[2], (float)(0.5 / g->dx[0]),
@@ -1129,6 +1171,7 @@ int spe_virial(spe_grid *g, spe_virial_t *out)
 int spe_get_psi(spe_grid *g, void *out, int where)
 {
     if (!g || !out || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
+    if (const int rc = settle(g)) return rc;
     return copy_out(g, out, g->psi, g->ncells * sizeof(float2), where);
 }
 
@@ -1137,6 +1180,7 @@ int spe_get_particles(spe_grid *g, float *pos3, float *vel3, int where)
     if (!g || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
     const size_t n = g->np;
     if (!n) return SPE_OK;
+    if (const int rc = settle(g)) return rc;
     if (where == SPE_DEVICE) {
         int rc = launch(g, KIND_COPY, [&] {
             return launch_particles_from_soa_by_id(g->px, g->py, g->pz, g->vx, g->vy, g->vz, g->pid, (int)n, pos3,
@@ -1176,7 +1220,14 @@ int spe_particle_count(spe_grid *g, size_t *n_out)
 int spe_sync(spe_grid *g)
 {
     if (!g) return SPE_EINVAL;
+    if (const int rc = settle(g)) return rc;
     return cuerr(cudaStreamSynchronize(g->st));
+}
+
+int spe_settle(spe_grid *g)
+{
+    if (!g) return SPE_EINVAL;
+    return settle(g);
 }
 
 int spe_launch_count(spe_grid *g, unsigned long long *count_out, int reset)
@@ -1515,12 +1566,21 @@ int spe_batch_step(spe_batch *b, int nsteps, const double *dts)
             if (fabs(dts[i]) > 0.5 * 4.0 / (3.0 * kPi) * dx * dx / g->cfg.hbar_over_m * (1.0 + 1e-12)) return SPE_ECFL;
         }
     }
+    // members owe their closing half kicks like lone grids (spe_step): merged into the leading
+    // kick when dt is unchanged, applied first otherwise
+    for (size_t i = 0; i < n; ++i) {
+        spe_grid *g = b->g[i];
+        if (g->kick_pending && g->pending_dt != dts[i] && (rc = settle(g))) return rc;
+    }
     if ((rc = batch_fork(b))) return rc;
     for (size_t i = 0; i < n; ++i) {
         spe_grid *g = b->g[i];
         if ((rc = ensure_drift_tables(g, dts[i]))) return rc;
         if (!g->phi_valid && (rc = compute_phi(g))) return rc;
-        if ((rc = step_body(g, 0.5 * dts[i], dts[i], false))) return rc;
+        const bool merge = g->kick_pending;
+        const double lead = merge ? g->pending_h + 0.5 * dts[i] : 0.5 * dts[i];
+        g->kick_pending = false;
+        if ((rc = step_body(g, lead, dts[i], merge))) return rc;
         g->steps_done++;
     }
     if ((rc = batch_join(b))) return rc;
@@ -1532,13 +1592,25 @@ int spe_batch_step(spe_batch *b, int nsteps, const double *dts)
             b->g[i]->steps_done += nsteps - 1;
             b->g[i]->launches += (unsigned long long)(nsteps - 1) * b->nodes[i];
         }
-        if ((rc = batch_fork(b))) return rc;
     }
-    for (size_t i = 0; i < n; ++i)
-        if ((rc = final_half_kick(b->g[i], 0.5 * dts[i]))) return rc;
-    if ((rc = batch_join(b))) return rc;
+    for (size_t i = 0; i < n; ++i) {
+        spe_grid *g = b->g[i];
+        g->kick_pending = true;
+        g->pending_h = 0.5 * dts[i];
+        g->pending_dt = dts[i];
+    }
     if (cudaStreamSynchronize(b->st) != cudaSuccess) return SPE_ECUDA;
     return SPE_OK;
+}
+
+int spe_batch_settle(spe_batch *b)
+{
+    if (!b) return SPE_EINVAL;
+    int rc;
+    if ((rc = batch_fork(b))) return rc;
+    for (auto g : b->g)
+        if ((rc = settle(g))) return rc;
+    return batch_join(b);
 }
 
 int spe_batch_launch_count(spe_batch *b, unsigned long long *count_out)

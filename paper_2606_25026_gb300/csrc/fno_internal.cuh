@@ -130,6 +130,8 @@ namespace spe {
 // solver internals the judge uses (api.cu)
 constexpr int kEnergyRaw = 18;   // raw energy sums copied per spe_energy
 int energy_issue(spe_grid *g, double *host_raw, bool copy_to_host);
+// apply the grid's deferred closing half kick, if any (spe_settle)
+int settle(spe_grid *g);
 int energy_from_raw(spe_grid *g, const double *raw, spe_energy_t *out);
 float2 *grid_psi(spe_grid *g);
 cudaStream_t grid_stream(spe_grid *g);

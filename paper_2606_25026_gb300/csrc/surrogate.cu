@@ -69,6 +69,7 @@ int issue_private(spe_surrogate *s, double kdt)
     int rc;
     if ((rc = spe_set_ic(s->coarse, s->psi0, s->ncells, SPE_DEVICE))) return rc;
     if ((rc = spe_step(s->coarse, 1, kdt))) return rc;
+    if ((rc = spe::settle(s->coarse))) return rc;
     if (cudaMemcpyAsync(s->psib, spe::grid_psi(s->coarse), s->ncells * sizeof(float2), cudaMemcpyDeviceToDevice,
                         s->own) != cudaSuccess)
         return SPE_ECUDA;
@@ -185,7 +186,8 @@ SPE_API int spe_surrogate_advance(spe_surrogate *s, spe_grid *g, int K, double d
     spe_launch_count(s->coarse, &c0, 0);
     spe_fno_launch_count(s->f, &f0, 0);
     bool replayed = false;
-    // 1. the state, handed to the private stream
+    // 1. the state (with any closing half kick it still owes), handed to the private stream
+    if ((rc = spe::settle(g))) return rc;
     if (cudaMemcpyAsync(s->psi0, spe::grid_psi(g), s->ncells * sizeof(float2), cudaMemcpyDeviceToDevice,
                         spe::grid_stream(g)) != cudaSuccess)
         return SPE_ECUDA;

@@ -31,11 +31,11 @@ SUPPORTED_N = (4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768
 EXPORTED = (
     "spe_workspace_bytes", "spe_create_grid", "spe_destroy", "spe_set_ic", "spe_add_particles",
     "spe_clear_particles", "spe_step", "spe_suggest_dt", "spe_density", "spe_potential", "spe_energy",
-    "spe_last_mass", "spe_get_psi", "spe_get_particles", "spe_particle_count", "spe_sync",
+    "spe_last_mass", "spe_get_psi", "spe_get_particles", "spe_particle_count", "spe_sync", "spe_settle",
     "spe_launch_count", "spe_profile_read", "spe_strerror", "spe_field_energy_noalloc",
     "spe_set_static_potential", "spe_virial", "spe_autotune", "spe_set_schedule", "spe_get_schedule",
     "spe_batch_create", "spe_batch_grid",
-    "spe_batch_autotune", "spe_batch_step", "spe_batch_launch_count", "spe_batch_destroy",
+    "spe_batch_autotune", "spe_batch_step", "spe_batch_settle", "spe_batch_launch_count", "spe_batch_destroy",
     # include/spe_fno.h
     "spe_fno_param_count", "spe_fno_create", "spe_fno_destroy", "spe_fno_set_params", "spe_fno_get_params",
     "spe_fno_get_grads", "spe_fno_forward", "spe_fno_backward", "spe_fno_adam", "spe_fno_sync",
@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH):
         "spe_get_particles": (I, [P, fp, fp, I]),
         "spe_particle_count": (I, [P, ctypes.POINTER(S)]),
         "spe_sync": (I, [P]),
+        "spe_settle": (I, [P]),
         "spe_launch_count": (I, [P, ctypes.POINTER(ctypes.c_ulonglong), I]),
         "spe_profile_read": (I, [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_ulonglong),
                                  ctypes.POINTER(D), I]),
@@ -135,6 +136,7 @@ def load_library(path: str = LIB_PATH):
         "spe_batch_grid": (I, [P, I, ctypes.POINTER(P)]),
         "spe_batch_autotune": (I, [P]),
         "spe_batch_step": (I, [P, I, ctypes.POINTER(D)]),
+        "spe_batch_settle": (I, [P]),
         "spe_batch_launch_count": (I, [P, ctypes.POINTER(ctypes.c_ulonglong)]),
         "spe_batch_destroy": (I, [P]),
         "spe_fno_param_count": (I, [ctypes.POINTER(spe_fno_config), ctypes.POINTER(S)]),
@@ -280,6 +282,10 @@ class Grid:
 
     def sync(self):
         _check(self._lib.spe_sync(self._h), "spe_sync")
+
+    def settle(self):
+        """Queue the closing half kick the last step() deferred (no wait)."""
+        _check(self._lib.spe_settle(self._h), "spe_settle")
 
     # -- state out
     def _field_out(self, fn, what, out, dtype_np, dtype_t):
@@ -449,6 +455,10 @@ class Batch:
     def step(self, nsteps, dts):
         d = (ctypes.c_double * len(self.members))(*[float(v) for v in dts])
         _check(self._lib.spe_batch_step(self._h, int(nsteps), d), "spe_batch_step")
+
+    def settle(self):
+        """Queue every member's deferred closing half kick on the batch stream (no wait)."""
+        _check(self._lib.spe_batch_settle(self._h), "spe_batch_settle")
 
     def launch_count(self) -> int:
         out = ctypes.c_ulonglong()

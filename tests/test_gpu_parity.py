@@ -275,7 +275,9 @@ def test_device_buffers_and_launch_count(spe):
     g.set_ic(torch.from_numpy(psi).cuda())
     g.launch_count(reset=True)
     g.step(4, 1e-4)
-    assert g.launch_count() == 4 * 8 + 1 + 4  # 8 kernels per step, the final kick, Phi(0) solve
+    assert g.launch_count() == 4 * 8 + 4      # 8 kernels per step, Phi(0) solve; the closing kick deferred
+    g.settle()
+    assert g.launch_count() == 4 * 8 + 4 + 1  # ... and applied
     out = torch.empty(psi.shape, dtype=torch.complex64, device="cuda")
     g.get_psi(out)
     assert rel_l2(out.cpu().numpy(), g.get_psi()) == 0.0
