@@ -188,6 +188,9 @@ struct spe_grid {
     bool kick_pending;
     double pending_h;
     double pending_dt;
+    // the raw mass sum a blocking spe_step read back (valid until anything writes diag[0] again)
+    double host_mass;
+    bool host_mass_valid;
     bool tables_valid;
     double table_dt;
     unsigned long long launches;
@@ -422,6 +425,7 @@ int static_flag(spe_grid *g) { return g->static_set ? X_STATIC : 0; }
 int compute_phi(spe_grid *g)
 {
     int rc = SPE_OK;
+    g->host_mass_valid = false;   // the density pass below rewrites diag[0]
     if (!g->gravity) {
         g->phi_valid = true;
         return SPE_OK;
@@ -495,6 +499,7 @@ int sort_particles(spe_grid *g)
 int step_body(spe_grid *g, double dtk, double dt, bool absorb_prev)
 {
     int rc;
+    g->host_mass_valid = false;
     const bool grav = g->gravity;
     const bool parts = g->np > 0;
     const bool skick = parts && stars_kicked(g);
@@ -587,12 +592,14 @@ int ensure_step_graph(spe_grid *g, double dt)
     return SPE_OK;
 }
 
-// Steps 2..nsteps of a call (dt_k = dt), by graph replay when allowed.
-int run_full_steps(spe_grid *g, int count, double dt)
+// Full steps (dt_k = dt, the previous step's absorbing layer applied), by graph replay when
+// allowed: from two steps up, or from one when single is set (a run of single-step calls, whose
+// every step is a full one).
+int run_full_steps(spe_grid *g, int count, double dt, bool single = false)
 {
     int rc;
     if (count <= 0) return SPE_OK;
-    if (!graphs_enabled(g) || count < 2) {
+    if (!graphs_enabled(g) || (count < 2 && !single)) {
         for (int s = 0; s < count; ++s) {
             if ((rc = step_body(g, dt, dt, true))) return rc;
             g->steps_done++;
@@ -1029,9 +1036,15 @@ int spe_step(spe_grid *g, int nsteps, double dt)
     const bool merge = g->kick_pending;
     const double lead = merge ? g->pending_h + 0.5 * dt : 0.5 * dt;
     g->kick_pending = false;
-    if ((rc = step_body(g, lead, dt, merge))) return rc;
-    g->steps_done++;
-    if ((rc = run_full_steps(g, nsteps - 1, dt))) return rc;
+    g->host_mass_valid = false;
+    if (merge && lead == dt) {
+        // the owed half kick and this call's leading one make the full kick of a step inside a call
+        if ((rc = run_full_steps(g, nsteps, dt, true))) return rc;
+    } else {
+        if ((rc = step_body(g, lead, dt, merge))) return rc;
+        g->steps_done++;
+        if ((rc = run_full_steps(g, nsteps - 1, dt))) return rc;
+    }
     g->kick_pending = true;
     g->pending_h = 0.5 * dt;
     g->pending_dt = dt;
@@ -1041,6 +1054,8 @@ int spe_step(spe_grid *g, int nsteps, double dt)
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     if (e != cudaSuccess) return SPE_ECUDA;
     if (!isfinite(mass)) return SPE_ENONFINITE;
+    g->host_mass = mass;          // spe_last_mass answers from here until the next step
+    g->host_mass_valid = true;
     if (g->tc) {
         int st = 0;
         e = cudaMemcpyAsync(&st, g->status, sizeof(int), cudaMemcpyDeviceToHost, g->st);
@@ -1057,6 +1072,10 @@ int spe_step(spe_grid *g, int nsteps, double dt)
 int spe_last_mass(spe_grid *g, double *mass_out)
 {
     if (!g || !mass_out) return SPE_EINVAL;
+    if (g->host_mass_valid) {
+        *mass_out = g->host_mass * g->dv;
+        return SPE_OK;
+    }
     double m = 0.0;
     cudaError_t e = cudaMemcpyAsync(&m, g->diag, sizeof(double), cudaMemcpyDeviceToHost, g->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
@@ -1571,6 +1590,7 @@ int spe_batch_step(spe_batch *b, int nsteps, const double *dts)
     for (size_t i = 0; i < n; ++i) {
         spe_grid *g = b->g[i];
         if (g->kick_pending && g->pending_dt != dts[i] && (rc = settle(g))) return rc;
+        g->host_mass_valid = false;
     }
     if ((rc = batch_fork(b))) return rc;
     for (size_t i = 0; i < n; ++i) {
