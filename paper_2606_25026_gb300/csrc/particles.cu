@@ -128,44 +128,66 @@ __global__ void __launch_bounds__(kPartThreads, 4) particles_kernel(PParams p)
             __syncthreads();
         }
         float gx = 0.f, gy = 0.f, gz = 0.f;
-        if (live) {
+        if (live && tiled) {
+            // the eight corners' central differences read 32 distinct nodes: the four x nodes
+            // i0-1 .. i0+2 of the corner rows, and the rows j0-1, j0+2 and planes k0-1, k0+2
+            const int sz = ex * ey;
+            const float *q0 = sphi + ((cz.i0 - oz) * ey + (cy.i0 - oy)) * ex + (cx.i0 - ox);
+            float r[2][2][4];
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int b2 = 0; b2 < 2; ++b2)
+#pragma unroll
+                    for (int a4 = 0; a4 < 4; ++a4) r[c][b2][a4] = q0[c * sz + b2 * ex + a4 - 1];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float wz = c ? cz.w1 : cz.w0;
+#pragma unroll
+                for (int b2 = 0; b2 < 2; ++b2) {
+                    const float wy = b2 ? cy.w1 : cy.w0;
+#pragma unroll
+                    for (int a = 0; a < 2; ++a) {
+                        const float w = (a ? cx.w1 : cx.w0) * wy * wz;
+                        const float dphix = r[c][b2][a + 2] - r[c][b2][a];
+                        const float yp = b2 ? q0[c * sz + 2 * ex + a] : r[c][1][a + 1];
+                        const float ym = b2 ? r[c][0][a + 1] : q0[c * sz - ex + a];
+                        const float zp = c ? q0[2 * sz + b2 * ex + a] : r[1][b2][a + 1];
+                        const float zm = c ? r[0][b2][a + 1] : q0[-sz + b2 * ex + a];
+                        gx -= w * dphix;
+                        gy -= w * (yp - ym);
+                        gz -= w * (zp - zm);
+                    }
+                }
+            }
+        } else if (live) {
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const int k = c ? cz.i1 : cz.i0;
-                const int ku = cz.i0 + c;     // unwrapped
                 const float wz = c ? cz.w1 : cz.w0;
 #pragma unroll
                 for (int b2 = 0; b2 < 2; ++b2) {
                     const int j = b2 ? cy.i1 : cy.i0;
-                    const int ju = cy.i0 + b2;
                     const float wy = b2 ? cy.w1 : cy.w0;
 #pragma unroll
                     for (int a = 0; a < 2; ++a) {
                         const int ii = a ? cx.i1 : cx.i0;
-                        const int iu = cx.i0 + a;
                         const float w = (a ? cx.w1 : cx.w0) * wy * wz;
-                        float dphix, dphiy, dphiz;
-                        if (tiled) {
-                            const float *q = sphi + ((ku - oz) * ey + (ju - oy)) * ex + (iu - ox);
-                            const int sz = ex * ey;
-                            dphix = q[1] - q[-1];
-                            dphiy = q[ex] - q[-ex];
-                            dphiz = q[sz] - q[-sz];
-                        } else {
-                            const size_t plane = (size_t)k * ny;
-                            const float *row = p.phi + (plane + j) * nx;
-                            dphix = __ldg(&row[wrapi(ii + 1, nx)]) - __ldg(&row[wrapi(ii - 1, nx)]);
-                            dphiy = __ldg(&p.phi[(plane + wrapi(j + 1, ny)) * nx + ii]) -
-                                    __ldg(&p.phi[(plane + wrapi(j - 1, ny)) * nx + ii]);
-                            dphiz = __ldg(&p.phi[((size_t)wrapi(k + 1, nz) * ny + j) * nx + ii]) -
-                                    __ldg(&p.phi[((size_t)wrapi(k - 1, nz) * ny + j) * nx + ii]);
-                        }
+                        const size_t plane = (size_t)k * ny;
+                        const float *row = p.phi + (plane + j) * nx;
+                        const float dphix = __ldg(&row[wrapi(ii + 1, nx)]) - __ldg(&row[wrapi(ii - 1, nx)]);
+                        const float dphiy = __ldg(&p.phi[(plane + wrapi(j + 1, ny)) * nx + ii]) -
+                                            __ldg(&p.phi[(plane + wrapi(j - 1, ny)) * nx + ii]);
+                        const float dphiz = __ldg(&p.phi[((size_t)wrapi(k + 1, nz) * ny + j) * nx + ii]) -
+                                            __ldg(&p.phi[((size_t)wrapi(k - 1, nz) * ny + j) * nx + ii]);
                         gx -= w * dphix;
                         gy -= w * dphiy;
                         gz -= w * dphiz;
                     }
                 }
             }
+        }
+        if (live) {
             vx += p.kick * gx * p.gx_scale;
             vy += p.kick * gy * p.gy_scale;
             vz += p.kick * gz * p.gz_scale;
