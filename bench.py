@@ -39,7 +39,9 @@ from paper_2606_25026_gb300 import replicas  # noqa: E402
 #   x_kick_fwd        : R psi 8 + R Phi_hat 4 + W psi 8 + W Phi 4           = 24
 #   y_fft_psi         : R 8 + W 8                                           = 16
 #   z_fft_drift       : R 8 + W 8                                           = 16
-#   x_inv_density_r2c : R psi_hat 8 + R deposit 8 + W deposit 8 (clear) + W psi 8 + W rho_hat 4 = 36
+#   x_inv_density_r2c : R psi_hat 8 + R deposit 8 + W deposit 8 (clear) + W psi 8 + W rho_hat 4 = 36,
+#                       the deposit's 16 only on rows (y, z) that hold stars' mass: 20 + 16 f, f the
+#                       fraction of such rows (deposit_row_fraction), 36 at f = 1
 #   y_fft_rho, z_fft_poisson : R 4 + W 4 (half spectrum)                    = 8
 #   x_kick_final      : R psi 8 + R Phi_hat 4 + W psi 8 + W Phi 4           = 24
 BYTES_PER_CELL = {
@@ -48,6 +50,19 @@ BYTES_PER_CELL = {
 }
 BYTES_PER_CELL_NO_STARS = dict(BYTES_PER_CELL, x_kick_fwd=20.0, x_inv_density_r2c=20.0, x_kick_final=20.0)
 FALLBACK_HBM_GBS = 6800.0
+
+
+def deposit_row_fraction(pos, shape, L=1.0):
+    """Fraction of the (y, z) rows that the stars' CIC stencils (nodes i0, i0 + 1 per axis) touch:
+    the density pass reads and clears the deposit of those rows only."""
+    nz, ny, nx = shape
+    if len(pos) == 0:
+        return 0.0
+    u = (np.asarray(pos, dtype=np.float64) + 0.5 * L) / L
+    j0 = np.floor(u[:, 1] * ny).astype(np.int64) % ny
+    k0 = np.floor(u[:, 2] * nz).astype(np.int64) % nz
+    rows = np.concatenate([((k0 + dz) % nz) * ny + (j0 + dy) % ny for dy in (0, 1) for dz in (0, 1)])
+    return float(np.unique(rows).size) / (ny * nz)
 
 
 def parse():
@@ -254,7 +269,9 @@ def ensemble_arm(args, r):
     replicas.barrier(r)
     clk = clocks.stop()
     ms = replicas.max_over_ranks(r, ev0.elapsed_time(ev1), device="cuda")
-    bytes_step = sum((132.0 if len(m["mass"]) else 112.0) * m["n"] ** 3 for m in members)
+    # 112 B/cell without stars; with stars + 4 (Phi for the stars) + 16 f (the deposit's rows)
+    bytes_step = sum(((116.0 + 16.0 * deposit_row_fraction(m["pos"], (m["n"],) * 3)) if len(m["mass"]) else 112.0)
+                     * m["n"] ** 3 for m in members)
     peak, kind = measured_peak()
     ach = bytes_step * args.steps / (ms * 1e-3) / 1e9
     line = {"metric": "grid_cell_steps_per_s", "value": replicas.job_rate(r, cells * args.steps, ms * 1e-3),
@@ -265,7 +282,8 @@ def ensemble_arm(args, r):
                        "sizes": {str(n): sum(1 for m in members if m["n"] == n) for n in (64, 96, 128, 192)},
                        "cells": cells, "stars": stars, "autotune": not args.no_autotune},
             "step_roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                              "model": "132 B/cell/step with stars, 112 without, per member"},
+                              "model": "per member 112 B/cell/step without stars, 116 + 16 f with (f the "
+                                       "fraction of rows holding deposits)"},
             "gpu_launches": int(b.launch_count() - l0), "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -538,7 +556,8 @@ def grid_arm(args, r):
     value = replicas.job_rate(r, ncells * args.steps, ms * 1e-3)
 
     # roofline of the dominant kernel
-    bpc = BYTES_PER_CELL if nstar else BYTES_PER_CELL_NO_STARS
+    frows = deposit_row_fraction(pos, psi.shape) if nstar else 0.0
+    bpc = dict(BYTES_PER_CELL, x_inv_density_r2c=20.0 + 16.0 * frows) if nstar else BYTES_PER_CELL_NO_STARS
     dom = max((k for k in prof if k in bpc), key=lambda k: prof[k][1])
     n_launch, dom_ms = prof[dom]
     per_launch_s = dom_ms * 1e-3 / max(n_launch, 1)
@@ -565,7 +584,8 @@ def grid_arm(args, r):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                      else "fallback 6800 GB/s", "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "bytes_per_cell": bpc[dom], "launches": n_launch,
+                     "traffic": traffic, "bytes_per_cell": bpc[dom], "deposit_row_fraction": frows,
+                     "launches": n_launch,
                      "avg_launch_ms": per_launch_s * 1e3},
         "step_roofline": {"bytes_per_cell_step": step_bytes,
                           "achieved_GBs": step_bytes * ncells * args.steps / (ms * 1e-3) / 1e9,

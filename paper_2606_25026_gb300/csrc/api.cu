@@ -91,7 +91,8 @@ struct ProfRec {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t psi, phik, phi, phib, dep, part, bins, tw, k2, drift, absorb, tcw, partials, counter, diag, status, total;
+    size_t psi, phik, phi, phib, dep, dflag, part, bins, tw, k2, drift, absorb, tcw, partials, counter, diag, status,
+        total;
 };
 
 int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
@@ -112,6 +113,8 @@ int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
     L->phi = off;      off = align256(off + ncells * sizeof(float));
     L->phib = off;     off = align256(off + ((c->flags & SPE_STATIC_POTENTIAL) ? ncells * sizeof(float) : 0));
     L->dep = off;      off = align256(off + (c->max_particles ? ncells * sizeof(long long) : 0));
+    // one byte per row marking the rows whose deposit may be nonzero (padded: read 16 at a time)
+    L->dflag = off;    off = align256(off + (c->max_particles ? (size_t)c->ny * c->nz + 16 : 0));
     // two sets of star arrays (x, y, z, vx, vy, vz, m, id) for reordering, sort keys, block counters
     L->part = off;     off = align256(off + 17 * align256(c->max_particles * sizeof(float)));
     L->bins = off;     off = align256(off + sizeof(int) * (size_t)((c->nx + 3) / 4) * ((c->ny + 3) / 4) * ((c->nz + 3) / 4));
@@ -146,6 +149,7 @@ struct spe_grid {
     float2 *psi, *phik;
     float *phi;
     long long *dep;
+    unsigned char *dflag;   // rows whose deposit may be nonzero (set by the star kernel, cleared by the density pass)
     float *px, *py, *pz, *vx, *vy, *vz, *pm;
     unsigned int *pid;            // insertion index of the star in each memory slot
     float *alt[7];                // second set of star arrays (reordering target)
@@ -248,6 +252,7 @@ XParams base_x(spe_grid *g)
     p.phik = g->phik;
     p.phi_out = g->phi;
     p.dep = g->dep;
+    p.dflag = g->dflag;
     p.tw = g->tw[0];
     p.k2 = g->k2[0];
     p.rows = g->n[1] * g->n[2];
@@ -330,6 +335,7 @@ PParams base_p(spe_grid *g)
     p.m = g->pm;
     p.phi = g->phi;
     p.dep = g->dep;
+    p.dflag = g->dflag;
     p.n = (int)g->np;
     p.nx = g->n[0]; p.ny = g->n[1]; p.nz = g->n[2];
     p.Lx = (float)g->L[0]; p.Ly = (float)g->L[1]; p.Lz = (float)g->L[2];
@@ -846,6 +852,7 @@ int spe_create_grid(const spe_config *cfg, void *workspace, size_t workspace_byt
     g->phik = (float2 *)(b + L.phik);
     g->phi = (float *)(b + L.phi);
     g->dep = cfg->max_particles ? (long long *)(b + L.dep) : nullptr;
+    g->dflag = cfg->max_particles ? (unsigned char *)(b + L.dflag) : nullptr;
     const size_t pstride = align256(cfg->max_particles * sizeof(float));
     float **parr[7] = {&g->px, &g->py, &g->pz, &g->vx, &g->vy, &g->vz, &g->pm};
     for (int i = 0; i < 7; ++i) *parr[i] = (float *)(b + L.part + i * pstride);

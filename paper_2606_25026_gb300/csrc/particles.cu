@@ -12,7 +12,9 @@
 // Deposit: every particle adds round(m w / q) to a 64-bit integer per node,
 // q a mass quantum (total star mass / 2^50).  Integer addition is
 // associative, so the deposited field does not depend on the order in
-// which threads run: the step stays bitwise reproducible.
+// which threads run: the step stays bitwise reproducible.  Every row (y, z)
+// that receives mass is also marked in a byte array, so that the density
+// pass reads and clears only the rows that can hold deposits.
 #include "spe_internal.cuh"
 
 #include <climits>
@@ -241,6 +243,7 @@ __global__ void __launch_bounds__(kPartThreads, 4) particles_kernel(PParams p)
                             reinterpret_cast<unsigned long long *>(p.dep) + ((size_t)k * ny + j) * nx;
                         if (q0) atomicAdd(&row[cx.i0], (unsigned long long)q0);
                         if (q1) atomicAdd(&row[cx.i1], (unsigned long long)q1);
+                        if (q0 | q1) p.dflag[(size_t)k * ny + j] = 1;
                     }
                 }
             }
@@ -254,7 +257,9 @@ __global__ void __launch_bounds__(kPartThreads, 4) particles_kernel(PParams p)
                 if (q) {
                     const int r = div_small(v, mx), c = div_small(r, my);
                     const int a = v - r * ex, b = r - c * ey;
-                    atomicAdd(&dep[((size_t)wrapi(oz + c, nz) * ny + wrapi(oy + b, ny)) * nx + wrapi(ox + a, nx)], q);
+                    const size_t row = (size_t)wrapi(oz + c, nz) * ny + wrapi(oy + b, ny);
+                    atomicAdd(&dep[row * nx + wrapi(ox + a, nx)], q);
+                    p.dflag[row] = 1;   // every writer stores the same byte
                 }
             }
         }

@@ -38,6 +38,7 @@ struct XParams {
     float2 *phik;             // rows of P complex (half spectrum)
     float *phi_out;           // rows of nx floats (X_WRITE_PHI)
     long long *dep;           // fixed-point star mass per node (X_DEP)
+    unsigned char *dflag;     // per row: nonzero when the row's deposit may be nonzero (X_DEP)
     const float4 *tw;         // nx twiddles, (hi, lo) float pairs
     const float *k2;          // nx values of kx^2 (X_KIN)
     int rows;                 // ny * nz
@@ -100,6 +101,7 @@ struct PParams {
     const float *m;
     const float *phi;        // nodes, x fastest
     long long *dep;          // fixed-point deposit (PK_DEPOSIT)
+    unsigned char *dflag;    // set to 1 for every row (y + ny z) that receives deposit
     int n;
     int nx, ny, nz;
     float Lx, Ly, Lz;

@@ -231,15 +231,22 @@ __global__ void __launch_bounds__(XCfg<N, TC>::NT) xpass_kernel(XParams p)
             if (row < p.rows) cp_async8(&tile[n * TP + t], &p.psi[(size_t)row * N + n]);
             else tile[n * TP + t] = make_float2(0.f, 0.f);
         }
+        // rows the star kernel did not mark hold no deposit: neither read nor cleared
+        unsigned live_rows = 0;   // bit t: row row0 + t is marked
+        if (flags & X_DEP) {
+            const uint4 f = __ldg(reinterpret_cast<const uint4 *>(p.dflag + row0));
+            const unsigned w[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+                if (((w[t >> 2] >> (8 * (t & 3))) & 0xffu) && row0 + t < p.rows) live_rows |= 1u << t;
+        }
         if (flags & X_DEP) {
             // loads only: a zero store to an address whose load is still in flight has to wait
             // for that load, which serialises the loop on memory latency (measured 4x slower)
             const long long *__restrict__ dep = p.dep + (size_t)row0 * N;
 #pragma unroll 4
-            for (int idx = tid; idx < T * N; idx += NT) {
-                const int row = row0 + idx / N;
-                aux[idx] = (row < p.rows) ? (float)__ldcs(&dep[idx]) * p.dep_scale : 0.f;
-            }
+            for (int idx = tid; idx < T * N; idx += NT)
+                aux[idx] = ((live_rows >> (idx / N)) & 1u) ? (float)__ldcs(&dep[idx]) * p.dep_scale : 0.f;
         }
         cp_async_wait_all();
         __syncthreads();
@@ -247,7 +254,8 @@ __global__ void __launch_bounds__(XCfg<N, TC>::NT) xpass_kernel(XParams p)
             // every deposit value of the tile has been consumed by now: clear for the next step
             long long *__restrict__ dep = p.dep + (size_t)row0 * N;
             for (int idx = tid; idx < T * N; idx += NT)
-                if (row0 + idx / N < p.rows) __stcs(&dep[idx], 0ll);
+                if ((live_rows >> (idx / N)) & 1u) __stcs(&dep[idx], 0ll);
+            if (tid < T && ((live_rows >> tid) & 1u)) p.dflag[row0 + tid] = 0;
         }
         if (ifft) tfft<N, T, TP, NT, +1, TC>(tile, p.tw, tcs, p.status);
         float msum = 0.f;
