@@ -197,6 +197,35 @@ def test_full_size_256_with_1e6_stars_parity(spe):
     assert periodic_err(gp, op, 1.0) <= POS_TOL
 
 
+def test_fast_stars_sweeping_rows_parity(spe):
+    """Stars spread over the whole box and moving ~0.7 cells per step across y and z rows: the
+    density pass must read every row that got deposit (rows are marked by the star kernel and
+    cleared by the density pass), also after energy() deposited and cleared on its own."""
+    n = 32
+    rng = np.random.default_rng(91)
+    psi = inputs.gaussian_packets(n, seed=92).astype(np.complex64)
+    dt = inputs.kinetic_dt(n)
+    m = 2000
+    pos = rng.uniform(-0.5, 0.5, (m, 3)).astype(np.float32)
+    vel = (rng.choice([-1.0, 1.0], (m, 3)) * rng.uniform(0.4, 0.7, (m, 3)) / n / dt).astype(np.float32)
+    mass = np.full(m, 0.2 / m, np.float32)
+    g = spe.Grid(n, G=1.0, max_particles=m)
+    g.set_ic(psi)
+    g.add_particles(pos, vel, mass)
+    o = oracle.Oracle(n, n, n, 1.0, G=1.0)
+    o.set_ic(as_oracle(psi))
+    o.set_particles(as_oracle(pos), as_oracle(vel), as_oracle(mass))
+    for call in range(3):
+        g.step(5, dt)
+        o.step(5, dt)
+        eg, eo = g.energy(), o.energy()
+        assert abs(eg["potential"] - eo["potential"]) <= 1e-5 * abs(eo["potential"]), call
+    assert rel_l2(g.get_psi(), o.get_psi()) <= PSI_TOL
+    gp, _ = g.get_particles()
+    op, _ = o.get_particles()
+    assert periodic_err(gp, op, 1.0) <= POS_TOL
+
+
 # --------------------------------------------------------------------------- properties at any size
 
 
