@@ -605,38 +605,43 @@ def grid_arm(args, r):
         h_vel = torch.from_numpy(vel).pin_memory()
         h_mass = torch.from_numpy(mass).pin_memory()
         o_psi = torch.empty(psi.shape, dtype=torch.complex64).pin_memory()
-        o_pos = np.empty((nstar, 3), np.float32)
-        ge = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, flags=prec_flag, stream=stream)
+        ge = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, flags=prec_flag | spe.SPE_ASYNC, stream=stream)
         if not args.no_autotune:
             ge.autotune()
         ke = max(1, min(args.steps, 200))
+        h_mass_out = torch.zeros(ke, dtype=torch.float64).pin_memory()
         # warm the path once
         ge.set_ic(h_psi)
         if nstar:
             ge.add_particles(h_pos, h_vel, h_mass)
         ge.step(2, dt)
-        ge.last_mass()
+        ge.mass_async(h_mass_out[:1])
+        ge.sync()
         barrier()
         t0 = time.perf_counter()
         ge.set_ic(h_psi)
         ge.clear_particles()
         if nstar:
             ge.add_particles(h_pos, h_vel, h_mass)
-        for _ in range(ke):
+        for k in range(ke):
             ge.step(1, dt)
-            ge.last_mass()
+            ge.mass_async(h_mass_out[k:k + 1])
         ge.get_psi(o_psi)
         if nstar:
             ge.get_particles()
         barrier()
         sec = time.perf_counter() - t0
+        masses = h_mass_out.numpy()
+        if not (np.isfinite(masses).all() and np.abs(masses / masses[0] - 1.0).max() < 1e-5):
+            raise RuntimeError(f"per-step masses read back in the e2e loop are off: {masses[:4]} ...")
         sec = replicas.max_over_ranks(r, sec, device="cuda")
         h2d = psi.nbytes + pos.nbytes + vel.nbytes + mass.nbytes
         d2h = ke * 8 + psi.nbytes + pos.nbytes + vel.nbytes
         line["e2e"] = {"value": replicas.job_rate(r, ncells * ke, sec), "unit": "cell-steps/s", "steps": ke,
                        "h2d_bytes_per_step": h2d / ke, "d2h_bytes_per_step": d2h / ke,
-                       "what": "pinned-host upload of psi and stars, single-step spe_step calls each followed "
-                               "by a device->host read of the step's mass, final download of psi and stars"}
+                       "what": "pinned-host upload of psi and stars; single-step SPE_ASYNC spe_step calls, each "
+                               "followed by a device->host copy of that step's mass into pinned memory "
+                               "(spe_mass_async, checked after the loop); final download of psi and stars"}
         ge.destroy()
         del ge
 

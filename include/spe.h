@@ -175,6 +175,13 @@ SPE_API int spe_energy(spe_grid *g, spe_energy_t *out);
 /* Mass of the field as computed inside the last step (no extra pass). */
 SPE_API int spe_last_mass(spe_grid *g, double *mass_out);
 
+/* Queue a copy of the same mass (one double, cell volume applied) to dst on
+ * the grid's stream and return without waiting: dst in pinned host memory or
+ * device memory (pageable host memory works but makes the copy wait).  The
+ * value lands when the stream reaches this point, so a loop of SPE_ASYNC
+ * spe_step calls can read every step's mass back without stalling the GPU. */
+SPE_API int spe_mass_async(spe_grid *g, double *dst);
+
 /* Copy psi out: nx*ny*nz complex64 values. */
 SPE_API int spe_get_psi(spe_grid *g, void *out, int where);
 

@@ -262,6 +262,7 @@ XParams base_x(spe_grid *g)
     p.partials = g->partials;
     p.counter = g->counter;
     p.result = g->diag;
+    p.mass_scale = g->dv;
     p.absorb_x = g->absorb;
     p.absorb_y = g->absorb + g->n[0];
     p.absorb_z = g->absorb + g->n[0] + g->n[1];
@@ -972,7 +973,24 @@ int spe_add_particles(spe_grid *g, size_t n, const float *pos3, const float *vel
     const size_t o = g->np;
     cudaError_t e = cudaSuccess;
     double msum = 0.0;
-    if (where == SPE_HOST) {
+    if (where == SPE_HOST && 7 * n <= g->ncells) {
+        // staged through the real-potential buffer (every step rewrites it before reading it), so the
+        // wrap and the AoS -> SoA split run on the device
+        float *stage = g->phi;
+        e = cudaMemcpyAsync(stage, pos3, 3 * n * sizeof(float), cudaMemcpyHostToDevice, g->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(stage + 3 * n, vel3, 3 * n * sizeof(float), cudaMemcpyHostToDevice, g->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(stage + 6 * n, mass, n * sizeof(float), cudaMemcpyHostToDevice, g->st);
+        for (size_t i = 0; i < n; ++i) msum += mass[i];
+        if (e == cudaSuccess)
+            e = launch_particles_to_soa(stage, stage + 3 * n, stage + 6 * n, (int)n, g->px + o, g->py + o,
+                                        g->pz + o, g->vx + o, g->vy + o, g->vz + o, g->pm + o, (float)g->L[0],
+                                        (float)g->L[1], (float)g->L[2], g->st);
+        g->launches++;
+        // the caller may reuse its arrays on return
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    } else if (where == SPE_HOST) {
         std::vector<float> soa(7 * n);
         for (size_t i = 0; i < n; ++i) {
             for (int a = 0; a < 3; ++a) {
@@ -1089,6 +1107,12 @@ int spe_last_mass(spe_grid *g, double *mass_out)
     if (e != cudaSuccess) return SPE_ECUDA;
     *mass_out = m * g->dv;
     return SPE_OK;
+}
+
+int spe_mass_async(spe_grid *g, double *dst)
+{
+    if (!g || !dst) return SPE_EINVAL;
+    return cuerr(cudaMemcpyAsync(dst, g->diag + 1, sizeof(double), cudaMemcpyDefault, g->st));
 }
 
 int spe_suggest_dt(spe_grid *g, double safety, double *dt_out)
@@ -1214,6 +1238,21 @@ int spe_get_particles(spe_grid *g, float *pos3, float *vel3, int where)
         });
         if (rc) return rc;
         return cuerr(cudaStreamSynchronize(g->st));
+    }
+    if (6 * n <= g->ncells) {
+        // ordered on the device into the real-potential buffer (free between steps), then copied out
+        float *stage = g->phi;
+        int rc = launch(g, KIND_COPY, [&] {
+            return launch_particles_from_soa_by_id(g->px, g->py, g->pz, g->vx, g->vy, g->vz, g->pid, (int)n,
+                                                   pos3 ? stage : nullptr, vel3 ? stage + 3 * n : nullptr, g->st);
+        });
+        if (rc) return rc;
+        cudaError_t e = cudaSuccess;
+        if (pos3) e = cudaMemcpyAsync(pos3, stage, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, g->st);
+        if (vel3 && e == cudaSuccess)
+            e = cudaMemcpyAsync(vel3, stage + 3 * n, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, g->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+        return cuerr(e);
     }
     std::vector<float> soa(6 * n);
     std::vector<unsigned int> id(n);

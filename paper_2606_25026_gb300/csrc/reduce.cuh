@@ -45,10 +45,12 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], int maxmask, double
 }
 
 // All blocks of the launch must call this exactly once.  partials holds
-// nblocks * K doubles; counter starts (and ends) at 0.
+// nblocks * K doubles; counter starts (and ends) at 0.  With out_scaled, the
+// results times scale are written there as well.
 template <int K, int NT>
 __device__ __forceinline__ void grid_reduce(double (&v)[K], int maxmask, double *partials,
-                                            unsigned int *counter, double *out)
+                                            unsigned int *counter, double *out, double *out_scaled = nullptr,
+                                            double scale = 1.0)
 {
     __shared__ double sh[K * (NT / 32)];
     __shared__ int last;
@@ -79,6 +81,10 @@ __device__ __forceinline__ void grid_reduce(double (&v)[K], int maxmask, double 
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) out[k] = acc[k];
+        if (out_scaled) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) out_scaled[k] = acc[k] * scale;
+        }
         *counter = 0u;
     }
 }

@@ -48,7 +48,8 @@ struct XParams {
     float dep_scale;          // mass quantum / cell volume
     double *partials;         // per-block partial sums
     unsigned int *counter;    // last-block ticket (returns to 0 after use)
-    double *result;           // where the final reduction goes
+    double *result;           // where the final reduction goes (X_MASS: the sum, then the sum times mass_scale)
+    double mass_scale;        // cell volume (X_MASS)
     int *status;              // device status word (bit 0: non-finite mass)
     const float *absorb_x, *absorb_y, *absorb_z;  // per-axis absorbing-layer factors (X_ABSORB)
     const float *phib;        // static external potential, nodes (X_STATIC)

@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(XCfg<N, TC>::NT) xpass_kernel(XParams p)
         }
         if (flags & X_MASS) {
             double v[1] = {(double)msum};
-            grid_reduce<1, NT>(v, 0, p.partials, p.counter, p.result);
+            grid_reduce<1, NT>(v, 0, p.partials, p.counter, p.result, p.result + 1, p.mass_scale);
         }
     }
 

@@ -31,7 +31,7 @@ SUPPORTED_N = (4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768
 EXPORTED = (
     "spe_workspace_bytes", "spe_create_grid", "spe_destroy", "spe_set_ic", "spe_add_particles",
     "spe_clear_particles", "spe_step", "spe_suggest_dt", "spe_density", "spe_potential", "spe_energy",
-    "spe_last_mass", "spe_get_psi", "spe_get_particles", "spe_particle_count", "spe_sync", "spe_settle",
+    "spe_last_mass", "spe_mass_async", "spe_get_psi", "spe_get_particles", "spe_particle_count", "spe_sync", "spe_settle",
     "spe_launch_count", "spe_profile_read", "spe_strerror", "spe_field_energy_noalloc",
     "spe_set_static_potential", "spe_virial", "spe_autotune", "spe_set_schedule", "spe_get_schedule",
     "spe_batch_create", "spe_batch_grid",
@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH):
         "spe_potential": (I, [P, fp, I]),
         "spe_energy": (I, [P, ctypes.POINTER(spe_energy_t)]),
         "spe_last_mass": (I, [P, ctypes.POINTER(D)]),
+        "spe_mass_async": (I, [P, P]),
         "spe_get_psi": (I, [P, P, I]),
         "spe_get_particles": (I, [P, fp, fp, I]),
         "spe_particle_count": (I, [P, ctypes.POINTER(S)]),
@@ -356,6 +357,16 @@ class Grid:
         out = ctypes.c_double()
         _check(self._lib.spe_last_mass(self._h, ctypes.byref(out)), "spe_last_mass")
         return out.value
+
+    def mass_async(self, dst):
+        """Queue a copy of the last step's mass into dst (a float64 tensor element: pinned host or
+        CUDA memory) on the grid's stream; no wait."""
+        import torch
+        if not isinstance(dst, torch.Tensor) or dst.dtype != torch.float64 or dst.numel() < 1:
+            raise ValueError("mass_async needs a float64 tensor")
+        if not dst.is_cuda and not dst.is_pinned():
+            raise ValueError("mass_async needs pinned host or device memory")
+        _check(self._lib.spe_mass_async(self._h, ctypes.c_void_p(dst.data_ptr())), "spe_mass_async")
 
     def particle_count(self) -> int:
         out = ctypes.c_size_t()

@@ -156,3 +156,24 @@ def test_settle_is_idempotent(spe):
     a.sync()
     b.step(3, dt)
     assert np.array_equal(a.get_psi(), b.get_psi())
+
+
+def test_mass_async_matches_last_mass(spe):
+    """spe_mass_async queues the step's mass (cell volume applied on the device) without waiting;
+    pinned-host and device destinations get exactly what spe_last_mass reports."""
+    import torch
+    n = 32
+    psi, pos, vel, mass, dt = halo(n, 500)
+    g = grid(spe, n, psi, pos, vel, mass, flags=spe.SPE_ASYNC)
+    host = torch.zeros(4, dtype=torch.float64).pin_memory()
+    dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for k in range(4):
+        g.step(1, dt)
+        g.mass_async(host[k:k + 1])
+    g.mass_async(dev)
+    g.sync()
+    last = g.last_mass()
+    assert host[3].item() == last and dev.item() == last
+    assert np.all(np.abs(host.numpy() / last - 1.0) < 1e-6)
+    with pytest.raises(ValueError):
+        g.mass_async(torch.zeros(1, dtype=torch.float64))          # pageable host memory
