@@ -5,11 +5,13 @@ Workload (default): 256^3 complex64 grid, central soliton + granular halo, 1e6 P
 kick-drift-kick step of the field and the stars (every kernel of the hot path).
 
 Prints one JSON line (rank 0).  ``value`` is device-resident throughput (inputs already in HBM,
-CUDA events on the grid's stream, K steps in one spe_step call).  ``e2e`` is the same metric through
+CUDA events on the grid's stream, K steps in one spe_step call: every step after the first is a
+CUDA graph replay).  ``e2e`` is the same metric through
 the C ABI with host buffers: pinned-host upload of the initial field and stars, K single-step calls
 each followed by a device->host read of the step's mass, and the final download of psi and the
 stars, all inside the timed region.  ``roofline`` is the dominant kernel's algorithmic bytes over
-its CUDA-event duration, against the measured HBM copy bandwidth.  ``cpu_baseline`` is the FP64
+its CUDA-event duration, taken in a second run of the same K steps with events around every
+(direct) launch, against the measured HBM copy bandwidth.  ``cpu_baseline`` is the FP64
 oracle on the host cores on about ten seconds of steps of the same workload.
 
 Multi-GPU: the grid does not shard here; N ranks run N independent replicas (weak scaling).
@@ -525,35 +527,56 @@ def grid_arm(args, r):
     def barrier():
         replicas.barrier(r)
 
-    # ---------------- device-resident timed region
+    # ---------------- device-resident timed region (the production path: every step after a call's
+    # first one is a CUDA graph replay; no per-kernel events)
     prec_flag = spe.SPE_PREC_SPLIT16 if args.prec == "split16" else 0
-    g = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar,
-                 flags=spe.SPE_ASYNC | spe.SPE_PROFILE | prec_flag, stream=stream)
-    g.set_ic(torch.from_numpy(psi).cuda())
-    if nstar:
-        g.add_particles(torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda(), torch.from_numpy(mass).cuda())
+
+    def make_grid(flags):
+        grid = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, flags=flags | prec_flag, stream=stream)
+        grid.set_ic(torch.from_numpy(psi).cuda())
+        if nstar:
+            grid.add_particles(torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda(),
+                               torch.from_numpy(mass).cuda())
+        return grid
+
+    def timed_steps(grid, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        grid.step(steps, dt)
+        grid.settle()          # the closing half kick of the last step, inside the timed region
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    g = make_grid(spe.SPE_ASYNC)
     tiles = g.autotune() if not args.no_autotune else None
     schedule = g.schedule()
     g.step(args.warmup, dt)
     g.sync()
-    g.profile_read()
     g.launch_count(reset=True)
     clocks = ClockSampler(local)
     barrier()
     clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    g.step(args.steps, dt)
-    g.settle()          # the closing half kick of the last step, inside the timed region
-    ev1.record(stream)
-    ev1.synchronize()
+    ms = timed_steps(g, args.steps)
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
     launches = g.launch_count()
-    prof = g.profile_read()
     ms = replicas.max_over_ranks(r, ms, device="cuda")
     value = replicas.job_rate(r, ncells * args.steps, ms * 1e-3)
+    g.destroy()
+    del g
+    torch.cuda.empty_cache()
+
+    # ---------------- the same steps with CUDA events around every kernel launch (direct launches,
+    # no graphs): per-kernel durations for the roofline and the kernel split
+    gp = make_grid(spe.SPE_ASYNC | spe.SPE_PROFILE)
+    if tiles is not None:
+        gp.set_schedule(*schedule)
+    gp.step(args.warmup, dt)
+    gp.sync()
+    gp.profile_read()
+    ms_prof = timed_steps(gp, args.steps)
+    prof = gp.profile_read()
 
     # roofline of the dominant kernel
     frows = deposit_row_fraction(pos, psi.shape) if nstar else 0.0
@@ -579,7 +602,7 @@ def grid_arm(args, r):
                    "precision": args.prec, "strided_schedule_yz": {"tiles": list(schedule[0]),
                                                                    "alt_radix_plan": list(schedule[1]),
                                                                    "autotuned": tiles is not None},
-                   "l2": f"working set {g.workspace.numel() / 2**20:.0f} MiB > 129 MB L2 (no flush needed)",
+                   "l2": f"working set {gp.workspace.numel() / 2**20:.0f} MiB > 129 MB L2 (no flush needed)",
                    "parallelism": f"{world} independent replica(s)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
@@ -590,12 +613,15 @@ def grid_arm(args, r):
         "step_roofline": {"bytes_per_cell_step": step_bytes,
                           "achieved_GBs": step_bytes * ncells * args.steps / (ms * 1e-3) / 1e9,
                           "frac": step_bytes * ncells * args.steps / (ms * 1e-3) / 1e9 / peak},
+        "kernel_timing": {"what": "per-kernel CUDA events in a second run of the same steps with direct "
+                                  "launches (no graphs); value above is the graph-replayed run",
+                          "ms_per_step": ms_prof / args.steps},
         "kernels": kernel_split,
         "gpu_launches": int(launches),
         "clocks": clk,
     }
-    g.destroy()
-    del g
+    gp.destroy()
+    del gp
     torch.cuda.empty_cache()
 
     # ---------------- end to end through the C ABI with host buffers

@@ -189,6 +189,7 @@ struct spe_grid {
     bool phi_valid;
     // the closing half kick of the last spe_step, not yet applied: the next spe_step with the same
     // dt merges it into its leading kick, anything that reads or changes the state applies it first
+    bool sort_due;          // reorder the stars by cell block at the next step (stars were added)
     bool kick_pending;
     double pending_h;
     double pending_dt;
@@ -489,6 +490,7 @@ int sort_particles(spe_grid *g)
     int rc = launch(g, KIND_SORT, [&] { return launch_particle_sort(sp, g->st, &extra); });
     g->launches += extra > 0 ? extra - 1 : 0;
     if (rc) return rc;
+    g->sort_due = false;
     // copy the reordered arrays back so that the star arrays never move (captured graphs hold
     // their addresses)
     cudaError_t e = cudaSuccess;
@@ -516,7 +518,7 @@ int step_body(spe_grid *g, double dtk, double dt, bool absorb_prev)
     xp.kick_scale = (float)(dtk / g->cfg.hbar_over_m);
     if ((rc = run_x(g, KIND_X_KICK_FFT, xp))) return rc;
     if (parts) {
-        if (!g->capturing && g->steps_done % kSortEvery == 0 && (rc = sort_particles(g))) return rc;
+        if (!g->capturing && (g->sort_due || g->steps_done % kSortEvery == 0) && (rc = sort_particles(g))) return rc;
         PParams pp = base_p(g);
         pp.flags = PK_DRIFT | (skick ? PK_KICK : 0) | (grav ? PK_DEPOSIT : 0);
         pp.kick = (float)dtk;
@@ -615,7 +617,7 @@ int run_full_steps(spe_grid *g, int count, double dt, bool single = false)
     }
     if ((rc = ensure_step_graph(g, dt))) return rc;
     for (int s = 0; s < count; ++s) {
-        if (g->np && g->steps_done % kSortEvery == 0 && (rc = sort_particles(g))) return rc;
+        if (g->np && (g->sort_due || g->steps_done % kSortEvery == 0) && (rc = sort_particles(g))) return rc;
         if (cudaGraphLaunch(g->step_exec, g->st) != cudaSuccess) return SPE_ECUDA;
         g->launches += g->graph_nodes;
         g->steps_done++;
@@ -1026,6 +1028,7 @@ int spe_add_particles(spe_grid *g, size_t n, const float *pos3, const float *vel
     g->mstar += msum;
     update_quantum(g);
     g->phi_valid = false;
+    g->sort_due = true;   // new stars arrive in insertion order: reorder them at the next step
     return SPE_OK;
 }
 
