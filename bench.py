@@ -591,6 +591,13 @@ def grid_arm(args, r):
     # x kick pass, y fwd, z drift, y inv, x density pass, and the three half-spectrum passes
     step_bytes = (bpc["x_kick_fwd"] + 2 * bpc["y_fft_psi"] + bpc["z_fft_drift"] + bpc["x_inv_density_r2c"] +
                   2 * bpc["y_fft_rho"] + bpc["z_fft_poisson"])
+    # DRAM bytes of one step from the committed ncu capture (null unless taken on these sources)
+    per_step = {"x_kick_fwd": 1, "x_inv_density_r2c": 1, "y_fft_psi": 2, "z_fft_drift": 1, "y_fft_rho": 2,
+                "z_fft_poisson": 1}
+    if nstar:
+        per_step["particles_kdk_deposit"] = 1
+    rec = {k: recorded_traffic(k, args.workload) for k in per_step}
+    step_dram = sum(rec[k] * c for k, c in per_step.items()) if all(v is not None for v in rec.values()) else None
     kernel_split = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / max(1e-9, sum(
         x[1] for x in prof.values())), 4)} for k, v in prof.items() if v[0]}
 
@@ -612,7 +619,13 @@ def grid_arm(args, r):
                      "avg_launch_ms": per_launch_s * 1e3},
         "step_roofline": {"bytes_per_cell_step": step_bytes,
                           "achieved_GBs": step_bytes * ncells * args.steps / (ms * 1e-3) / 1e9,
-                          "frac": step_bytes * ncells * args.steps / (ms * 1e-3) / 1e9 / peak},
+                          "frac": step_bytes * ncells * args.steps / (ms * 1e-3) / 1e9 / peak,
+                          # against the 64 B/cell/step floor of two-pass 3D transforms with every
+                          # pointwise operation fused
+                          "frac_vs_64B_floor": 64.0 * ncells * args.steps / (ms * 1e-3) / 1e9 / peak,
+                          "dram_bytes_per_step_measured": step_dram,
+                          "frac_measured_dram": (step_dram * args.steps / (ms * 1e-3) / 1e9 / peak
+                                                 if step_dram else None)},
         "kernel_timing": {"what": "per-kernel CUDA events in a second run of the same steps with direct "
                                   "launches (no graphs); value above is the graph-replayed run",
                           "ms_per_step": ms_prof / args.steps},
