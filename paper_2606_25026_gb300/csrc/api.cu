@@ -117,7 +117,9 @@ int compute_layout(const spe_config *c, Layout *L, int *W, int *P)
     L->dflag = off;    off = align256(off + (c->max_particles ? (size_t)c->ny * c->nz + 16 : 0));
     // two sets of star arrays (x, y, z, vx, vy, vz, m, id) for reordering, sort keys, block counters
     L->part = off;     off = align256(off + 17 * align256(c->max_particles * sizeof(float)));
-    L->bins = off;     off = align256(off + sizeof(int) * (size_t)((c->nx + 3) / 4) * ((c->ny + 3) / 4) * ((c->nz + 3) / 4));
+    // block counters, then the span totals of their scan (one per 2048 counters)
+    const size_t nbins = (size_t)((c->nx + 3) / 4) * ((c->ny + 3) / 4) * ((c->nz + 3) / 4);
+    L->bins = off;     off = align256(off + sizeof(int) * (nbins + (nbins + 2047) / 2048));
     L->tw = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float4));
     L->k2 = off;       off = align256(off + (size_t)(c->nx + c->ny + c->nz) * sizeof(float));
     L->drift = off;    off = align256(off + ((size_t)c->nx * c->ny + c->nz) * sizeof(float4));
@@ -478,6 +480,7 @@ int sort_particles(spe_grid *g)
     sp.dst_id = g->alt_id;
     sp.key = g->skey;
     sp.count = g->bins;
+    sp.totals = g->bins + g->nbins;
     sp.n = (int)g->np;
     sp.nbins = g->nbins;
     sp.nx = g->n[0]; sp.ny = g->n[1]; sp.nz = g->n[2];

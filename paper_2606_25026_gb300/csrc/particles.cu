@@ -372,16 +372,64 @@ __global__ void sort_hist_kernel(SortParams s)
     warp_aggregated_add(s.count, k, active);
 }
 
-// Exclusive scan of count[0..nbins) in place, one CTA of 1024 threads:
-// each thread scans a contiguous chunk, a block scan combines the chunks.
-__global__ void __launch_bounds__(1024) sort_scan_kernel(int *count, int nbins)
+// Exclusive scan of count[0..nbins) in place, in three launches: each CTA of 256 threads
+// totals a span of kScanSpan bins (8 consecutive bins per thread), one CTA scans those totals,
+// and each CTA then scans its span again with its total's offset.  Integer sums, so the result
+// is exact and independent of scheduling.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanSpan = kScanThreads * kScanPer;
+
+// inclusive block scan of one int per thread (kScanThreads threads); returns this thread's
+// inclusive prefix, total in *block_total
+__device__ __forceinline__ int block_scan_incl(int v, int *sh, int *block_total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < kScanThreads / 32 ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        if (lane < kScanThreads / 32) sh[lane] = w;
+    }
+    __syncthreads();
+    const int r = v + (warp ? sh[warp - 1] : 0);
+    *block_total = sh[kScanThreads / 32 - 1];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) sort_span_totals_kernel(const int *count, int nbins, int *totals)
+{
+    __shared__ int sh[kScanThreads / 32];
+    const int b0 = blockIdx.x * kScanSpan + threadIdx.x * kScanPer;
+    int sum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q)
+        if (b0 + q < nbins) sum += count[b0 + q];
+    int total;
+    block_scan_incl(sum, sh, &total);
+    if (threadIdx.x == 0) totals[blockIdx.x] = total;
+}
+
+// exclusive scan of the span totals in place, one CTA of 1024 threads, contiguous chunks
+__global__ void __launch_bounds__(1024) sort_scan_totals_kernel(int *totals, int nspans)
 {
     __shared__ int part[1024];
-    const int chunk = (nbins + 1023) / 1024;
-    const int b0 = threadIdx.x * chunk;
-    const int b1 = min(b0 + chunk, nbins);
+    const int chunk = (nspans + 1023) / 1024;
+    const int s0 = threadIdx.x * chunk;
+    const int s1 = min(s0 + chunk, nspans);
     int sum = 0;
-    for (int b = b0; b < b1; ++b) sum += count[b];
+    for (int k = s0; k < s1; ++k) sum += totals[k];
     part[threadIdx.x] = sum;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
@@ -391,10 +439,30 @@ __global__ void __launch_bounds__(1024) sort_scan_kernel(int *count, int nbins)
         __syncthreads();
     }
     int run = part[threadIdx.x] - sum;
-    for (int b = b0; b < b1; ++b) {
-        const int c = count[b];
-        count[b] = run;
+    for (int k = s0; k < s1; ++k) {
+        const int c = totals[k];
+        totals[k] = run;
         run += c;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) sort_span_scan_kernel(int *count, int nbins, const int *offsets)
+{
+    __shared__ int sh[kScanThreads / 32];
+    const int b0 = blockIdx.x * kScanSpan + threadIdx.x * kScanPer;
+    int c[kScanPer];
+    int sum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) {
+        c[q] = b0 + q < nbins ? count[b0 + q] : 0;
+        sum += c[q];
+    }
+    int total;
+    int run = block_scan_incl(sum, sh, &total) - sum + offsets[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) {
+        if (b0 + q < nbins) count[b0 + q] = run;
+        run += c[q];
     }
 }
 
@@ -415,10 +483,13 @@ cudaError_t launch_particle_sort(const SortParams &s, cudaStream_t st, int *laun
     cudaError_t e = cudaMemsetAsync(s.count, 0, sizeof(int) * (size_t)s.nbins, st);
     if (e != cudaSuccess) return e;
     const int nb = (s.n + 255) / 256;
+    const int nspans = (s.nbins + kScanSpan - 1) / kScanSpan;
     sort_hist_kernel<<<nb, 256, 0, st>>>(s);
-    sort_scan_kernel<<<1, 1024, 0, st>>>(s.count, s.nbins);
+    sort_span_totals_kernel<<<nspans, kScanThreads, 0, st>>>(s.count, s.nbins, s.totals);
+    sort_scan_totals_kernel<<<1, 1024, 0, st>>>(s.totals, nspans);
+    sort_span_scan_kernel<<<nspans, kScanThreads, 0, st>>>(s.count, s.nbins, s.totals);
     sort_scatter_kernel<<<nb, 256, 0, st>>>(s);
-    if (launches) *launches += 3;
+    if (launches) *launches += 5;
     return cudaGetLastError();
 }
 

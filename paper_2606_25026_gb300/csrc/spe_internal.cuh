@@ -125,6 +125,7 @@ struct SortParams {
     unsigned int *src_id, *dst_id;
     int *key;                      // per star
     int *count;                    // nbins counters / offsets
+    int *totals;                   // ceil(nbins / 2048) span totals of the scan
     int n, nbins;
     int nx, ny, nz, nbx, nby;
     float Lx, Ly, Lz, inv_dx, inv_dy, inv_dz;
