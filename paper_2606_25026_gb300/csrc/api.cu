@@ -554,7 +554,7 @@ int step_body(spe_grid *g, double dtk, double dt, bool absorb_prev)
 // everything about the strided passes' launch shapes that a captured graph bakes in
 int schedule_key(const spe_grid *g)
 {
-    return ((g->stile[1] * 64 + g->stile[2]) * 2 + g->splan[1]) * 2 + g->splan[2];
+    return ((g->stile[1] * 64 + g->stile[2]) * 4 + g->splan[1]) * 4 + g->splan[2];
 }
 
 bool graphs_enabled(spe_grid *g) { return !(g->cfg.flags & (SPE_NO_GRAPH | SPE_PROFILE)); }
@@ -1379,11 +1379,11 @@ int autotune_grid(spe_grid *g, float2 *scratch)
             }
         }
         // candidates: tile widths 16, 8, 32 (32 only where it fits in shared memory) x the default
-        // and the alternative radix schedule (lengths that have one)
+        // and the alternative radix schedules (lengths that have them)
         float best_ms = 0.f;
         int best_tile = 16, best_plan = 0, rc;
         bool first = true;
-        for (int plan = 0; plan <= (has_alt_plan_n(g->n[axis]) ? 1 : 0); ++plan) {
+        for (int plan = 0; plan < plan_count_n(g->n[axis]); ++plan) {
             for (int tile : {16, 8, 32}) {
                 if (!spass_tile_ok(g->n[axis], tile)) continue;
                 float ms = 0.f;
@@ -1431,7 +1431,7 @@ extern "C" int spe_set_schedule(spe_grid *g, const int *tiles, const int *plans)
     for (int a = 0; a < 2; ++a) {
         const int n = g->n[a + 1];
         if (tiles[a] != 0 && !spass_tile_ok(n, tiles[a])) return SPE_EINVAL;
-        if (plans[a] != 0 && (plans[a] != 1 || !has_alt_plan_n(n))) return SPE_EINVAL;
+        if (plans[a] < 0 || plans[a] >= plan_count_n(n)) return SPE_EINVAL;
     }
     for (int a = 0; a < 2; ++a) {
         g->stile[a + 1] = tiles[a];

@@ -203,6 +203,78 @@ template <int DIR> struct Dft<16, DIR> {
     }
 };
 
+// cos(k pi / 16), k = 0..16, for the radix-32 butterfly (textbook values to 35 digits)
+constexpr double kCos16[17] = {
+    1.0,
+    0.98078528040323044912618223613424,
+    0.92387953251128675612818318939679,
+    0.83146961230254523707878837761791,
+    0.70710678118654752440084436210485,
+    0.55557023301960222474283081394853,
+    0.38268343236508977172845998403040,
+    0.19509032201612826784828486847702,
+    0.0,
+    -0.19509032201612826784828486847702,
+    -0.38268343236508977172845998403040,
+    -0.55557023301960222474283081394853,
+    -0.70710678118654752440084436210485,
+    -0.83146961230254523707878837761791,
+    -0.92387953251128675612818318939679,
+    -0.98078528040323044912618223613424,
+    -1.0};
+// cos and sin of e pi / 16 for any integer e
+__host__ __device__ constexpr double cos16(int e) { return kCos16[(e & 31) <= 16 ? (e & 31) : 32 - (e & 31)]; }
+__host__ __device__ constexpr double sin16(int e) { return cos16(e - 8); }
+
+template <int DIR> struct Dft<32, DIR> {
+    // 32 = 4 x 8: with n = 8a + b and k = c + 4d,
+    // X[c + 4d] = sum_b W8^{bd} W32^{bc} sum_a x[8a + b] W4^{ac}.
+    template <int E>
+    __device__ __forceinline__ static void rot(float2 &v)
+    {
+        // v *= W32^E = exp(DIR i pi E / 16), the constant split into (hi, lo) float pairs
+        if constexpr (E % 32 == 0) {
+        } else if constexpr (E % 32 == 8) {
+            v = rot90<DIR>(v);
+        } else {
+            constexpr double c = cos16(E), sn = DIR * sin16(E);
+            constexpr float ch = (float)c, sh = (float)sn;
+            constexpr float cl = (float)(c - (double)ch), sl = (float)(sn - (double)sh);
+            v = cmul_comp(v, make_float2(ch, sh), make_float2(cl, sl));
+        }
+    }
+    template <int B, int C>
+    __device__ __forceinline__ static void rot_bc(float2 (&u)[8][4])
+    {
+        rot<B * C>(u[B][C]);
+    }
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        float2 u[8][4];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            float2 t[4] = {v[b], v[8 + b], v[16 + b], v[24 + b]};
+            Dft<4, DIR>::run(t);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) u[b][c] = t[c];
+        }
+        rot_bc<1, 1>(u); rot_bc<1, 2>(u); rot_bc<1, 3>(u);
+        rot_bc<2, 1>(u); rot_bc<2, 2>(u); rot_bc<2, 3>(u);
+        rot_bc<3, 1>(u); rot_bc<3, 2>(u); rot_bc<3, 3>(u);
+        rot_bc<4, 1>(u); rot_bc<4, 2>(u); rot_bc<4, 3>(u);
+        rot_bc<5, 1>(u); rot_bc<5, 2>(u); rot_bc<5, 3>(u);
+        rot_bc<6, 1>(u); rot_bc<6, 2>(u); rot_bc<6, 3>(u);
+        rot_bc<7, 1>(u); rot_bc<7, 2>(u); rot_bc<7, 3>(u);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float2 t[8] = {u[0][c], u[1][c], u[2][c], u[3][c], u[4][c], u[5][c], u[6][c], u[7][c]};
+            Dft<8, DIR>::run(t);
+#pragma unroll
+            for (int d = 0; d < 8; ++d) v[c + 4 * d] = t[d];
+        }
+    }
+};
+
 // ---- radix plans per transform length ----
 
 template <int... R> struct RList {};
@@ -240,6 +312,9 @@ template <> struct PlanSel<384, 1> { using type = RList<3, 8, 16>; };
 template <> struct PlanSel<512, 1> { using type = RList<16, 16, 2>; };
 template <> struct PlanSel<768, 1> { using type = RList<3, 16, 16>; };
 template <> struct PlanSel<1024, 1> { using type = RList<8, 8, 16>; };
+// A third schedule (PL = 2) where a radix-32 last stage saves a pass through shared memory.
+template <> struct PlanSel<512, 2> { using type = RList<16, 32>; };
+template <int N> constexpr bool has_plan2() { return N == 512; }
 template <int N> constexpr bool has_alt_plan()
 {
     return N == 32 || N == 48 || N == 64 || N == 96 || N == 128 || N == 192 || N == 256 || N == 384 || N == 512 ||

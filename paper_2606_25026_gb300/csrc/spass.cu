@@ -27,6 +27,17 @@ bool has_alt_plan_n(int n)
     }
 }
 
+int plan_count_n(int n)
+{
+    switch (n) {
+#define X(n) \
+    case n: return has_plan2<n>() ? 3 : (has_alt_plan<n>() ? 2 : 1);
+        SPE_FOR_EACH_N(X)
+#undef X
+    default: return 1;
+    }
+}
+
 bool spass_tile_ok(int n, int tile)
 {
     return tile == 8 || tile == 16 || (tile == 32 && (size_t)n * 32 * 8 <= 227 * 1024);

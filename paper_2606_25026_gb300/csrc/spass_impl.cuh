@@ -172,8 +172,11 @@ template <int n, int W>
 cudaError_t spass_launch_w(const SParams &p, cudaStream_t st, int *blocks_out)
 {
     if constexpr (tile_fits<n>(W)) {
+        if constexpr (has_plan2<n>()) {
+            if (p.plan == 2) return launch_s_nt<n, W, false, 2>(p, st, blocks_out);
+        }
         if constexpr (has_alt_plan<n>()) {
-            if (p.plan) return launch_s_nt<n, W, false, 1>(p, st, blocks_out);
+            if (p.plan == 1) return launch_s_nt<n, W, false, 1>(p, st, blocks_out);
         }
         return launch_s_nt<n, W>(p, st, blocks_out);
     } else {
@@ -192,6 +195,11 @@ cudaError_t spass_attr_w()
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(spass_kernel<n, W, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SCfg<n, W, false, 1>::smem);
+        }
+        if constexpr (has_plan2<n>()) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(spass_kernel<n, W, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SCfg<n, W, false, 2>::smem);
         }
     }
     return e;

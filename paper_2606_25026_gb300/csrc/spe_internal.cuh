@@ -13,6 +13,7 @@ bool supported_n(int n);
 bool spass_tile_ok(int n, int tile);      // strided-pass tile width 8, 16 or 32 usable at length n
 int spass_default_tile(int n);            // the width used when none is chosen
 bool has_alt_plan_n(int n);               // length n has an alternative radix schedule
+int plan_count_n(int n);                  // radix schedules available at length n (1, 2 or 3)
 
 // ---------------------------------------------------------------- x passes
 // Lines along x are contiguous rows of nx complex values; rows = ny * nz.
@@ -88,7 +89,7 @@ struct SParams {
     unsigned int *counter;
     double *result;
     int tile;             // columns per CTA: 8, 16 or 32 (0 = the per-length default)
-    int plan;             // radix schedule: 0 default, 1 the alternative (lengths that have one)
+    int plan;             // radix schedule: 0 default, 1 and 2 the alternatives (lengths that have them)
     int tc;               // radix-16 stages on the tensor cores (split FP16), N = 256 and 512
     const void *tcw;
     int *status;          // device status word (tensor-stage timeouts)

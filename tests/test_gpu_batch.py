@@ -110,12 +110,13 @@ def test_autotune_stays_within_parity(spe, members):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("n", [64, 96, 128, 256])
+@pytest.mark.parametrize("n", [64, 96, 128, 256, 512])
 def test_every_schedule_matches_oracle(spe, n):
-    """Each tile width and radix schedule of the strided passes against the FP64 oracle."""
+    """Each tile width and radix schedule of the strided passes (y and z both of length n) against
+    the FP64 oracle."""
     import oracle
     oracle.build()
-    psi = inputs.soliton_halo((n, n, 16) if n == 256 else n, seed=n).astype(np.complex64)
+    psi = inputs.soliton_halo((16, n, n) if n >= 256 else n, seed=n).astype(np.complex64)
     shape = psi.shape
     nz, ny, nx = shape
     dt = inputs.kinetic_dt((nx, ny, nz))
@@ -123,7 +124,8 @@ def test_every_schedule_matches_oracle(spe, n):
     o.set_ic(psi.astype(np.complex128))
     o.step(4, dt)
     ref = o.get_psi()
-    for plan in (0, 1):
+    tried = 0
+    for plan in (0, 1, 2):
         for tile in (8, 16, 32):
             g = spe.Grid(nx, ny, nz, G=1.0)
             try:
@@ -134,3 +136,6 @@ def test_every_schedule_matches_oracle(spe, n):
             g.step(4, dt)
             err = np.linalg.norm(g.get_psi() - ref) / np.linalg.norm(ref)
             assert err <= 1e-5, (n, tile, plan, err)
+            tried += 1
+    # every length here has at least the default and one alternative schedule; 512 has three
+    assert tried >= (6 if n == 512 else 4), tried
