@@ -67,7 +67,9 @@ struct PoissonOp {
     __device__ __forceinline__ float2 operator()(float2 v, int n, int t) const
     {
         const float k2 = colk2[t] + __ldg(&linek2[n]);
-        return cscale(v, (k2 > 0.f) ? scale / k2 : 0.f);
+        // k^2 lies between (2 pi / L)^2 and 3 (pi N / L)^2, far inside the range where the fast
+        // division is within 2 ulp: a 2e-7 relative error on Phi_hat, well below its FP32 transforms'
+        return cscale(v, (k2 > 0.f) ? __fdividef(scale, k2) : 0.f);
     }
 };
 
