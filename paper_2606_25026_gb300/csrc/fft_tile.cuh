@@ -451,4 +451,102 @@ __device__ __forceinline__ void tile_fft_fwd_op_inv(float2 *s, const float4 *tw,
     fft_stages<N, T, TP, NT, +1, R>(s, tw, typename Reverse<Init>::type{});
 }
 
+// ---- one transform whose first stage reads global memory and whose last stage writes it
+//
+// The first Stockham stage (Ns = 1, no twiddles) of butterfly j reads points j + r N/R_1; with
+// lanes over t and then j, each of those loads covers whole rows of the tile's columns, so the
+// thread can load them from global memory straight into registers; the last stage writes points
+// j + q N/R_m (Ns = N/R_m) straight back.  Against staging the tile in shared memory first and
+// copying it out last, this saves one shared-memory write and read per element on each side.
+// ld(n, t) returns point n of line t; st(n, t, v) stores it.
+
+template <class L> struct Length;
+template <int... Rs> struct Length<RList<Rs...>> { static constexpr int value = sizeof...(Rs); };
+template <class L> struct SplitFirst;
+template <int R, int... Rs> struct SplitFirst<RList<R, Rs...>> {
+    static constexpr int first = R;
+    using rest = RList<Rs...>;
+};
+
+template <int N, int T, int TP, int NT, int DIR, int R, class Ld>
+__device__ __forceinline__ void fft_stage_from(float2 *s, const Ld &ld)
+{
+    constexpr int B = N / R;
+    constexpr int TOTAL = B * T;
+    constexpr int PER = (TOTAL + NT - 1) / NT;
+    float2 v[PER][R];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (TOTAL % NT == 0 || idx < TOTAL) {
+            const int t = idx % T, j = idx / T;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[p][r] = ld(j + r * B, t);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (TOTAL % NT == 0 || idx < TOTAL) {
+            const int t = idx % T, j = idx / T;
+            Dft<R, DIR>::run(v[p]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[(j * R + r) * TP + t] = v[p][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int N, int T, int TP, int NT, int DIR, int R, class St>
+__device__ __forceinline__ void fft_stage_to(const float2 *s, const float4 *__restrict__ tw, const St &st)
+{
+    constexpr int B = N / R;   // = Ns of the last stage
+    constexpr int TOTAL = B * T;
+    constexpr int PER = (TOTAL + NT - 1) / NT;
+    float2 v[PER][R];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (TOTAL % NT == 0 || idx < TOTAL) {
+            const int t = idx % T, j = idx / T;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[p][r] = s[(j + r * B) * TP + t];
+        }
+    }
+    // as in fft_stage, a barrier between the tile reads and the twiddle loads (without it the
+    // compiler hoists the twiddle loads above the reads and runs out of registers)
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (TOTAL % NT == 0 || idx < TOTAL) {
+            const int t = idx % T, j = idx / T;
+            if (B > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float4 w = __ldg(&tw[j * r]);
+                    const float2 hi = make_float2(w.x, DIR > 0 ? -w.y : w.y);
+                    const float2 lo = make_float2(w.z, DIR > 0 ? -w.w : w.w);
+                    v[p][r] = cmul_comp(v[p][r], hi, lo);
+                }
+            }
+            Dft<R, DIR>::run(v[p]);
+#pragma unroll
+            for (int q = 0; q < R; ++q) st(j + q * B, t, v[p][q]);
+        }
+    }
+}
+
+// one transform of all T lines from ld to st, for plans of two stages or more
+template <int N, int T, int TP, int NT, int DIR, int PL, class Ld, class St>
+__device__ __forceinline__ void tile_fft_direct(float2 *s, const float4 *tw, const Ld &ld, const St &st)
+{
+    using Full = typename PlanSel<N, PL>::type;
+    constexpr int R1 = SplitFirst<Full>::first;
+    using Init = typename SplitLast<Full>::init;       // R_1 .. R_{m-1}
+    fft_stage_from<N, T, TP, NT, DIR, R1>(s, ld);
+    fft_stages<N, T, TP, NT, DIR, R1>(s, tw, typename SplitFirst<Init>::rest{});
+    fft_stage_to<N, T, TP, NT, DIR, SplitLast<Full>::last>(s, tw, st);
+}
+
 }  // namespace spe

@@ -152,6 +152,41 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams 
     if constexpr (TC) tc_teardown(*tcs);
 }
 
+// One forward or inverse transform (S_FWD or S_INV alone) with FP32 stages, its first stage
+// loading straight from global memory and its last storing straight back (tile_fft_direct): a
+// kernel of its own, so that its register allocation is not the fused passes'.  Lengths whose
+// plan has a single stage use spass_kernel.
+template <int N, int TW, int PL> struct LineCfg {
+    static constexpr int NT = SCfg<N, TW, false, PL>::NT;
+    static constexpr int RMAX = MaxRadix<typename PlanSel<N, PL>::type>::value;
+    // used where it fits 64 registers (four CTAs of 256 threads per SM): the power-of-two lengths
+    // from 64 to 256, whose stages are radix 16 and smaller.  Elsewhere (radix-3 stages, 512 and
+    // up) it needs 88-148 registers and ran slower than the staged kernel (512-point y passes
+    // 415 -> 600 us), so those keep spass_kernel.
+    static constexpr int MINB = 1024 / NT;
+    static constexpr bool usable = RMAX <= 16 && N >= 64 && N <= 256 && (N & (N - 1)) == 0 &&
+                                   Length<typename PlanSel<N, PL>::type>::value >= 2;
+};
+
+template <int N, int TW, int PL>
+__global__ void __launch_bounds__(LineCfg<N, TW, PL>::NT, LineCfg<N, TW, PL>::MINB) spass_line_kernel(SParams p)
+{
+    constexpr int T = TW, NT = LineCfg<N, TW, PL>::NT;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+    float2 *base = p.data + (size_t)blockIdx.y * p.bstride + blockIdx.x * T;
+    const int live = p.W - (int)blockIdx.x * T;
+    const long long S = p.S;
+    const auto ld = [base, live, S](int n, int t) {
+        return t < live ? __ldcg(base + n * S + t) : make_float2(0.f, 0.f);
+    };
+    const auto st = [base, live, S](int n, int t, float2 v) {
+        if (t < live) base[n * S + t] = v;
+    };
+    if (p.flags & S_FWD) tile_fft_direct<N, T, T, NT, -1, PL>(tile, p.tw, ld, st);
+    else tile_fft_direct<N, T, T, NT, +1, PL>(tile, p.tw, ld, st);
+}
+
 // widths that fit in shared memory for length N
 template <int N> constexpr bool tile_fits(int tw) { return (size_t)N * tw * sizeof(float2) <= 227 * 1024; }
 
@@ -160,8 +195,27 @@ static cudaError_t launch_s_nt(const SParams &p, cudaStream_t st, int *blocks_ou
 {
     dim3 grid((p.W + TW - 1) / TW, p.batches);
     if (blocks_out) *blocks_out = grid.x * grid.y;
+    if constexpr (!TC && LineCfg<N, TW, PL>::usable) {
+        if (p.flags == S_FWD || p.flags == S_INV) {
+            spass_line_kernel<N, TW, PL><<<grid, LineCfg<N, TW, PL>::NT, SCfg<N, TW, false, PL>::smem, st>>>(p);
+            return cudaGetLastError();
+        }
+    }
     spass_kernel<N, TW, TC, PL><<<grid, SCfg<N, TW, TC, PL>::NT, SCfg<N, TW, TC, PL>::smem, st>>>(p);
     return cudaGetLastError();
+}
+
+template <int N, int TW, int PL>
+static cudaError_t attr_s(int smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(spass_kernel<N, TW, false, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem);
+    if constexpr (LineCfg<N, TW, PL>::usable) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(spass_line_kernel<N, TW, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem);
+    }
+    return e;
 }
 
 }  // namespace spe
@@ -191,17 +245,12 @@ cudaError_t spass_attr_w()
 {
     cudaError_t e = cudaSuccess;
     if constexpr (tile_fits<n>(W)) {
-        e = cudaFuncSetAttribute(spass_kernel<n, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)SCfg<n, W>::smem);
+        e = attr_s<n, W, 0>((int)SCfg<n, W>::smem);
         if constexpr (has_alt_plan<n>()) {
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(spass_kernel<n, W, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SCfg<n, W, false, 1>::smem);
+            if (e == cudaSuccess) e = attr_s<n, W, 1>((int)SCfg<n, W, false, 1>::smem);
         }
         if constexpr (has_plan2<n>()) {
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(spass_kernel<n, W, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SCfg<n, W, false, 2>::smem);
+            if (e == cudaSuccess) e = attr_s<n, W, 2>((int)SCfg<n, W, false, 2>::smem);
         }
     }
     return e;
