@@ -90,12 +90,19 @@ def parse():
 
 
 def source_hash() -> str:
-    """Hash of the solver's CUDA sources (the surrogate's fno* and surrogate.cu files excluded)."""
+    """Hash of the solver's CUDA sources (the surrogate's fno* and surrogate.cu files excluded),
+    comments and whitespace left out, so that only a change of the code itself invalidates the
+    recorded DRAM traffic."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_25026_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh")) and not f.startswith(("fno", "surrogate")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+            text = open(os.path.join(csrc, f), encoding="utf-8").read()
+            text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", " ", text)
+            h.update(f.encode())
+            h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
