@@ -3,11 +3,15 @@
 // adjacent in memory.
 //
 // One CTA owns a tile of T adjacent columns x N points (T = 32 for N < 256,
-// 16 from 256 up), so every row of the tile is one coalesced 128/256-byte
-// segment.  Loads are asynchronous 16-byte copies straight into shared memory
-// (every load of the tile in flight at once); stores are float4.  The tile lives in
-// shared memory element-major (tile[n * T + t]) with lanes over t: the FFT
-// stages are then bank-conflict free without padding.
+// 16 from 256 up; 8, 16 or 32 as the autotuner picks), so every row of the
+// tile is one coalesced segment.  In spass_kernel the loads are asynchronous
+// 16-byte copies straight into shared memory (every load of the tile in flight
+// at once) and the stores are float4; spass_line_kernel (one transform alone,
+// lengths 64-256) loads its first stage straight into registers and stores its
+// last stage straight from them.  The tile lives in shared memory
+// element-major (tile[n * T + t]) with lanes over t: the FFT stages are then
+// bank-conflict free without padding.  Radix schedules: the default plan per
+// length, and up to two alternatives (PL = 1, 2) the autotuner may pick.
 //
 // Flags select forward transform, a pointwise multiply in k space, and the
 // inverse transform, all on the same tile; with a multiply, the last forward
