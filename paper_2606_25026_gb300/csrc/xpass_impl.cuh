@@ -259,22 +259,45 @@ __global__ void __launch_bounds__(XCfg<N, TC>::NT) xpass_kernel(XParams p)
         }
         if (ifft) tfft<N, T, TP, NT, +1, TC>(tile, p.tw, tcs, p.status);
         float msum = 0.f;
-        for (int idx = tid; idx < T * N; idx += NT) {
-            const int n = idx % N, t = idx / N;
-            const int row = row0 + t;
-            const float2 v = tile[n * TP + t];
-            if (ifft && row < p.rows) p.psi[(size_t)row * N + n] = v;
-            float r = v.x * v.x + v.y * v.y;
-            msum += r;
-            if (flags & X_DEP) r += aux[t * N + n];
-            aux[t * N + n] = r;
-        }
-        __syncthreads();
-        if (flags & X_R2C) {
-            for (int idx = tid; idx < (T / 2) * N; idx += NT) {
-                const int n = idx % N, m = idx / N;
-                tile[n * TP + m] = make_float2(aux[(2 * m) * N + n], aux[(2 * m + 1) * N + n]);
+        if constexpr (NT == N && N <= 256) {
+            // one thread per point n: it alone reads and writes column n of the tile (and its
+            // deposit values in aux), so rho goes from registers straight into the packed lines
+            // Z_m[n] = rho[2m][n] + i rho[2m+1][n], with no pass through aux and no barrier between
+            // (at 512 points the sixteen extra registers cost more than the pass saves)
+            const int n = tid;
+            float r[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const float2 v = tile[n * TP + t];
+                if (ifft && row0 + t < p.rows) p.psi[(size_t)(row0 + t) * N + n] = v;
+                r[t] = v.x * v.x + v.y * v.y;
+                msum += r[t];
+                if (flags & X_DEP) r[t] += aux[t * N + n];
             }
+            if (flags & X_R2C) {
+#pragma unroll
+                for (int m = 0; m < T / 2; ++m) tile[n * TP + m] = make_float2(r[2 * m], r[2 * m + 1]);
+            }
+        } else {
+            for (int idx = tid; idx < T * N; idx += NT) {
+                const int n = idx % N, t = idx / N;
+                const int row = row0 + t;
+                const float2 v = tile[n * TP + t];
+                if (ifft && row < p.rows) p.psi[(size_t)row * N + n] = v;
+                float r = v.x * v.x + v.y * v.y;
+                msum += r;
+                if (flags & X_DEP) r += aux[t * N + n];
+                aux[t * N + n] = r;
+            }
+            __syncthreads();
+            if (flags & X_R2C) {
+                for (int idx = tid; idx < (T / 2) * N; idx += NT) {
+                    const int n = idx % N, m = idx / N;
+                    tile[n * TP + m] = make_float2(aux[(2 * m) * N + n], aux[(2 * m + 1) * N + n]);
+                }
+            }
+        }
+        if (flags & X_R2C) {
             __syncthreads();
             tfft<N, T / 2, TP, NT, -1, TC>(tile, p.tw, tcs, p.status);
             // separate the two real rows: A_k = (Z_k + conj Z_{N-k}) / 2, B_k = (Z_k - conj Z_{N-k}) / (2i)
