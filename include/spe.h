@@ -234,10 +234,10 @@ SPE_API int spe_profile_read(spe_grid *g, const char **names, unsigned long long
 SPE_API int spe_field_energy_noalloc(const void *psi_c64, size_t n, double cell_volume, double kappa,
                                      double *out2, int where, void *cuda_stream);
 
-/* ---- tuning and batches (spec additions; the paper steps one grid) ----
+/* ---- tuning and batches (beyond the paper, which steps one grid) ----------
  * spe_autotune: time the strided (y, z) passes on a scratch field of the
  * grid's size (allocated and freed inside the call) over tile widths 8, 16
- * and 32 columns (32 where it fits in shared memory) and both radix schedules
+ * and 32 columns (32 where it fits in shared memory) and every radix schedule
  * of the length (see spe_set_schedule), and keep the fastest per axis;
  * choices are cached per (axis, length, nx) for the process.  tiles_out
  * (optional): the y and z widths chosen (spe_get_schedule also gives the
@@ -246,8 +246,9 @@ SPE_API int spe_autotune(spe_grid *g, int *tiles_out);
 
 /* Pin the strided passes' schedule: tiles[0..1] = tile width of the y and z
  * passes (8, 16 or 32 columns; 0 = the default for the length) and plans[0..1]
- * = radix schedule (0 = default, 1 = the alternative, for lengths that have
- * one: 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024).  Tile widths only
+ * = radix schedule (0 = default; 1 = the first alternative, for 32, 48, 64,
+ * 96, 128, 192, 256, 384, 512, 768 and 1024; 2 = the two-stage [16, 32]
+ * schedule, for 512).  Tile widths only
  * regroup independent lines (results bitwise unchanged); a radix schedule
  * changes the FP32 rounding of the transform.  SPE_EINVAL for an unusable
  * choice.  spe_get_schedule reports the schedule in use. */
