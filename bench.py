@@ -213,6 +213,9 @@ def cpu_baseline(psi, pos, vel, mass, dt, budget_s=10.0, max_steps=20):
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
+    if world > 1:
+        # the launcher sets one OpenMP thread per rank; rank 0 runs alone here and takes the cores
+        os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
     psi, pos, vel, mass, dt = make_inputs(args.workload)
     import oracle
     oracle.build()
