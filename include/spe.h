@@ -66,7 +66,8 @@ extern "C" {
 #define SPE_GRAVITY_OFF   (1 << 0)  /* G treated as 0: no Poisson solve */
 #define SPE_NO_CFL_CHECK  (1 << 1)  /* spe_step does not reject dt above the kinetic CFL bound */
 #define SPE_ASYNC         (1 << 2)  /* spe_step returns after enqueueing; no status check */
-#define SPE_PROFILE       (1 << 3)  /* time every kernel launch with CUDA events (spe_profile_read) */
+#define SPE_PROFILE       (1 << 3)  /* time every kernel launch with CUDA events (spe_profile_read);
+                                       launches go directly, not through CUDA graphs */
 #define SPE_NO_GRAPH      (1 << 4)  /* launch the per-step kernels directly, never through a CUDA graph */
 #define SPE_STATIC_POTENTIAL (1 << 5) /* reserve a static external potential (spe_set_static_potential) */
 #define SPE_PREC_SPLIT16  (1 << 6)  /* axes of 256 or 512 points: radix-16 DFT stages on the tensor cores,
