@@ -348,6 +348,101 @@ def test_free_streaming_particles():
     assert (p >= -0.5).all() and (p < 0.5).all()
 
 
+def test_star_leapfrog_harmonic_orbit_is_the_discrete_kdk_map():
+    """Sec. 3.2.2 (dynamic mode) with the lock-step KDK leapfrog of Sec. 3.1 Eq. (SPE_solver_KDK).
+
+    G = 0, psi = 0 and a static potential Phi_b = w^2 |r|^2 / 2: the central difference of a
+    quadratic is exact and the CIC interpolation of a linear node field is exact, so away from the
+    periodic seam every star feels g = -w^2 r exactly.  A kick of dt/2, a drift of dt and a kick of
+    dt/2 is then the linear map (x, v) -> M (x, v) per axis with
+        M = [[1 - w^2 dt^2 / 2, dt], [-w^2 dt (1 - w^2 dt^2 / 4), 1 - w^2 dt^2 / 2]],
+    so after n steps the state is M^n (x0, v0).  A full-size kick, a drift-kick-drift order or a
+    flipped force sign each give another orbit."""
+    n, L = 32, 1.0
+    x, y, z = mesh(n, n, n, (L, L, L))
+    w = 2 * np.pi
+    dt = 0.01
+    o = Oracle(n, n, n, L, G=0.0)
+    o.set_ic(np.zeros((n, n, n), complex))
+    o.set_static_phi(0.5 * w ** 2 * (x ** 2 + y ** 2 + z ** 2))
+    pos = np.array([[0.2, -0.1, 0.05], [-0.13, 0.17, 0.0]])
+    vel = np.array([[0.0, 0.3, -0.2], [0.25, 0.0, 0.1]])
+    o.set_particles(pos, vel, np.full(2, 1e-3))
+    steps = 50
+    o.step(steps, dt)
+    p, v = o.get_particles()
+    a = 1 - 0.5 * (w * dt) ** 2
+    M = np.array([[a, dt], [-w ** 2 * dt * (1 - 0.25 * (w * dt) ** 2), a]])
+    Mn = np.linalg.matrix_power(M, steps)
+    ref_p = Mn[0, 0] * pos + Mn[0, 1] * vel
+    ref_v = Mn[1, 0] * pos + Mn[1, 1] * vel
+    # the orbit stays inside |r| < 0.3, so every stencil node is off the periodic seam
+    assert np.abs(ref_p).max() < 0.3
+    assert np.abs(p - ref_p).max() < 1e-12
+    assert np.abs(v - ref_v).max() < 1e-11
+
+
+def test_star_leapfrog_step_in_sinusoidal_potential():
+    """One KDK step (Sec. 3.2.2, dynamic mode) in Phi_b = cos(k x) with G = 0, psi = 0, for a star
+    between nodes: the node force is sin(k x_i) sin(k dx) / dx (central difference) and the CIC
+    interpolation is linear in the fraction f, so the step written out by hand is
+        v_h = v0 + g(x0) dt / 2,  x1 = x0 + v_h dt,  v1 = v_h + g(x1) dt / 2.
+    The force changes across the drift, which fixes that the closing kick reads the new position."""
+    n, L = 16, 1.0
+    x, y, z = mesh(n, n, n, (L, L, L))
+    k = 2 * np.pi / L
+    dx = L / n
+    xi = coords(n, L)
+    o = Oracle(n, n, n, L, G=0.0)
+    o.set_ic(np.zeros((n, n, n), complex))
+    o.set_static_phi(np.cos(k * x))
+
+    def g(px):
+        u = (px + 0.5 * L) / dx
+        i0 = int(math.floor(u))
+        f = u - i0
+        node = lambda i: math.sin(k * xi[i % n]) * math.sin(k * dx) / dx
+        return (1 - f) * node(i0) + f * node(i0 + 1)
+
+    x0, v0, dt = xi[3] + 0.37 * dx, 3.0, 0.06
+    o.set_particles(np.array([[x0, 0.1, -0.2]]), np.array([[v0, 0.0, 0.0]]), np.ones(1))
+    o.step(1, dt)
+    p, v = o.get_particles()
+    vh = v0 + 0.5 * dt * g(x0)
+    x1 = x0 + vh * dt
+    v1 = vh + 0.5 * dt * g(x1)
+    assert abs(x1 - x0) > 2 * dx          # the star crosses cells, so g(x1) differs from g(x0)
+    assert p[0, 0] == pytest.approx(x1, abs=1e-14)
+    assert v[0, 0] == pytest.approx(v1, abs=1e-13)
+    assert abs(p[0, 1] - 0.1) < 1e-15 and abs(p[0, 2] + 0.2) < 1e-15 and np.abs(v[0, 1:]).max() < 1e-13
+
+
+def test_energy_drift_with_stars_is_reported_and_small():
+    """With gravitating stars, psi != 0 and G > 0 the PM force (CIC deposit, central difference,
+    CIC interpolation) conserves the total energy (star kinetic energy included) only
+    approximately, so no order is asserted: the drift is printed for dt and dt/2 and bounded."""
+    n = 16
+    psi = _packets(n, seed=21)
+    rng = np.random.default_rng(22)
+    pos = (rng.random((30, 3)) - 0.5) * 0.6
+    vel = rng.standard_normal((30, 3)) * 0.2
+    mass = np.full(30, 0.01)
+    T = 0.02
+    drifts = []
+    for dt in (1e-3, 5e-4):
+        o = Oracle(n, n, n, 1.0, G=2.0)
+        o.set_ic(psi)
+        o.set_particles(pos, vel, mass)
+        e0 = o.energy()
+        o.step(int(round(T / dt)), dt)
+        e1 = o.energy()
+        assert e1["star_kinetic"] > 0.0
+        drifts.append(abs(e1["total"] - e0["total"]) / abs(e0["total"]))
+    print(f"relative energy drift with stars over t = {T}: dt = 1e-3 -> {drifts[0]:.3e}, "
+          f"dt = 5e-4 -> {drifts[1]:.3e}")
+    assert max(drifts) < 1e-3, drifts
+
+
 # --------------------------------------------------------------------------- CFL
 
 
