@@ -227,9 +227,11 @@ SPE_API int spe_profile_read(spe_grid *g, const char **names, unsigned long long
  * Every call shares that array, so calls that overlap on the GPU race and
  * must be serialised by the caller.  The first call on each device finds the
  * array's device address (with that device current) and remembers it; make
- * that first call before any stream capture.
+ * that first call before any stream capture.  The remembered address does not
+ * survive cudaDeviceReset: do not call this again on a device that was reset.
  * Returns SPE_EINVAL for n == 0, n > SPE_NOALLOC_MAX_CELLS, a non-positive
- * cell volume or a NULL pointer. */
+ * cell volume, a NULL pointer, psi_c64 not 8-byte aligned, or (SPE_DEVICE)
+ * out2 not 8-byte aligned. */
 #define SPE_NOALLOC_MAX_CELLS ((size_t)1 << 30)
 #define SPE_NOALLOC_SCRATCH_DOUBLES 2064
 SPE_API int spe_field_energy_noalloc(const void *psi_c64, size_t n, double cell_volume, double kappa,

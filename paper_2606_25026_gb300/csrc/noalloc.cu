@@ -20,8 +20,11 @@
 // Set-up: the first call on each device looks up the array's device address
 // with cudaGetSymbolAddress while that device is current (the name is only a
 // host-side stand-in, not a device address) and caches it per device.  Make
-// that first call before any stream capture.
+// that first call before any stream capture.  cudaDeviceReset unloads the
+// module, so the cached address is stale afterwards: a process that resets a
+// device must not call this entry point on that device again.
 #include <mutex>
+#include <stdint.h>
 
 #include "reduce.cuh"
 #include "spe.h"
@@ -88,6 +91,8 @@ extern "C" int spe_field_energy_noalloc(const void *psi_c64, size_t n, double ce
     if (!psi_c64 || !out2 || n == 0 || (where != SPE_HOST && where != SPE_DEVICE)) return SPE_EINVAL;
     if (n > SPE_NOALLOC_MAX_CELLS) return SPE_EINVAL;
     if (!(cell_volume > 0) || !isfinite(cell_volume) || !isfinite(kappa)) return SPE_EINVAL;
+    // the kernel reads psi as float2 and writes out2 as doubles: both need 8-byte alignment
+    if (((uintptr_t)psi_c64 & 7u) != 0 || (where == SPE_DEVICE && ((uintptr_t)out2 & 7u) != 0)) return SPE_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return SPE_ECUDA;
     double *scratch = nullptr;
