@@ -72,6 +72,8 @@ extern "C" {
 #define SPE_STATIC_POTENTIAL (1 << 5) /* reserve a static external potential (spe_set_static_potential) */
 #define SPE_PREC_SPLIT16  (1 << 6)  /* axes of 256 or 512 points: radix-16 DFT stages on the tensor cores,
                                        split FP16 (hi + lo) operands, FP32 accumulation */
+#define SPE_NO_TMA        (1 << 7)  /* the strided (y, z) passes stage their tiles with per-thread
+                                       asynchronous copies instead of TMA bulk-tensor copies */
 
 typedef struct spe_grid spe_grid;   /* opaque */
 

@@ -286,6 +286,7 @@ SParams base_y(spe_grid *g, float2 *data, int W, int P)
     p.tile = g->stile[1];
     p.plan = g->splan[1];
     p.tc = g->tc;
+    p.tma = !g->tc && !(g->cfg.flags & SPE_NO_TMA);
     p.tcw = g->tcw;
     p.status = g->status;
     p.S = P;
@@ -309,6 +310,7 @@ SParams base_z(spe_grid *g, float2 *data, int W, int P)
     p.tile = g->stile[2];
     p.plan = g->splan[2];
     p.tc = g->tc;
+    p.tma = !g->tc && !(g->cfg.flags & SPE_NO_TMA);
     p.tcw = g->tcw;
     p.status = g->status;
     p.S = (long long)P * g->n[1];

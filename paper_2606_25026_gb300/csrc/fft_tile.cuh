@@ -338,7 +338,8 @@ __device__ __forceinline__ void fft_stage(float2 *s, const float4 *__restrict__ 
             for (int r = 0; r < R; ++r) v[p][r] = s[(j + r * B) * TP + t];
         }
     }
-    __syncthreads();
+    // the last stage of a transform (Ns R = N) writes back exactly the points each thread read
+    if constexpr (Ns * R != N) __syncthreads();
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
         const int idx = threadIdx.x + p * NT;

@@ -1,9 +1,29 @@
 // Strided-pass dispatch: picks the tile width (the per-length default, or the
 // width the autotuner chose in SParams::tile) and the kernel instance.
+#include <mutex>
+
 #include "spe_internal.cuh"
 #include "fft_tile.cuh"
+#include "tma.cuh"
 
 namespace spe {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
 
 cudaError_t launch_spass_t8(int n, const SParams &p, cudaStream_t st, int *blocks_out);
 cudaError_t launch_spass_t16(int n, const SParams &p, cudaStream_t st, int *blocks_out);

@@ -30,6 +30,7 @@
 #include "reduce.cuh"
 #include "spe_internal.cuh"
 #include "tc16.cuh"
+#include "tma.cuh"
 
 namespace spe {
 
@@ -49,9 +50,10 @@ template <int N, int TW, bool TC = false, int PL = 0> struct SCfg {
     static constexpr int TP = T;
     static constexpr int W = N * T / MaxRadix<typename PlanSel<N, PL>::type>::value;  // butterflies per stage
     static constexpr int NT = W >= 512 ? 512 : (W >= 256 ? 256 : (W >= 128 ? 128 : 64));
+    // + 128: the tile starts at the first 128-byte boundary of the dynamic area (TMA destination)
     static constexpr size_t base = sizeof(float2) * N * TP;
     static constexpr size_t tc_off = (base + 127) & ~(size_t)127;
-    static constexpr size_t smem = TC ? tc_off + sizeof(TcSmem) : base;
+    static constexpr size_t smem = (TC ? tc_off + sizeof(TcSmem) : base) + 128;
 };
 
 struct DriftOp {
@@ -78,11 +80,13 @@ struct PoissonOp {
 };
 
 template <int N, int TW, bool TC = false, int PL = 0>
-__global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams p)
+__global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams p, const __grid_constant__ CUtensorMap tm)
 {
     constexpr int T = SCfg<N, TW, TC, PL>::T, TP = SCfg<N, TW, TC, PL>::TP, NT = SCfg<N, TW, TC, PL>::NT,
                   HT = T / 2;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int BR = tma_box_rows(N), NB = N / BR;
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char *smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     TcSmem *tcs = nullptr;
     if constexpr (TC) {
         tcs = reinterpret_cast<TcSmem *>(smem_raw + SCfg<N, TW, TC>::tc_off);
@@ -91,12 +95,19 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams 
     float2 *tile = reinterpret_cast<float2 *>(smem_raw);
     __shared__ float4 colfac[T];
     __shared__ float colk2[T];
+    __shared__ __align__(8) unsigned long long tma_bar;
     const int c0 = blockIdx.x * T;
     const int b = blockIdx.y;
     const int tid = threadIdx.x;
     const int flags = p.flags;
     float2 *base = p.data + (size_t)b * p.bstride + c0;
+    // the launcher clears p.tma when the tensor map could not be encoded for this shape
+    const bool tma = !TC && p.tma;
 
+    if (tma && tid == 0) {
+        mbar_init(&tma_bar, 1);
+        fence_mbar_init();
+    }
     if (tid < T) {
         const int c = c0 + tid;
         if (flags & S_DRIFT)
@@ -104,12 +115,22 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams 
         if (flags & S_POISSON) colk2[tid] = (c < p.W) ? __ldg(&p.colk2[c]) + __ldg(&p.batchk2[b]) : 0.f;
     }
 
-    for (int idx = tid; idx < N * HT; idx += NT) {
-        const int n = idx / HT, q = idx % HT;
-        if (c0 + 2 * q < p.W) cp_async16(&tile[n * TP + 2 * q], base + (size_t)n * p.S + 2 * q);
-        else *reinterpret_cast<float4 *>(&tile[n * TP + 2 * q]) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tma) {
+        __syncthreads();   // the mbarrier is initialised
+        if (tid == 0) {
+            mbar_expect_tx(&tma_bar, (uint32_t)(N * T * sizeof(float2)));
+#pragma unroll
+            for (int k = 0; k < NB; ++k) tma_load_3d(tile + k * BR * TP, &tm, 2 * c0, k * BR, b, &tma_bar);
+        }
+        if (!mbar_wait(&tma_bar, 0) && (tid & 31) == 0) atomicOr(p.status, kTcStatusTimeout);
+    } else {
+        for (int idx = tid; idx < N * HT; idx += NT) {
+            const int n = idx / HT, q = idx % HT;
+            if (c0 + 2 * q < p.W) cp_async16(&tile[n * TP + 2 * q], base + (size_t)n * p.S + 2 * q);
+            else *reinterpret_cast<float4 *>(&tile[n * TP + 2 * q]) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cp_async_wait_all();
     }
-    cp_async_wait_all();
     __syncthreads();
     if ((flags & (S_FWD | S_INV)) == (S_FWD | S_INV) && (flags & (S_DRIFT | S_POISSON))) {
         if constexpr (TC) {
@@ -147,11 +168,22 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams 
         return;
     }
 
-    for (int idx = tid; idx < N * HT; idx += NT) {
-        const int n = idx / HT, q = idx % HT;
-        if (c0 + 2 * q < p.W)
-            *reinterpret_cast<float4 *>(base + (size_t)n * p.S + 2 * q) =
-                *reinterpret_cast<const float4 *>(&tile[n * TP + 2 * q]);
+    if (tma) {
+        // every thread's tile writes are visible to the async proxy before one thread stores the boxes
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+#pragma unroll
+            for (int k = 0; k < NB; ++k) tma_store_3d(&tm, 2 * c0, k * BR, b, tile + k * BR * TP);
+            tma_store_commit_wait_read();
+        }
+    } else {
+        for (int idx = tid; idx < N * HT; idx += NT) {
+            const int n = idx / HT, q = idx % HT;
+            if (c0 + 2 * q < p.W)
+                *reinterpret_cast<float4 *>(base + (size_t)n * p.S + 2 * q) =
+                    *reinterpret_cast<const float4 *>(&tile[n * TP + 2 * q]);
+        }
     }
     if constexpr (TC) tc_teardown(*tcs);
 }
@@ -205,7 +237,15 @@ static cudaError_t launch_s_nt(const SParams &p, cudaStream_t st, int *blocks_ou
             return cudaGetLastError();
         }
     }
-    spass_kernel<N, TW, TC, PL><<<grid, SCfg<N, TW, TC, PL>::NT, SCfg<N, TW, TC, PL>::smem, st>>>(p);
+    CUtensorMap tm;
+    SParams q = p;
+    if constexpr (TC) {
+        q.tma = 0;
+    } else {
+        if (!encode_spass_tmap(p, N, TW, &tm)) q.tma = 0;
+    }
+    if (!q.tma) memset(&tm, 0, sizeof(tm));
+    spass_kernel<N, TW, TC, PL><<<grid, SCfg<N, TW, TC, PL>::NT, SCfg<N, TW, TC, PL>::smem, st>>>(q, tm);
     return cudaGetLastError();
 }
 

@@ -92,7 +92,8 @@ struct SParams {
     int plan;             // radix schedule: 0 default, 1 and 2 the alternatives (lengths that have them)
     int tc;               // radix-16 stages on the tensor cores (split FP16), N = 256 and 512
     const void *tcw;
-    int *status;          // device status word (tensor-stage timeouts)
+    int *status;          // device status word (tensor-stage and tile-copy timeouts)
+    int tma;              // stage the tiles with TMA bulk-tensor copies where the shape allows
     int flags;
 };
 

@@ -1,0 +1,427 @@
+// Fused x passes of the production step (FP32 Stockham path, gravitating grid).
+//
+// The generic x pass (xpass_impl.cuh) selects its work with runtime flags and
+// moves every intermediate through shared memory.  These two kernels serve the
+// two flag sets every step uses, with the flags known at compile time and the
+// boundaries between transforms fused into register-resident steps:
+//
+//   kick pass (Sec. 3.1 steps (a)/(d) and the first axis of step (b)):
+//     the first inverse stage of the packed Phi lines reads the staged half
+//     spectrum and unpacks it (Hermitian extension of two real rows as one
+//     complex line) on the way; the last inverse stage of Phi is in place per
+//     butterfly (its outputs are its inputs' points), so the thread that owns
+//     it kicks psi at exactly those points of the two rows of the packed line:
+//     psi *= exp(-i (Phi + kappa |psi|^2) dt_k / eta); then the forward
+//     transform of psi.
+//   density pass (last axis of step (b), step (c) and the first axis of the
+//     Poisson transform): the last inverse stage of psi is in place per
+//     butterfly, so its owner forms rho = |psi|^2 (+ rho_*) of the two rows of
+//     a packed line at those points, reduces the mass, and takes the first
+//     stage of the real forward transform of rho with the radix plan reversed
+//     (its first radix is the inverse plan's last, so its butterfly reads the
+//     same points).
+//
+// Every Stockham stage otherwise follows fft_tile.cuh (lanes over lines, tile
+// element-major with pitch TP = T + 1, compensated (hi, lo) twiddles); a
+// transform's last stage skips the barrier between its loads and stores, since
+// each thread writes back the points it read.
+#pragma once
+#include "xpass_impl.cuh"
+
+namespace spe {
+
+template <class L> struct MiddleOf {
+    using type = typename SplitFirst<typename SplitLast<L>::init>::rest;
+};
+
+// The last stage of a transform (Ns = N / R): butterfly j of line t reads and writes the points
+// j + r N/R, so no barrier separates its loads from its stores.  Ends with a barrier.
+template <int N, int T, int TP, int NT, int DIR, int R>
+__device__ __forceinline__ void xf_last_stage(float2 *s, const float4 *__restrict__ tw)
+{
+    constexpr int B = N / R;
+    constexpr int TOTAL = B * T;
+    constexpr int PER = (TOTAL + NT - 1) / NT;
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (TOTAL % NT == 0 || idx < TOTAL) {
+            const int t = idx % T, j = idx / T;
+            float2 v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = s[(j + r * B) * TP + t];
+            if (B > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float4 w = __ldg(&tw[j * r]);
+                    v[r] = cmul_comp(v[r], make_float2(w.x, DIR > 0 ? -w.y : w.y),
+                                     make_float2(w.z, DIR > 0 ? -w.w : w.w));
+                }
+            }
+            Dft<R, DIR>::run(v);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[(j + r * B) * TP + t] = v[r];
+        }
+    }
+    __syncthreads();
+}
+
+// The last stage of a transform straight to the global rows: lanes over the butterflies j of a
+// line (the tile reads stay conflict free at the odd pitch TP, and each warp stores whole row
+// segments), so the tile is not walked again for a separate copy-out.  No barrier at the end.
+template <int N, int T, int TP, int NT, int DIR, int R>
+__device__ __forceinline__ void xf_last_stage_to_rows(const float2 *s, const float4 *__restrict__ tw,
+                                                      float2 *__restrict__ dst, int row0, int rows)
+{
+    constexpr int B = N / R;
+    constexpr int TOTAL = B * T;
+    constexpr int PER = (TOTAL + NT - 1) / NT;
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (TOTAL % NT == 0 || idx < TOTAL) {
+            const int j = idx % B, t = idx / B;
+            float2 v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = s[(j + r * B) * TP + t];
+            if (B > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const float4 w = __ldg(&tw[j * r]);
+                    v[r] = cmul_comp(v[r], make_float2(w.x, DIR > 0 ? -w.y : w.y),
+                                     make_float2(w.z, DIR > 0 ? -w.w : w.w));
+                }
+            }
+            Dft<R, DIR>::run(v);
+            const int row = row0 + t;
+            if (row < rows) {
+                float2 *d = dst + (size_t)row * N + j;
+#pragma unroll
+                for (int r = 0; r < R; ++r) d[r * B] = v[r];
+            }
+        }
+    }
+}
+
+// The stages of a plan that ends the transform (Ns * R = N at its last radix): fft_stage for all
+// but the last, xf_last_stage for the last.
+template <int N, int T, int TP, int NT, int DIR, int Ns, int R>
+__device__ __forceinline__ void xf_stages(float2 *s, const float4 *tw, RList<R>)
+{
+    static_assert(Ns * R == N, "plan does not cover the length");
+    xf_last_stage<N, T, TP, NT, DIR, R>(s, tw);
+}
+template <int N, int T, int TP, int NT, int DIR, int Ns, int R0, int R1, int... Rs>
+__device__ __forceinline__ void xf_stages(float2 *s, const float4 *tw, RList<R0, R1, Rs...>)
+{
+    fft_stage<N, T, TP, NT, DIR, Ns, R0>(s, tw);
+    xf_stages<N, T, TP, NT, DIR, Ns * R0>(s, tw, RList<R1, Rs...>{});
+}
+
+// Packed lines (M = 8 of them, lanes over the line first): element n of line m at aux[n * 8 + m].
+// A half-warp then holds 8 lines x 2 consecutive butterflies; at pitch 8 the points j + r B of two
+// consecutive butterflies fall in opposite halves of the banks, so every stage but the first is
+// conflict free.  The first stage (Ns = 1) writes points j R + r, of equal parity for both
+// butterflies: odd butterflies write their outputs in the order r ^ 1, which puts them in the
+// other half.
+template <int R, int HP>
+__device__ __forceinline__ void xf_store_first_stage(float2 *aux, const float2 (&v)[R], int j, int m)
+{
+    if constexpr (R % 2 == 0) {
+        const bool odd = j & 1;
+#pragma unroll
+        for (int r = 0; r < R; ++r) aux[(j * R + (r ^ (int)odd)) * HP + m] = odd ? v[r ^ 1] : v[r];
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) aux[(j * R + r) * HP + m] = v[r];
+    }
+}
+
+// rows t of the tile from global rows row0 + t (zeros past the last row), asynchronously; one warp
+// per row, lanes over the points (coalesced reads, conflict-free element-major writes)
+template <int N, int T, int TP, int NT>
+__device__ __forceinline__ void xf_rows_in(float2 *tile, const float2 *__restrict__ src, int row0, int rows)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = warp; t < T; t += NT / 32) {
+        const int row = row0 + t;
+        if (row < rows) {
+            const float2 *r = src + (size_t)row * N;
+            for (int n = lane; n < N; n += 32) cp_async8(&tile[n * TP + t], r + n);
+        } else {
+            for (int n = lane; n < N; n += 32) tile[n * TP + t] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
+template <int N, int T, int TP, int NT>
+__device__ __forceinline__ void xf_rows_out(const float2 *tile, float2 *__restrict__ dst, int row0, int rows)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = warp; t < T; t += NT / 32) {
+        const int row = row0 + t;
+        if (row < rows) {
+            float2 *r = dst + (size_t)row * N;
+            for (int n = lane; n < N; n += 32) r[n] = tile[n * TP + t];
+        }
+    }
+}
+
+// Resident CTAs per SM the register allocation is held to: as many as the tile's shared memory
+// allows, up to 1024 threads per SM (64 registers a thread).  The 256-point density pass holds
+// 32 complex values across its fused radix-16 step and keeps three CTAs (85 registers) instead of
+// spilling at 64.
+template <int N, bool DENS> struct XFMinBlocks {
+    static constexpr int by_smem = (int)((227 * 1024) / (XCfg<N>::smem + 1024));
+    static constexpr int by_threads = 1024 / XCfg<N>::NT;
+    static constexpr int fit = by_smem < by_threads ? by_smem : by_threads;
+    static constexpr int value = (DENS && N == 256 && fit > 3) ? 3 : (fit < 1 ? 1 : fit);
+};
+
+template <int N> constexpr bool xfused_ok() { return N >= 32 && Length<typename Plan<N>::type>::value >= 2; }
+
+// ---------------------------------------------------------------- kick pass
+// flags X_HAS_PHI | X_KICK | X_FFT, plus X_WRITE_PHI when WPHI (stars interpolate the real Phi).
+template <int N, bool WPHI>
+__global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, false>::value) xkick_fused_kernel(XParams p)
+{
+    using C = XCfg<N>;
+    constexpr int T = C::T, TP = C::TP, NT = C::NT, H = N / 2, M = T / 2, HP = M, SP = H + 1;
+    using PP = typename Plan<N>::type;      // Phi, inverse: R_1 .. R_m
+    using PS = typename Reverse<PP>::type;  // psi, forward: R_m .. R_1
+    constexpr int R1 = SplitFirst<PP>::first, RL = SplitLast<PP>::last;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+    float2 *aux = tile + N * TP;   // staged half-spectrum rows [t * SP + k], then packed lines [n * HP + m]
+    const int row0 = blockIdx.x * T, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+
+    // half-spectrum rows of Phi first, then psi, all in flight at once
+    for (int t = warp; t < T; t += NT / 32) {
+        const int row = row0 + t;
+        if (row < p.rows) {
+            const float2 *r = p.phik + (size_t)row * p.P;
+            for (int k = lane; k < SP; k += 32) cp_async8(&aux[t * SP + k], r + k);
+        } else {
+            for (int k = lane; k < SP; k += 32) aux[t * SP + k] = make_float2(0.f, 0.f);
+        }
+    }
+    cp_async_commit();
+    xf_rows_in<N, T, TP, NT>(tile, p.psi, row0, p.rows);
+    cp_async_commit();
+    cp_async_wait_group<1>();
+    __syncthreads();
+
+    // first inverse stage of the packed lines Z_m = A + i B (A, B the rows 2m, 2m + 1), with the
+    // Hermitian extension A_{N-n} = conj A_n read straight from the staged rows
+    {
+        constexpr int B = N / R1, TOTAL = B * M, PER = (TOTAL + NT - 1) / NT;
+        float2 v[PER][R1];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int idx = tid + q * NT;
+            if (TOTAL % NT == 0 || idx < TOTAL) {
+                const int m = idx % M, j = idx / M;
+                const float2 *ra = aux + (2 * m) * SP;
+                const float2 *rb = ra + SP;
+#pragma unroll
+                for (int r = 0; r < R1; ++r) {
+                    const int n = j + r * B;
+                    float2 A, Bv;
+                    if (n <= H) {
+                        A = ra[n];
+                        Bv = rb[n];
+                        if (n == 0 || n == H) {
+                            A.y = 0.f;
+                            Bv.y = 0.f;
+                        }
+                    } else {
+                        A = cconj(ra[N - n]);
+                        Bv = cconj(rb[N - n]);
+                    }
+                    v[q][r] = make_float2(A.x - Bv.y, A.y + Bv.x);
+                }
+            }
+        }
+        __syncthreads();   // the packed lines overwrite the staged rows
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int idx = tid + q * NT;
+            if (TOTAL % NT == 0 || idx < TOTAL) {
+                const int m = idx % M, j = idx / M;
+                Dft<R1, +1>::run(v[q]);
+                xf_store_first_stage<R1, HP>(aux, v[q], j, m);
+            }
+        }
+        cp_async_wait_group<0>();
+        __syncthreads();
+    }
+    // the inverse stages between the first and the last
+    fft_stages<N, M, HP, NT, +1, R1>(aux, p.tw, typename MiddleOf<PP>::type{});
+
+    // last inverse stage of Phi (in place per butterfly) and the kick of psi at its points
+    {
+        constexpr int B = N / RL, TOTAL = B * M, PER = (TOTAL + NT - 1) / NT;
+        const float ks = p.kick_scale, kap = p.kappa;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int idx = tid + q * NT;
+            if (TOTAL % NT == 0 || idx < TOTAL) {
+                const int m = idx % M, j = idx / M;
+                float2 f[RL];
+#pragma unroll
+                for (int r = 0; r < RL; ++r) f[r] = aux[(j + r * B) * HP + m];
+                if (B > 1) {
+#pragma unroll
+                    for (int r = 1; r < RL; ++r) {
+                        const float4 w = __ldg(&p.tw[j * r]);
+                        f[r] = cmul_comp(f[r], make_float2(w.x, -w.y), make_float2(w.z, -w.w));
+                    }
+                }
+                Dft<RL, +1>::run(f);
+                // f[r] = Phi(row 2m, point j + r B) + i Phi(row 2m + 1, point j + r B)
+#pragma unroll
+                for (int r = 0; r < RL; ++r) {
+                    const int n = j + r * B;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int t = 2 * m + h;
+                        const float phi = h ? f[r].y : f[r].x;
+                        float2 v = tile[n * TP + t];
+                        // v exp(-i ph) = v + v (cos ph - 1 - i sin ph), cos ph - 1 = -2 sin^2(ph / 2)
+                        const float a2 = v.x * v.x + v.y * v.y;
+                        float sh, ch;
+                        half_angle_sincos(0.5f * ((phi + kap * a2) * ks), sh, ch);
+                        const float cm1 = -2.f * sh * sh, sn = 2.f * sh * ch;
+                        v = make_float2(fmaf(v.x, cm1, fmaf(v.y, sn, v.x)), fmaf(v.y, cm1, fmaf(-v.x, sn, v.y)));
+                        tile[n * TP + t] = v;
+                        if (WPHI && row0 + t < p.rows) p.phi_out[(size_t)(row0 + t) * N + n] = phi;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // forward transform of psi with the reversed plan, its last stage storing the rows
+    fft_stages<N, T, TP, NT, -1, 1>(tile, p.tw, typename SplitLast<PS>::init{});
+    xf_last_stage_to_rows<N, T, TP, NT, -1, SplitLast<PS>::last>(tile, p.tw, p.psi, row0, p.rows);
+}
+
+// ---------------------------------------------------------------- density pass
+// flags X_IFFT | X_MASS | X_R2C, plus X_DEP when DEP (the stars' fixed-point deposit).
+template <int N, bool DEP>
+__global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, true>::value) xdens_fused_kernel(XParams p)
+{
+    using C = XCfg<N>;
+    constexpr int T = C::T, TP = C::TP, NT = C::NT, H = N / 2, M = T / 2, HP = M, DP = N + 2;
+    using PI = typename Plan<N>::type;      // psi, inverse: R_1 .. R_m
+    using PR = typename Reverse<PI>::type;  // packed rho, forward: R_m .. R_1
+    constexpr int RL = SplitLast<PI>::last;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    static_assert((size_t)T * DP * sizeof(float) <= C::aux_bytes && (size_t)N * HP * sizeof(float2) <= C::aux_bytes,
+                  "aux area too small");
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+    float2 *aux = tile + N * TP;                  // packed rho lines [n * HP + m]
+    float *auxf = reinterpret_cast<float *>(aux);  // before them: deposit rows [t * DP + n]
+    const int row0 = blockIdx.x * T, tid = threadIdx.x;
+
+    xf_rows_in<N, T, TP, NT>(tile, p.psi, row0, p.rows);
+    cp_async_commit();
+    unsigned live_rows = 0;   // bit t: row row0 + t holds deposit (marked by the star kernel)
+    if (DEP) {
+        const uint4 f = __ldg(reinterpret_cast<const uint4 *>(p.dflag + row0));
+        const unsigned w[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+            if (((w[t >> 2] >> (8 * (t & 3))) & 0xffu) && row0 + t < p.rows) live_rows |= 1u << t;
+        // loads only here: a zero store to an address whose load is still in flight would wait for it
+        const long long *__restrict__ dep = p.dep + (size_t)row0 * N;
+#pragma unroll 4
+        // rows at pitch N + 2: the fused step below reads 8 rows x 4 points per warp, conflict free
+        for (int idx = tid; idx < T * N; idx += NT) {
+            const int t = idx / N;
+            auxf[t * DP + (idx - t * N)] = ((live_rows >> t) & 1u) ? (float)__ldcs(&dep[idx]) * p.dep_scale : 0.f;
+        }
+    }
+    cp_async_wait_group<0>();
+    __syncthreads();
+    if (DEP) {
+        long long *__restrict__ dep = p.dep + (size_t)row0 * N;
+        for (int idx = tid; idx < T * N; idx += NT)
+            if ((live_rows >> (idx / N)) & 1u) __stcs(&dep[idx], 0ll);
+        if (tid < T && ((live_rows >> tid) & 1u)) p.dflag[row0 + tid] = 0;
+    }
+
+    // inverse stages of psi but the last
+    fft_stages<N, T, TP, NT, +1, 1>(tile, p.tw, typename SplitLast<PI>::init{});
+
+    // last inverse stage of psi (in place per butterfly) for the rows 2m, 2m + 1, rho at its points,
+    // and the first forward stage of the packed line Z_m = rho_2m + i rho_2m+1
+    float msum = 0.f;
+    {
+        constexpr int B = N / RL, TOTAL = B * M, PER = (TOTAL + NT - 1) / NT;
+        float2 z[PER][RL];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int idx = tid + q * NT;
+            if (TOTAL % NT == 0 || idx < TOTAL) {
+                const int m = idx % M, j = idx / M;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int t = 2 * m + h;
+                    float2 v[RL];
+#pragma unroll
+                    for (int r = 0; r < RL; ++r) v[r] = tile[(j + r * B) * TP + t];
+                    if (B > 1) {
+#pragma unroll
+                        for (int r = 1; r < RL; ++r) {
+                            const float4 w = __ldg(&p.tw[j * r]);
+                            v[r] = cmul_comp(v[r], make_float2(w.x, -w.y), make_float2(w.z, -w.w));
+                        }
+                    }
+                    Dft<RL, +1>::run(v);
+#pragma unroll
+                    for (int r = 0; r < RL; ++r) {
+                        tile[(j + r * B) * TP + t] = v[r];
+                        float rho = v[r].x * v[r].x + v[r].y * v[r].y;
+                        msum += rho;
+                        if (DEP) rho += auxf[t * DP + j + r * B];
+                        if (h) z[q][r].y = rho;
+                        else z[q][r].x = rho;
+                    }
+                }
+            }
+        }
+        __syncthreads();   // the deposit rows in aux are all read; the packed lines overwrite them
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int idx = tid + q * NT;
+            if (TOTAL % NT == 0 || idx < TOTAL) {
+                const int m = idx % M, j = idx / M;
+                Dft<RL, -1>::run(z[q]);
+                xf_store_first_stage<RL, HP>(aux, z[q], j, m);
+            }
+        }
+        __syncthreads();
+    }
+    xf_rows_out<N, T, TP, NT>(tile, p.psi, row0, p.rows);
+    // the remaining forward stages of the packed lines
+    xf_stages<N, M, HP, NT, -1, RL>(aux, p.tw, typename SplitFirst<PR>::rest{});
+    // separate the two real rows: A_k = (Z_k + conj Z_{N-k}) / 2, B_k = (Z_k - conj Z_{N-k}) / (2i)
+    for (int idx = tid; idx < M * (H + 1); idx += NT) {
+        const int m = idx % M, k = idx / M;
+        const int ra = row0 + 2 * m;
+        const float2 Z = aux[k * HP + m];
+        const float2 Zc = cconj(aux[((N - k) % N) * HP + m]);
+        const float2 A = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
+        const float2 D = csub(Z, Zc);
+        const float2 Bk = make_float2(0.5f * D.y, -0.5f * D.x);
+        if (ra < p.rows) p.phik[(size_t)ra * p.P + k] = A;
+        if (ra + 1 < p.rows) p.phik[(size_t)(ra + 1) * p.P + k] = Bk;
+    }
+    double v[1] = {(double)msum};
+    grid_reduce<1, NT>(v, 0, p.partials, p.counter, p.result, p.result + 1, p.mass_scale);
+}
+
+}  // namespace spe

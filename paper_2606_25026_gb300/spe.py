@@ -24,6 +24,7 @@ SPE_PROFILE = 1 << 3
 SPE_NO_GRAPH = 1 << 4
 SPE_STATIC_POTENTIAL = 1 << 5
 SPE_PREC_SPLIT16 = 1 << 6
+SPE_NO_TMA = 1 << 7
 
 SUPPORTED_N = (4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024)
 
