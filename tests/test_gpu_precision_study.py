@@ -1,6 +1,7 @@
 """Precision study of the halo workload family: the FP32 path and the split-FP16 tensor-core path
 against the FP64 oracle over 200 steps, on a 256 x 256 x 32 grid (x and y on the tensor cores in
-split mode, z in FP32; the oracle at full 512^3 would take hours on the host).  Reports the
+split mode, z in FP32), small enough for a test run; the full 512^3 study is
+``bench.py --workload precision512`` (the oracle takes about half an hour there).  Reports the
 relative L2 error of psi, the mass and energy drifts and the error of the density power spectrum
 P(k) in shells of width 2 pi / L, per precision.
 
