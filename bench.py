@@ -268,8 +268,10 @@ def reference_arm(args, rank, world):
 
 
 def ensemble_arm(args, r):
-    """64 independent halos of uneven sizes stepped as one batch (a CUDA graph with a branch per
-    member); value = sum over members of cells x steps / time."""
+    """64 independent halos of uneven sizes stepped as one batch: by default one persistent
+    cooperative launch per step (eight phases, each a work list of every member's tiles, with
+    grid-wide barriers), and for comparison the graph of per-member branches.  value = sum over
+    members of cells x steps / time of the persistent form."""
     import torch
     from paper_2606_25026_gb300 import inputs, spe
     rank, world, local = r.rank, r.world, r.local
@@ -281,40 +283,52 @@ def ensemble_arm(args, r):
         if len(m["mass"]):
             g.add_particles(m["pos"], m["vel"], m["mass"])
     if not args.no_autotune:
-        b.autotune()
+        b.autotune()          # the graph form's strided tiles; the persistent form has its own
     dts = [m["dt"] for m in members]
-    b.step(max(args.warmup, 3), dts)
     cells = sum(m["n"] ** 3 for m in members)
     stars = sum(len(m["mass"]) for m in members)
-    l0 = b.launch_count()
-    replicas.barrier(r)
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    b.step(args.steps, dts)
-    b.settle()          # the members' closing half kicks, inside the timed region
-    ev1.record(stream)
-    ev1.synchronize()
-    replicas.barrier(r)
-    clk = clocks.stop()
-    ms = replicas.max_over_ranks(r, ev0.elapsed_time(ev1), device="cuda")
-    # 112 B/cell without stars; with stars + 4 (Phi for the stars) + 16 f (the deposit's rows)
-    bytes_step = sum(((116.0 + 16.0 * deposit_row_fraction(m["pos"], (m["n"],) * 3)) if len(m["mass"]) else 112.0)
-                     * m["n"] ** 3 for m in members)
+    # 112 B/cell without stars; with stars + 8 (Phi for the stars, rho_* for the density) and about
+    # 100 B per star
+    bytes_step = sum((120.0 if len(m["mass"]) else 112.0) * m["n"] ** 3 + 100.0 * len(m["mass"]) for m in members)
     peak, kind = measured_peak()
+
+    def timed(persistent):
+        b.set_persistent(persistent)
+        b.step(max(args.warmup, 3), dts)
+        l0 = b.launch_count()
+        replicas.barrier(r)
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        b.step(args.steps, dts)
+        b.settle()          # the members' closing half kicks, inside the timed region
+        ev1.record(stream)
+        ev1.synchronize()
+        replicas.barrier(r)
+        clk = clocks.stop()
+        ms = replicas.max_over_ranks(r, ev0.elapsed_time(ev1), device="cuda")
+        return ms, int(b.launch_count() - l0), clk, b.persistent()
+
+    ms_g, launches_g, clk_g, _ = timed(False)
+    ms, launches, clk, used = timed(True)
     ach = bytes_step * args.steps / (ms * 1e-3) / 1e9
+    ach_g = bytes_step * args.steps / (ms_g * 1e-3) / 1e9
     line = {"metric": "grid_cell_steps_per_s", "value": replicas.job_rate(r, cells * args.steps, ms * 1e-3),
             "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64", "data": "synthetic",
             "config": {"workload": "ensemble64", "members": len(members),
                        "sizes": {str(n): sum(1 for m in members if m["n"] == n) for n in (64, 96, 128, 192)},
-                       "cells": cells, "stars": stars, "autotune": not args.no_autotune},
+                       "cells": cells, "stars": stars, "autotune": not args.no_autotune,
+                       "launch": "persistent" if used else "graph of per-member branches"},
             "step_roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                              "model": "per member 112 B/cell/step without stars, 116 + 16 f with (f the "
-                                       "fraction of rows holding deposits)"},
-            "gpu_launches": int(b.launch_count() - l0), "clocks": clk}
+                              "model": "per member 112 B/cell/step without stars, 120 with, + 100 B per star"},
+            "graph_branches": {"value": replicas.job_rate(r, cells * args.steps, ms_g * 1e-3),
+                               "ms_per_step": ms_g / args.steps, "frac": ach_g / peak, "gpu_launches": launches_g,
+                               "clocks": clk_g},
+            "speedup_vs_graph_branches": ms_g / ms,
+            "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.destroy()

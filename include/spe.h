@@ -261,11 +261,19 @@ SPE_API int spe_set_schedule(spe_grid *g, const int *tiles, const int *plans);
 SPE_API int spe_get_schedule(spe_grid *g, int *tiles, int *plans);
 
 /* A batch of independent grids (sizes, parameters and particle counts may
- * all differ), stepped together: each member runs on its own stream and the
- * members' full steps are the parallel branches of one CUDA graph replayed on
- * the batch stream cfgs[0].cuda_stream.  Members allocate their own
- * workspaces; use spe_batch_grid to reach a member for spe_set_ic,
- * spe_add_particles, spe_get_psi, spe_energy, ... (not spe_destroy). */
+ * all differ), stepped together on the batch stream cfgs[0].cuda_stream.
+ * Members allocate their own workspaces; use spe_batch_grid to reach a member
+ * for spe_set_ic, spe_add_particles, spe_get_psi, spe_energy, ... (not
+ * spe_destroy).
+ * Two ways to run a step.  Persistent (the default when every member is a
+ * gravitating cube of 64, 96, 128 or 192 points without a static potential,
+ * an absorbing layer, tensor-core stages or SPE_PROFILE): one cooperative
+ * kernel launch per step walks eight phases (the passes of the step), each a
+ * work list of every member's tiles, with a grid-wide barrier between phases;
+ * full steps replay that launch as a CUDA graph.  Otherwise: each member runs
+ * its kernels on its own stream and the members' full steps are the parallel
+ * branches of one CUDA graph.  Both give every member bitwise the result of
+ * the same grid stepped alone. */
 typedef struct spe_batch spe_batch;
 SPE_API int spe_batch_create(const spe_config *cfgs, int count, spe_batch **out);
 SPE_API int spe_batch_grid(spe_batch *b, int index, spe_grid **out);
@@ -279,7 +287,28 @@ SPE_API int spe_batch_step(spe_batch *b, int nsteps, const double *dts);
 SPE_API int spe_batch_settle(spe_batch *b);
 /* kernel launches of all members since creation (graph replays counted per node) */
 SPE_API int spe_batch_launch_count(spe_batch *b, unsigned long long *count_out);
+/* Choose the persistent launch (on = 1, used where the members qualify) or the
+ * graph of per-member branches (on = 0).  wait_limit: polls of a grid-wide
+ * barrier before the kernel gives up (-1: the default, about half a second);
+ * a wait that gives up makes spe_batch_step return SPE_ETIMEOUT without
+ * hanging, and leaves the members' state undefined (set it again).  A limit
+ * of 0 makes every barrier give up unless it is already complete (a way to
+ * exercise that path).  spe_batch_get_persistent: 1 when the next step will
+ * use the persistent launch. */
+SPE_API int spe_batch_set_persistent(spe_batch *b, int on, long long wait_limit);
+SPE_API int spe_batch_get_persistent(spe_batch *b, int *on_out);
 SPE_API int spe_batch_destroy(spe_batch *b);
+
+/* Per-sample squared norms, for the surrogate's output scale and its relative
+ * errors against the solver (the paper has no counterpart): a and b hold
+ * `samples` fields of n complex64 values each in device memory, sample after
+ * sample (a may equal b); out is 2 * samples doubles of device memory and
+ * receives out[2s] = sum_i |a_si - b_si|^2 and out[2s + 1] = sum_i |b_si|^2,
+ * accumulated in FP64 in a fixed order (bitwise reproducible).  Asynchronous
+ * on cuda_stream (cudaStream_t or NULL); the caller keeps all three buffers.
+ * SPE_EINVAL for a NULL pointer, n == 0, samples <= 0 or a pointer that is not
+ * 8-byte aligned. */
+SPE_API int spe_pair_norms(const void *a, const void *b, size_t n, int samples, double *out, void *cuda_stream);
 
 /* Human-readable text for a status code (static storage). */
 SPE_API const char *spe_strerror(int status);

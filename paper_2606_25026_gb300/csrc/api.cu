@@ -1470,9 +1470,80 @@ struct spe_batch {
     std::vector<size_t> key_np;
     std::vector<int> key_tiles;
     std::vector<unsigned long long> nodes;  // kernel launches per member in one captured step
+    // one persistent launch per step (batch_persist.cu)
+    bool persist;                           // use it when every member qualifies
+    long long wait_limit;                   // barrier polls before a wait gives up
+    int pblocks;                            // co-resident CTAs of the persistent kernel
+    spe::BatchMember *d_mem;                // [2][count]: the first step of a call, then full steps
+    int *d_offs;                            // kBatchPhases x (count + 1) work-list prefix sums
+    unsigned int *d_bar;                    // barrier counter
+    int *d_status;                          // timeout bit
+    cudaGraphExec_t pexec;                  // memset of the counter + the launch of one full step
+    std::vector<double> pkey_dt;
+    std::vector<size_t> pkey_np;
+    unsigned long long plaunches;           // persistent launches (kernel launches outside the members)
 };
 
 namespace {
+
+constexpr long long kBatchWaitLimit = 1ll << 22;   // ~0.5 s of polling per barrier
+
+// the persistent kernel carries code for gravitating cubic members of 64, 96, 128 or 192 points without
+// a static potential, an absorbing layer or tensor-core stages
+bool persist_member_ok(const spe_grid *g)
+{
+    return g->n[0] == g->n[1] && g->n[1] == g->n[2] && spe::batch_persist_n_ok(g->n[0]) && g->gravity && !g->tc &&
+           !g->static_set && !g->absorbing && !(g->cfg.flags & SPE_PROFILE);
+}
+
+bool persist_ok(const spe_batch *b)
+{
+    if (!b->persist) return false;
+    for (auto g : b->g)
+        if (!persist_member_ok(g)) return false;
+    return true;
+}
+
+// A member's passes for one step with leading kick dtk (the first step of a call) or dt (full
+// steps), as step_body issues them for such a grid.
+spe::BatchMember persist_member(spe_grid *g, double dtk, double dt)
+{
+    spe::BatchMember m;
+    memset(&m, 0, sizeof(m));
+    const bool parts = g->np > 0;
+    const bool skick = parts && stars_kicked(g);
+    m.xk = base_x(g);
+    m.xk.flags = X_FFT | X_KICK | X_HAS_PHI | (skick ? X_WRITE_PHI : 0);
+    m.xk.kick_scale = (float)(dtk / g->cfg.hbar_over_m);
+    m.xd = base_x(g);
+    m.xd.flags = X_IFFT | X_MASS | X_R2C | (parts ? X_DEP : 0);
+    auto strided = [](SParams q, int flags) {
+        q.flags = flags;
+        q.tile = spe::kBatchTile;
+        q.plan = 0;
+        q.tma = 0;
+        q.tc = 0;
+        return q;
+    };
+    m.yf = strided(base_y(g, g->psi, g->n[0], g->n[0]), S_FWD);
+    m.zd = strided(base_z(g, g->psi, g->n[0], g->n[0]), S_FWD | S_DRIFT | S_INV);
+    m.yi = strided(base_y(g, g->psi, g->n[0], g->n[0]), S_INV);
+    m.rf = strided(base_y(g, g->phik, g->W, g->P), S_FWD);
+    m.rp = strided(base_z(g, g->phik, g->W, g->P), S_FWD | S_POISSON | S_INV);
+    m.ri = strided(base_y(g, g->phik, g->W, g->P), S_INV);
+    if (parts) {
+        m.pp = base_p(g);
+        m.pp.flags = PK_DRIFT | (skick ? PK_KICK : 0) | PK_DEPOSIT;
+        m.pp.kick = (float)dtk;
+        m.pp.drift = (float)dt;
+    }
+    m.n = g->n[0];
+    m.xtiles = (g->n[1] * g->n[2] + 15) / 16;
+    m.cols_psi = (g->n[0] + spe::kBatchTile - 1) / spe::kBatchTile;
+    m.cols_rho = (g->W + spe::kBatchTile - 1) / spe::kBatchTile;
+    m.pblocks = parts ? (int)((g->np + 255) / 256) : 0;
+    return m;
+}
 
 // every member stream waits for the batch stream
 int batch_fork(spe_batch *b)
@@ -1550,6 +1621,140 @@ int batch_graph(spe_batch *b, const double *dts)
     return SPE_OK;
 }
 
+// One step of every member as one launch: the work lists of the step's phases (prefix sums per
+// member) and the members' pass parameters go to the device; the barrier counter is cleared first.
+int persist_launch(spe_batch *b, const spe::BatchMember *d_set)
+{
+    spe::BatchLaunch L;
+    L.m = d_set;
+    L.count = (int)b->g.size();
+    L.offs = b->d_offs;
+    L.bar = b->d_bar;
+    L.status = b->d_status;
+    L.wait_limit = b->wait_limit;
+    if (cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned int), b->st) != cudaSuccess) return SPE_ECUDA;
+    return cuerr(spe::launch_batch_persist(L, b->pblocks, b->st));
+}
+
+int persist_setup(spe_batch *b)
+{
+    if (b->d_mem) return SPE_OK;
+    const size_t n = b->g.size();
+    if (cuerr(spe::batch_persist_setup(&b->pblocks))) return SPE_ECUDA;
+    if (cudaMalloc(&b->d_mem, 2 * n * sizeof(spe::BatchMember)) != cudaSuccess ||
+        cudaMalloc(&b->d_offs, spe::kBatchPhases * (n + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_bar, 256) != cudaSuccess || cudaMalloc(&b->d_status, 256) != cudaSuccess) {
+        cudaGetLastError();
+        return SPE_ENOMEM;
+    }
+    if (cudaMemsetAsync(b->d_status, 0, sizeof(int), b->st) != cudaSuccess) return SPE_ECUDA;
+    return SPE_OK;
+}
+
+int persist_step(spe_batch *b, int nsteps, const double *dts)
+{
+    const size_t n = b->g.size();
+    int rc;
+    if ((rc = persist_setup(b))) return rc;
+    // the batch stream takes over: it waits for the members' earlier work, and every member operation
+    // of this call (tables, Phi(0), star reordering) goes onto it
+    if ((rc = batch_join(b))) return rc;
+    std::vector<cudaStream_t> own(n);
+    for (size_t i = 0; i < n; ++i) {
+        own[i] = b->g[i]->st;
+        b->g[i]->st = b->st;
+    }
+    auto restore = [&](int code) {
+        for (size_t i = 0; i < n; ++i) b->g[i]->st = own[i];
+        const int f = batch_fork(b);
+        return code ? code : f;
+    };
+    std::vector<spe::BatchMember> h(2 * n);
+    std::vector<int> offs(spe::kBatchPhases * (n + 1), 0);
+    for (size_t i = 0; i < n; ++i) {
+        spe_grid *g = b->g[i];
+        if ((rc = ensure_drift_tables(g, dts[i]))) return restore(rc);
+        if (!g->phi_valid && (rc = compute_phi(g))) return restore(rc);
+        const double lead = g->kick_pending ? g->pending_h + 0.5 * dts[i] : 0.5 * dts[i];
+        g->kick_pending = false;
+        h[i] = persist_member(g, lead, dts[i]);
+        h[n + i] = persist_member(g, dts[i], dts[i]);
+        const spe::BatchMember &m = h[i];
+        const int items[spe::kBatchPhases] = {m.xtiles, m.cols_psi * m.n + m.pblocks, m.cols_psi * m.n,
+                                              m.cols_psi * m.n, m.xtiles, m.cols_rho * m.n, m.cols_rho * m.n,
+                                              m.cols_rho * m.n};
+        for (int ph = 0; ph < spe::kBatchPhases; ++ph) offs[ph * (n + 1) + i + 1] = offs[ph * (n + 1) + i] + items[ph];
+    }
+    if (cudaMemcpyAsync(b->d_mem, h.data(), h.size() * sizeof(spe::BatchMember), cudaMemcpyHostToDevice, b->st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->d_offs, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice, b->st) !=
+            cudaSuccess)
+        return restore(SPE_ECUDA);
+    // the full-step launch as a graph, captured again when dt or a star count changes
+    bool same = b->pexec && b->pkey_dt.size() == n;
+    for (size_t i = 0; same && i < n; ++i) same = b->pkey_dt[i] == dts[i] && b->pkey_np[i] == b->g[i]->np;
+    if (nsteps > 1 && !same) {
+        if (b->pexec) {
+            cudaGraphExecDestroy(b->pexec);
+            b->pexec = nullptr;
+        }
+        cudaStream_t keep = b->st;
+        b->st = b->cap;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        int lrc = (e == cudaSuccess) ? persist_launch(b, b->d_mem + n) : SPE_ECUDA;
+        const cudaError_t e2 = (e == cudaSuccess) ? cudaStreamEndCapture(b->cap, &graph) : e;
+        b->st = keep;
+        if (!lrc && e2 == cudaSuccess && cudaGraphInstantiate(&b->pexec, graph, 0) == cudaSuccess) {
+            b->pkey_dt.assign(dts, dts + n);
+            b->pkey_np.resize(n);
+            for (size_t i = 0; i < n; ++i) b->pkey_np[i] = b->g[i]->np;
+        } else {
+            b->pexec = nullptr;   // the steps go out as direct launches
+        }
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        for (size_t i = 0; i < n; ++i) {
+            spe_grid *g = b->g[i];
+            if (g->np && (g->sort_due || g->steps_done % kSortEvery == 0) && (rc = sort_particles(g)))
+                return restore(rc);
+        }
+        if (s > 0 && b->pexec) rc = cuerr(cudaGraphLaunch(b->pexec, b->st));
+        else rc = persist_launch(b, b->d_mem + (s == 0 ? 0 : n));
+        if (rc) return restore(rc);
+        b->plaunches++;
+        for (auto g : b->g) g->steps_done++;
+    }
+    for (size_t i = 0; i < n; ++i) {
+        spe_grid *g = b->g[i];
+        g->kick_pending = true;
+        g->pending_h = 0.5 * dts[i];
+        g->pending_dt = dts[i];
+    }
+    int status = 0;
+    if (cudaMemcpyAsync(&status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->st) != cudaSuccess ||
+        cudaStreamSynchronize(b->st) != cudaSuccess)
+        return restore(SPE_ECUDA);
+    if (status) {
+        // the launch stopped part way: clear what a partial step leaves behind (star deposits, row
+        // marks, reduction tickets) so that setting the state again starts from clean buffers
+        if (cudaMemsetAsync(b->d_status, 0, sizeof(int), b->st) != cudaSuccess) return restore(SPE_ECUDA);
+        for (auto g : b->g) {
+            if (g->dep && cudaMemsetAsync(g->dep, 0, g->ncells * sizeof(long long), b->st) != cudaSuccess)
+                return restore(SPE_ECUDA);
+            if (g->dflag && cudaMemsetAsync(g->dflag, 0, (size_t)g->n[1] * g->n[2], b->st) != cudaSuccess)
+                return restore(SPE_ECUDA);
+            if (cudaMemsetAsync(g->counter, 0, sizeof(unsigned int), b->st) != cudaSuccess) return restore(SPE_ECUDA);
+            g->phi_valid = false;
+        }
+        if (cudaStreamSynchronize(b->st) != cudaSuccess) return restore(SPE_ECUDA);
+        return restore(SPE_ETIMEOUT);
+    }
+    return restore(SPE_OK);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1563,7 +1768,12 @@ int spe_batch_destroy(spe_batch *b)
     for (auto e : b->ev) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->pexec) cudaGraphExecDestroy(b->pexec);
     if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->d_mem);
+    cudaFree(b->d_offs);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_status);
     delete b;
     return SPE_OK;
 }
@@ -1574,6 +1784,8 @@ int spe_batch_create(const spe_config *cfgs, int count, spe_batch **out)
     *out = nullptr;
     spe_batch *b = new (std::nothrow) spe_batch();
     if (!b) return SPE_ENOMEM;
+    b->persist = true;
+    b->wait_limit = kBatchWaitLimit;
     b->st = (cudaStream_t)cfgs[0].cuda_stream;
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1646,6 +1858,7 @@ int spe_batch_step(spe_batch *b, int nsteps, const double *dts)
         if (g->kick_pending && g->pending_dt != dts[i] && (rc = settle(g))) return rc;
         g->host_mass_valid = false;
     }
+    if (persist_ok(b)) return persist_step(b, nsteps, dts);
     if ((rc = batch_fork(b))) return rc;
     for (size_t i = 0; i < n; ++i) {
         spe_grid *g = b->g[i];
@@ -1690,9 +1903,32 @@ int spe_batch_settle(spe_batch *b)
 int spe_batch_launch_count(spe_batch *b, unsigned long long *count_out)
 {
     if (!b || !count_out) return SPE_EINVAL;
-    unsigned long long c = 0;
+    unsigned long long c = b->plaunches;
     for (auto g : b->g) c += g->launches;
     *count_out = c;
+    return SPE_OK;
+}
+
+int spe_pair_norms(const void *a, const void *b, size_t n, int samples, double *out, void *cuda_stream)
+{
+    if (!a || !b || !out || n == 0 || samples <= 0) return SPE_EINVAL;
+    if ((((uintptr_t)a | (uintptr_t)b | (uintptr_t)out) & 7) != 0) return SPE_EINVAL;
+    return cuerr(spe::launch_pair_norms(static_cast<const float2 *>(a), static_cast<const float2 *>(b), n, samples,
+                                        out, (cudaStream_t)cuda_stream));
+}
+
+int spe_batch_set_persistent(spe_batch *b, int on, long long wait_limit)
+{
+    if (!b || wait_limit < -1) return SPE_EINVAL;
+    b->persist = on != 0;
+    b->wait_limit = wait_limit < 0 ? kBatchWaitLimit : wait_limit;
+    return SPE_OK;
+}
+
+int spe_batch_get_persistent(spe_batch *b, int *on_out)
+{
+    if (!b || !on_out) return SPE_EINVAL;
+    *on_out = persist_ok(b) ? 1 : 0;
     return SPE_OK;
 }
 

@@ -35,6 +35,33 @@ __global__ void __launch_bounds__(kDiagNT) grid_diag_kernel(const float2 *__rest
     grid_reduce<5, kDiagNT>(acc, (1 << 3) | (1 << 4), partials, counter, out);
 }
 
+// Per-sample squared norms: one block per sample, a fixed per-thread stride and a fixed shuffle
+// tree, so the sums do not depend on scheduling.  out[2 s] = sum |a - b|^2, out[2 s + 1] = sum |b|^2.
+__global__ void __launch_bounds__(kDiagNT) pair_norms_kernel(const float2 *__restrict__ a,
+                                                             const float2 *__restrict__ b, size_t n, double *out)
+{
+    __shared__ double sh[2 * (kDiagNT / 32)];
+    const size_t base = (size_t)blockIdx.x * n;
+    double acc[2] = {0.0, 0.0};
+    for (size_t i = threadIdx.x; i < n; i += kDiagNT) {
+        const float2 x = a[base + i], y = b[base + i];
+        const double dr = (double)x.x - y.x, di = (double)x.y - y.y;
+        acc[0] += dr * dr + di * di;
+        acc[1] += (double)y.x * y.x + (double)y.y * y.y;
+    }
+    block_reduce<2, kDiagNT>(acc, 0, sh);
+    if (threadIdx.x == 0) {
+        out[2 * (size_t)blockIdx.x] = acc[0];
+        out[2 * (size_t)blockIdx.x + 1] = acc[1];
+    }
+}
+
+cudaError_t launch_pair_norms(const float2 *a, const float2 *b, size_t n, int samples, double *out, cudaStream_t st)
+{
+    pair_norms_kernel<<<samples, kDiagNT, 0, st>>>(a, b, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_grid_diag(const float2 *psi, const float *phi, long long *dep, float dep_scale, float kappa,
                              double dv, size_t ncells, double *partials, unsigned int *counter, double *out,
                              cudaStream_t st)

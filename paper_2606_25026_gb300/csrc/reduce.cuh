@@ -44,18 +44,16 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], int maxmask, double
     }
 }
 
-// All blocks of the launch must call this exactly once.  partials holds
-// nblocks * K doubles; counter starts (and ends) at 0.  With out_scaled, the
-// results times scale are written there as well.
+// The reduction over nblocks work units (tiles) numbered bid = 0 .. nblocks - 1: every unit calls
+// this exactly once, from whichever block runs it.  partials holds nblocks * K doubles; counter
+// starts (and ends) at 0.  With out_scaled, the results times scale are written there as well.
 template <int K, int NT>
-__device__ __forceinline__ void grid_reduce(double (&v)[K], int maxmask, double *partials,
-                                            unsigned int *counter, double *out, double *out_scaled = nullptr,
-                                            double scale = 1.0)
+__device__ __forceinline__ void tile_reduce(double (&v)[K], int maxmask, double *partials, unsigned int *counter,
+                                            double *out, double *out_scaled, double scale, unsigned int bid,
+                                            unsigned int nblocks)
 {
     __shared__ double sh[K * (NT / 32)];
     __shared__ int last;
-    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
-    const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     block_reduce<K, NT>(v, maxmask, sh);
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -87,6 +85,17 @@ __device__ __forceinline__ void grid_reduce(double (&v)[K], int maxmask, double 
         }
         *counter = 0u;
     }
+}
+
+// All blocks of the launch must call this exactly once (one unit per block).
+template <int K, int NT>
+__device__ __forceinline__ void grid_reduce(double (&v)[K], int maxmask, double *partials,
+                                            unsigned int *counter, double *out, double *out_scaled = nullptr,
+                                            double scale = 1.0)
+{
+    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    tile_reduce<K, NT>(v, maxmask, partials, counter, out, out_scaled, scale, bid, nblocks);
 }
 
 }  // namespace spe

@@ -79,13 +79,15 @@ struct PoissonOp {
     }
 };
 
-template <int N, int TW, bool TC = false, int PL = 0>
-__global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams p, const __grid_constant__ CUtensorMap tm)
+// The body works on column tile cx of batch b with NT threads and SCfg<N, TW, TC, PL>::smem bytes of
+// shared memory at smem_dyn (tm: the pass's tensor map when p.tma is set); the kernel below runs one
+// tile per block, a persistent kernel any tile from any block.
+template <int N, int TW, int NT, bool TC = false, int PL = 0>
+__device__ __forceinline__ void spass_body(const SParams &p, const CUtensorMap *tm, int cx, int b,
+                                           unsigned char *smem_dyn)
 {
-    constexpr int T = SCfg<N, TW, TC, PL>::T, TP = SCfg<N, TW, TC, PL>::TP, NT = SCfg<N, TW, TC, PL>::NT,
-                  HT = T / 2;
+    constexpr int T = SCfg<N, TW, TC, PL>::T, TP = SCfg<N, TW, TC, PL>::TP, HT = T / 2;
     constexpr int BR = tma_box_rows(N), NB = N / BR;
-    extern __shared__ __align__(128) unsigned char smem_dyn[];
     unsigned char *smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
     TcSmem *tcs = nullptr;
     if constexpr (TC) {
@@ -96,8 +98,7 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams 
     __shared__ float4 colfac[T];
     __shared__ float colk2[T];
     __shared__ __align__(8) unsigned long long tma_bar;
-    const int c0 = blockIdx.x * T;
-    const int b = blockIdx.y;
+    const int c0 = cx * T;
     const int tid = threadIdx.x;
     const int flags = p.flags;
     float2 *base = p.data + (size_t)b * p.bstride + c0;
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams 
         if (tid == 0) {
             mbar_expect_tx(&tma_bar, (uint32_t)(N * T * sizeof(float2)));
 #pragma unroll
-            for (int k = 0; k < NB; ++k) tma_load_3d(tile + k * BR * TP, &tm, 2 * c0, k * BR, b, &tma_bar);
+            for (int k = 0; k < NB; ++k) tma_load_3d(tile + k * BR * TP, tm, 2 * c0, k * BR, b, &tma_bar);
         }
         if (!mbar_wait(&tma_bar, 0) && (tid & 31) == 0) atomicOr(p.status, kTcStatusTimeout);
     } else {
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams 
         __syncthreads();
         if (tid == 0) {
 #pragma unroll
-            for (int k = 0; k < NB; ++k) tma_store_3d(&tm, 2 * c0, k * BR, b, tile + k * BR * TP);
+            for (int k = 0; k < NB; ++k) tma_store_3d(tm, 2 * c0, k * BR, b, tile + k * BR * TP);
             tma_store_commit_wait_read();
         }
     } else {
@@ -186,6 +187,13 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams 
         }
     }
     if constexpr (TC) tc_teardown(*tcs);
+}
+
+template <int N, int TW, bool TC = false, int PL = 0>
+__global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams p, const __grid_constant__ CUtensorMap tm)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    spass_body<N, TW, SCfg<N, TW, TC, PL>::NT, TC, PL>(p, &tm, blockIdx.x, blockIdx.y, smem_dyn);
 }
 
 // One forward or inverse transform (S_FWD or S_INV alone) with FP32 stages, its first stage

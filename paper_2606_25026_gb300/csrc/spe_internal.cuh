@@ -133,6 +133,38 @@ struct SortParams {
     float Lx, Ly, Lz, inv_dx, inv_dy, inv_dz;
 };
 
+// ---------------------------------------------------------------- batch: one persistent launch per step
+// (batch_persist.cu).  A member's passes with their parameters, and the launch's work lists.
+
+constexpr int kBatchThreads = 256;   // threads per CTA of the persistent kernel
+constexpr int kBatchTile = 16;       // strided-pass tile width in it
+constexpr int kBatchPhases = 8;
+
+struct BatchMember {
+    XParams xk, xd;                    // x kick pass, x density pass
+    SParams yf, zd, yi;                // psi: forward y, z drift, inverse y
+    SParams rf, rp, ri;                // half spectrum: forward y, z Poisson, inverse y
+    PParams pp;                        // stars (n = 0: none)
+    int n;                             // axis length (members are cubes)
+    int xtiles;                        // x-pass tiles (16 rows each)
+    int cols_psi, cols_rho;            // strided column tiles of psi and of the half spectrum
+    int pblocks;                       // star blocks (256 stars each)
+};
+
+struct BatchLaunch {
+    const BatchMember *m;
+    int count;
+    const int *offs;                   // kBatchPhases rows of count + 1 prefix sums: items per phase
+    unsigned int *bar;                 // grid-barrier counter, 0 at launch
+    int *status;                       // bit 1 set when a barrier wait gave up
+    long long wait_limit;              // polls of a barrier before it gives up
+};
+
+bool batch_persist_n_ok(int n);
+size_t batch_persist_smem();
+cudaError_t batch_persist_setup(int *blocks_out);   // grid size of a co-resident launch
+cudaError_t launch_batch_persist(const BatchLaunch &L, int blocks, cudaStream_t st);
+
 // ---------------------------------------------------------------- launchers
 // Each returns cudaGetLastError() after the launch.  blocks_out (if given)
 // receives the grid size, for the reductions' partial counts.
@@ -172,6 +204,9 @@ cudaError_t launch_particle_ke(const float *vx, const float *vy, const float *vz
 // dens[i] = |psi_i|^2 + dep_i * dep_scale; clears dep if given.
 cudaError_t launch_density(const float2 *psi, long long *dep, float dep_scale, float *dens, size_t ncells,
                            cudaStream_t st);
+
+// out[2 s] = sum |a - b|^2, out[2 s + 1] = sum |b|^2 over sample s of n complex values (FP64).
+cudaError_t launch_pair_norms(const float2 *a, const float2 *b, size_t n, int samples, double *out, cudaStream_t st);
 
 // Maximum number of partial-sum slots any reduction uses.
 constexpr int kMaxPartials = 1 << 17;

@@ -182,18 +182,20 @@ template <int N> constexpr bool xfused_ok() { return N >= 32 && Length<typename 
 
 // ---------------------------------------------------------------- kick pass
 // flags X_HAS_PHI | X_KICK | X_FFT, plus X_WRITE_PHI when WPHI (stars interpolate the real Phi).
-template <int N, bool WPHI>
-__global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, false>::value) xkick_fused_kernel(XParams p)
+// The body works on tile `tile` (rows 16 tile .. 16 tile + 15) with NT threads and XCfg<N>::smem
+// bytes of shared memory at smem_raw; the kernel below runs one tile per block, a persistent kernel
+// any tile from any block.
+template <int N, int NT, bool WPHI>
+__device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, unsigned char *smem_raw)
 {
     using C = XCfg<N>;
-    constexpr int T = C::T, TP = C::TP, NT = C::NT, H = N / 2, M = T / 2, HP = M, SP = H + 1;
+    constexpr int T = C::T, TP = C::TP, H = N / 2, M = T / 2, HP = M, SP = H + 1;
     using PP = typename Plan<N>::type;      // Phi, inverse: R_1 .. R_m
     using PS = typename Reverse<PP>::type;  // psi, forward: R_m .. R_1
     constexpr int R1 = SplitFirst<PP>::first, RL = SplitLast<PP>::last;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
-    float2 *aux = tile + N * TP;   // staged half-spectrum rows [t * SP + k], then packed lines [n * HP + m]
-    const int row0 = blockIdx.x * T, tid = threadIdx.x;
+    float2 *tile_s = reinterpret_cast<float2 *>(smem_raw);
+    float2 *aux = tile_s + N * TP;   // staged half-spectrum rows [t * SP + k], then packed lines [n * HP + m]
+    const int row0 = tile * T, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
 
     // half-spectrum rows of Phi first, then psi, all in flight at once
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, false>::value) xki
         }
     }
     cp_async_commit();
-    xf_rows_in<N, T, TP, NT>(tile, p.psi, row0, p.rows);
+    xf_rows_in<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
     cp_async_commit();
     cp_async_wait_group<1>();
     __syncthreads();
@@ -287,14 +289,14 @@ __global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, false>::value) xki
                     for (int h = 0; h < 2; ++h) {
                         const int t = 2 * m + h;
                         const float phi = h ? f[r].y : f[r].x;
-                        float2 v = tile[n * TP + t];
+                        float2 v = tile_s[n * TP + t];
                         // v exp(-i ph) = v + v (cos ph - 1 - i sin ph), cos ph - 1 = -2 sin^2(ph / 2)
                         const float a2 = v.x * v.x + v.y * v.y;
                         float sh, ch;
                         half_angle_sincos(0.5f * ((phi + kap * a2) * ks), sh, ch);
                         const float cm1 = -2.f * sh * sh, sn = 2.f * sh * ch;
                         v = make_float2(fmaf(v.x, cm1, fmaf(v.y, sn, v.x)), fmaf(v.y, cm1, fmaf(-v.x, sn, v.y)));
-                        tile[n * TP + t] = v;
+                        tile_s[n * TP + t] = v;
                         if (WPHI && row0 + t < p.rows) p.phi_out[(size_t)(row0 + t) * N + n] = phi;
                     }
                 }
@@ -303,30 +305,44 @@ __global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, false>::value) xki
         __syncthreads();
     }
 
-    // forward transform of psi with the reversed plan, its last stage storing the rows
-    fft_stages<N, T, TP, NT, -1, 1>(tile, p.tw, typename SplitLast<PS>::init{});
-    xf_last_stage_to_rows<N, T, TP, NT, -1, SplitLast<PS>::last>(tile, p.tw, p.psi, row0, p.rows);
+    // forward transform of psi with the reversed plan; a last stage of radix 8 or less stores the rows
+    // itself (with lanes over the butterflies each lane loads its own twiddles, which costs more than
+    // the copy-out it saves once the stage has 15 of them)
+    if constexpr (SplitLast<PS>::last <= 8) {
+        fft_stages<N, T, TP, NT, -1, 1>(tile_s, p.tw, typename SplitLast<PS>::init{});
+        xf_last_stage_to_rows<N, T, TP, NT, -1, SplitLast<PS>::last>(tile_s, p.tw, p.psi, row0, p.rows);
+    } else {
+        xf_stages<N, T, TP, NT, -1, 1>(tile_s, p.tw, PS{});
+        xf_rows_out<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
+    }
+}
+
+template <int N, bool WPHI>
+__global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, false>::value) xkick_fused_kernel(XParams p)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    xkick_fused_body<N, XCfg<N>::NT, WPHI>(p, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------- density pass
 // flags X_IFFT | X_MASS | X_R2C, plus X_DEP when DEP (the stars' fixed-point deposit).
-template <int N, bool DEP>
-__global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, true>::value) xdens_fused_kernel(XParams p)
+// The body works on tile `tile` of the ntiles tiles of the pass (the mass reduction counts them).
+template <int N, int NT, bool DEP>
+__device__ __forceinline__ void xdens_fused_body(const XParams &p, int tile, int ntiles, unsigned char *smem_raw)
 {
     using C = XCfg<N>;
-    constexpr int T = C::T, TP = C::TP, NT = C::NT, H = N / 2, M = T / 2, HP = M, DP = N + 2;
+    constexpr int T = C::T, TP = C::TP, H = N / 2, M = T / 2, HP = M, DP = N + 2;
     using PI = typename Plan<N>::type;      // psi, inverse: R_1 .. R_m
     using PR = typename Reverse<PI>::type;  // packed rho, forward: R_m .. R_1
     constexpr int RL = SplitLast<PI>::last;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     static_assert((size_t)T * DP * sizeof(float) <= C::aux_bytes && (size_t)N * HP * sizeof(float2) <= C::aux_bytes,
                   "aux area too small");
-    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
-    float2 *aux = tile + N * TP;                  // packed rho lines [n * HP + m]
+    float2 *tile_s = reinterpret_cast<float2 *>(smem_raw);
+    float2 *aux = tile_s + N * TP;                // packed rho lines [n * HP + m]
     float *auxf = reinterpret_cast<float *>(aux);  // before them: deposit rows [t * DP + n]
-    const int row0 = blockIdx.x * T, tid = threadIdx.x;
+    const int row0 = tile * T, tid = threadIdx.x;
 
-    xf_rows_in<N, T, TP, NT>(tile, p.psi, row0, p.rows);
+    xf_rows_in<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
     cp_async_commit();
     unsigned live_rows = 0;   // bit t: row row0 + t holds deposit (marked by the star kernel)
     if (DEP) {
@@ -354,7 +370,7 @@ __global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, true>::value) xden
     }
 
     // inverse stages of psi but the last
-    fft_stages<N, T, TP, NT, +1, 1>(tile, p.tw, typename SplitLast<PI>::init{});
+    fft_stages<N, T, TP, NT, +1, 1>(tile_s, p.tw, typename SplitLast<PI>::init{});
 
     // last inverse stage of psi (in place per butterfly) for the rows 2m, 2m + 1, rho at its points,
     // and the first forward stage of the packed line Z_m = rho_2m + i rho_2m+1
@@ -372,7 +388,7 @@ __global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, true>::value) xden
                     const int t = 2 * m + h;
                     float2 v[RL];
 #pragma unroll
-                    for (int r = 0; r < RL; ++r) v[r] = tile[(j + r * B) * TP + t];
+                    for (int r = 0; r < RL; ++r) v[r] = tile_s[(j + r * B) * TP + t];
                     if (B > 1) {
 #pragma unroll
                         for (int r = 1; r < RL; ++r) {
@@ -383,7 +399,7 @@ __global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, true>::value) xden
                     Dft<RL, +1>::run(v);
 #pragma unroll
                     for (int r = 0; r < RL; ++r) {
-                        tile[(j + r * B) * TP + t] = v[r];
+                        tile_s[(j + r * B) * TP + t] = v[r];
                         float rho = v[r].x * v[r].x + v[r].y * v[r].y;
                         msum += rho;
                         if (DEP) rho += auxf[t * DP + j + r * B];
@@ -405,7 +421,7 @@ __global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, true>::value) xden
         }
         __syncthreads();
     }
-    xf_rows_out<N, T, TP, NT>(tile, p.psi, row0, p.rows);
+    xf_rows_out<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
     // the remaining forward stages of the packed lines
     xf_stages<N, M, HP, NT, -1, RL>(aux, p.tw, typename SplitFirst<PR>::rest{});
     // separate the two real rows: A_k = (Z_k + conj Z_{N-k}) / 2, B_k = (Z_k - conj Z_{N-k}) / (2i)
@@ -421,7 +437,15 @@ __global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, true>::value) xden
         if (ra + 1 < p.rows) p.phik[(size_t)(ra + 1) * p.P + k] = Bk;
     }
     double v[1] = {(double)msum};
-    grid_reduce<1, NT>(v, 0, p.partials, p.counter, p.result, p.result + 1, p.mass_scale);
+    tile_reduce<1, NT>(v, 0, p.partials, p.counter, p.result, p.result + 1, p.mass_scale, (unsigned)tile,
+                       (unsigned)ntiles);
+}
+
+template <int N, bool DEP>
+__global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, true>::value) xdens_fused_kernel(XParams p)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    xdens_fused_body<N, XCfg<N>::NT, DEP>(p, blockIdx.x, gridDim.x, smem_raw);
 }
 
 }  // namespace spe

@@ -37,6 +37,7 @@ EXPORTED = (
     "spe_set_static_potential", "spe_virial", "spe_autotune", "spe_set_schedule", "spe_get_schedule",
     "spe_batch_create", "spe_batch_grid",
     "spe_batch_autotune", "spe_batch_step", "spe_batch_settle", "spe_batch_launch_count", "spe_batch_destroy",
+    "spe_batch_set_persistent", "spe_batch_get_persistent", "spe_pair_norms",
     # include/spe_fno.h
     "spe_fno_param_count", "spe_fno_create", "spe_fno_destroy", "spe_fno_set_params", "spe_fno_get_params",
     "spe_fno_get_grads", "spe_fno_forward", "spe_fno_backward", "spe_fno_adam", "spe_fno_sync",
@@ -140,6 +141,9 @@ def load_library(path: str = LIB_PATH):
         "spe_batch_step": (I, [P, I, ctypes.POINTER(D)]),
         "spe_batch_settle": (I, [P]),
         "spe_batch_launch_count": (I, [P, ctypes.POINTER(ctypes.c_ulonglong)]),
+        "spe_batch_set_persistent": (I, [P, I, ctypes.c_longlong]),
+        "spe_pair_norms": (I, [P, P, S, I, P, P]),
+        "spe_batch_get_persistent": (I, [P, ctypes.POINTER(I)]),
         "spe_batch_destroy": (I, [P]),
         "spe_fno_param_count": (I, [ctypes.POINTER(spe_fno_config), ctypes.POINTER(S)]),
         "spe_fno_create": (I, [ctypes.POINTER(spe_fno_config), ctypes.POINTER(P)]),
@@ -404,6 +408,25 @@ def create_grid(*args, **kwargs) -> Grid:
     return Grid(*args, **kwargs)
 
 
+def pair_norms(a, b, stream=None):
+    """Per-sample (sum |a - b|^2, sum |b|^2) of two (S, ...) complex64 CUDA tensors, through
+    spe_pair_norms (FP64, fixed order); returns two numpy arrays of length S."""
+    import torch
+    lib = load_library()
+    for t in (a, b):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()):
+            raise TypeError("a and b must be contiguous complex64 CUDA tensors")
+    if a.shape != b.shape:
+        raise ValueError("a and b differ in shape")
+    S = a.shape[0]
+    out = torch.empty((S, 2), dtype=torch.float64, device=a.device)
+    st = (stream or torch.cuda.current_stream(a.device)).cuda_stream
+    _check(lib.spe_pair_norms(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), a[0].numel(), S,
+                              ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st)), "spe_pair_norms")
+    h = out.cpu().numpy()
+    return h[:, 0].copy(), h[:, 1].copy()
+
+
 def field_energy_noalloc(psi, cell_volume, kappa=0.0, stream=None):
     """(mass, interaction) of a complex64 CUDA tensor through spe_field_energy_noalloc: the
     library allocates nothing for it (its scratch is a fixed array inside libspe)."""
@@ -476,6 +499,23 @@ class Batch:
         out = ctypes.c_ulonglong()
         _check(self._lib.spe_batch_launch_count(self._h, ctypes.byref(out)), "spe_batch_launch_count")
         return out.value
+
+    def set_persistent(self, on=True, wait_limit=-1):
+        """One persistent launch per step (on) or the graph of per-member branches (off);
+        wait_limit: polls of a grid-wide barrier before it gives up (-1 = default)."""
+        _check(self._lib.spe_batch_set_persistent(self._h, int(bool(on)), int(wait_limit)),
+               "spe_batch_set_persistent")
+
+    def persistent(self) -> bool:
+        """True when the next step runs as one persistent launch."""
+        out = ctypes.c_int()
+        _check(self._lib.spe_batch_get_persistent(self._h, ctypes.byref(out)), "spe_batch_get_persistent")
+        return bool(out.value)
+
+    def step_status(self, nsteps, dts) -> int:
+        """spe_batch_step's status code, without raising."""
+        d = (ctypes.c_double * len(self.members))(*[float(v) for v in dts])
+        return int(self._lib.spe_batch_step(self._h, int(nsteps), d))
 
     def destroy(self):
         if getattr(self, "_h", None):

@@ -82,17 +82,17 @@ def generate_pairs(ics, n, K, dt, pairs_per_ic=1, warmup_steps=0, G=1.0):
 
 
 def correction_scale(pairs: PairSet) -> float:
-    """rms |psi_{t+K dt} - psi_b| over the set: the output scale sigma."""
-    import torch
-    d = (pairs.target - pairs.psi_b).abs().pow(2).mean(dim=(1, 2, 3))
-    return float(torch.sqrt(d.mean()))
+    """rms |psi_{t+K dt} - psi_b| over the set: the output scale sigma (sums by the library's
+    FP64 reduction kernel)."""
+    num, _ = spe.pair_norms(pairs.target, pairs.psi_b)
+    return float(np.sqrt(num.sum() / (len(num) * pairs.psi[0].numel())))
 
 
 def rel_errors(a, b):
-    """Per-sample ||a - b|| / ||b|| of (S, n, n, n) tensors."""
-    num = (a - b).abs().pow(2).sum(dim=(1, 2, 3))
-    den = b.abs().pow(2).sum(dim=(1, 2, 3))
-    return (num / den).sqrt().cpu().numpy()
+    """Per-sample ||a - b|| / ||b|| of (S, n, n, n) tensors (sums by the library's FP64 reduction
+    kernel)."""
+    num, den = spe.pair_norms(a.contiguous(), b.contiguous())
+    return np.sqrt(num / den)
 
 
 def train(net: spe.Fno, pairs: PairSet, epochs=10, batch=8, lr=1e-3, lr_min=1e-5, seed=0, log=None):

@@ -131,3 +131,20 @@ def test_graph_replayed_advance_matches_direct(spe):
     g.set_ic(psi)
     s.advance(g, K, dt)
     assert s.launch_count() >= 40
+
+
+def test_pair_norms_match_host_fp64(spe):
+    """spe_pair_norms (the surrogate's output scale and relative errors) against FP64 sums on the
+    host, for an odd sample length; a == b gives zero differences."""
+    import torch
+    rng = np.random.default_rng(31)
+    S, n = 5, 3 * 17 * 19
+    a = (rng.standard_normal((S, n)) + 1j * rng.standard_normal((S, n))).astype(np.complex64)
+    b = (rng.standard_normal((S, n)) + 1j * rng.standard_normal((S, n))).astype(np.complex64)
+    da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    num, den = spe.pair_norms(da, db)
+    ref_num = (np.abs(a.astype(np.complex128) - b.astype(np.complex128)) ** 2).sum(1)
+    ref_den = (np.abs(b.astype(np.complex128)) ** 2).sum(1)
+    assert np.allclose(num, ref_num, rtol=1e-12) and np.allclose(den, ref_den, rtol=1e-12)
+    z, _ = spe.pair_norms(db, db)
+    assert np.all(z == 0.0)
