@@ -265,15 +265,15 @@ SPE_API int spe_get_schedule(spe_grid *g, int *tiles, int *plans);
  * Members allocate their own workspaces; use spe_batch_grid to reach a member
  * for spe_set_ic, spe_add_particles, spe_get_psi, spe_energy, ... (not
  * spe_destroy).
- * Two ways to run a step.  Persistent (the default when every member is a
+ * Two ways to run a step.  By default each member runs its kernels on its own
+ * stream and the members' full steps are the parallel branches of one CUDA
+ * graph.  With spe_batch_set_persistent(b, 1, ...), when every member is a
  * gravitating cube of 64, 96, 128 or 192 points without a static potential,
- * an absorbing layer, tensor-core stages or SPE_PROFILE): one cooperative
+ * an absorbing layer, tensor-core stages or SPE_PROFILE, one cooperative
  * kernel launch per step walks eight phases (the passes of the step), each a
  * work list of every member's tiles, with a grid-wide barrier between phases;
- * full steps replay that launch as a CUDA graph.  Otherwise: each member runs
- * its kernels on its own stream and the members' full steps are the parallel
- * branches of one CUDA graph.  Both give every member bitwise the result of
- * the same grid stepped alone. */
+ * full steps replay that launch as a CUDA graph.  Both give every member
+ * bitwise the result of the same grid stepped alone. */
 typedef struct spe_batch spe_batch;
 SPE_API int spe_batch_create(const spe_config *cfgs, int count, spe_batch **out);
 SPE_API int spe_batch_grid(spe_batch *b, int index, spe_grid **out);

@@ -1784,7 +1784,7 @@ int spe_batch_create(const spe_config *cfgs, int count, spe_batch **out)
     *out = nullptr;
     spe_batch *b = new (std::nothrow) spe_batch();
     if (!b) return SPE_ENOMEM;
-    b->persist = true;
+    b->persist = false;   // the graph of per-member branches measured faster (the persistent form is opt-in)
     b->wait_limit = kBatchWaitLimit;
     b->st = (cudaStream_t)cfgs[0].cuda_stream;
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
