@@ -211,22 +211,32 @@ __device__ __forceinline__ void particles_body(const PParams &p, int block, unsi
         }
         if (live) {
             const float mq = p.m[i] * p.inv_quantum;
+            if (tiled) {
+                // lane l visits its corners starting at corner l mod 8: where a warp's stars share a
+                // cell (a dense cluster), the lanes of one atomic spread over the eight corner nodes
+                // instead of all meeting on one.  The quantised values are the ones of the loop below.
+                const int rot = threadIdx.x & 7;
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int k = c ? cz.i1 : cz.i0;
-                const float wz = c ? cz.w1 : cz.w0;
+                for (int kk = 0; kk < 8; ++kk) {
+                    const int cc = (kk + rot) & 7;
+                    const int a = cc & 1, b2 = (cc >> 1) & 1, c = cc >> 2;
+                    const float wyz = (b2 ? cy.w1 : cy.w0) * (c ? cz.w1 : cz.w0);
+                    const long long q = llrintf(mq * (a ? cx.w1 : cx.w0) * wyz);
+                    if (q)
+                        atomicAdd(&sdep[((cz.i0 + c - oz) * ey + (cy.i0 + b2 - oy)) * ex + (cx.i0 + a - ox)],
+                                  (unsigned long long)q);
+                }
+            } else {
 #pragma unroll
-                for (int b2 = 0; b2 < 2; ++b2) {
-                    const int j = b2 ? cy.i1 : cy.i0;
-                    const float wyz = (b2 ? cy.w1 : cy.w0) * wz;
-                    const long long q0 = llrintf(mq * cx.w0 * wyz);
-                    const long long q1 = llrintf(mq * cx.w1 * wyz);
-                    if (tiled) {
-                        unsigned long long *srow =
-                            sdep + ((cz.i0 + c - oz) * ey + (cy.i0 + b2 - oy)) * ex + (cx.i0 - ox);
-                        if (q0) atomicAdd(&srow[0], (unsigned long long)q0);
-                        if (q1) atomicAdd(&srow[1], (unsigned long long)q1);
-                    } else {
+                for (int c = 0; c < 2; ++c) {
+                    const int k = c ? cz.i1 : cz.i0;
+                    const float wz = c ? cz.w1 : cz.w0;
+#pragma unroll
+                    for (int b2 = 0; b2 < 2; ++b2) {
+                        const int j = b2 ? cy.i1 : cy.i0;
+                        const float wyz = (b2 ? cy.w1 : cy.w0) * wz;
+                        const long long q0 = llrintf(mq * cx.w0 * wyz);
+                        const long long q1 = llrintf(mq * cx.w1 * wyz);
                         unsigned long long *row =
                             reinterpret_cast<unsigned long long *>(p.dep) + ((size_t)k * ny + j) * nx;
                         if (q0) atomicAdd(&row[cx.i0], (unsigned long long)q0);

@@ -82,7 +82,7 @@ struct PoissonOp {
 // The body works on column tile cx of batch b with NT threads and SCfg<N, TW, TC, PL>::smem bytes of
 // shared memory at smem_dyn (tm: the pass's tensor map when p.tma is set); the kernel below runs one
 // tile per block, a persistent kernel any tile from any block.
-template <int N, int TW, int NT, bool TC = false, int PL = 0>
+template <int N, int TW, int NT, bool TC = false, int PL = 0, bool SINGLE = false>
 __device__ __forceinline__ void spass_body(const SParams &p, const CUtensorMap *tm, int cx, int b,
                                            unsigned char *smem_dyn)
 {
@@ -133,14 +133,14 @@ __device__ __forceinline__ void spass_body(const SParams &p, const CUtensorMap *
         cp_async_wait_all();
     }
     __syncthreads();
-    if ((flags & (S_FWD | S_INV)) == (S_FWD | S_INV) && (flags & (S_DRIFT | S_POISSON))) {
+    if (!SINGLE && (flags & (S_FWD | S_INV)) == (S_FWD | S_INV) && (flags & (S_DRIFT | S_POISSON))) {
         if constexpr (TC) {
             if (flags & S_DRIFT)
                 tile_fft_fwd_op_inv_tc<N, T, TP, NT>(tile, p.tw, DriftOp{colfac, p.ez}, *tcs, p.status);
             else
                 tile_fft_fwd_op_inv_tc<N, T, TP, NT>(tile, p.tw, PoissonOp{colk2, p.linek2, p.poisson * p.norm},
                                                      *tcs, p.status);
-        } else {
+        } else if constexpr (!SINGLE) {
             if (flags & S_DRIFT) tile_fft_fwd_op_inv<N, T, TP, NT, DriftOp, PL>(tile, p.tw, DriftOp{colfac, p.ez});
             else
                 tile_fft_fwd_op_inv<N, T, TP, NT, PoissonOp, PL>(tile, p.tw,
@@ -194,6 +194,22 @@ __global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams 
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     spass_body<N, TW, SCfg<N, TW, TC, PL>::NT, TC, PL>(p, &tm, blockIdx.x, blockIdx.y, smem_dyn);
+}
+
+// One forward or inverse transform alone, where spass_line_kernel does not apply: the same body
+// without the fused multiply, so that its register budget is its own.  At 512 points with the
+// [16, 32] plan it holds three CTAs of 256 threads (16-column tiles) or six of 128 (8-column tiles)
+// per SM at about 80 registers, instead of two or three at 106-133.
+template <int N, int TW, int PL> struct SingleMinBlocks {
+    static constexpr int value = (N == 512 && PL == 2) ? (TW == 16 ? 3 : (TW == 8 ? 6 : 1)) : 1;
+};
+
+template <int N, int TW, int PL>
+__global__ void __launch_bounds__(SCfg<N, TW, false, PL>::NT, SingleMinBlocks<N, TW, PL>::value)
+    spass_single_kernel(SParams p, const __grid_constant__ CUtensorMap tm)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    spass_body<N, TW, SCfg<N, TW, false, PL>::NT, false, PL, true>(p, &tm, blockIdx.x, blockIdx.y, smem_dyn);
 }
 
 // One forward or inverse transform (S_FWD or S_INV alone) with FP32 stages, its first stage
@@ -253,6 +269,12 @@ static cudaError_t launch_s_nt(const SParams &p, cudaStream_t st, int *blocks_ou
         if (!encode_spass_tmap(p, N, TW, &tm)) q.tma = 0;
     }
     if (!q.tma) memset(&tm, 0, sizeof(tm));
+    if constexpr (!TC && SingleMinBlocks<N, TW, PL>::value > 1) {
+        if (p.flags == S_FWD || p.flags == S_INV) {
+            spass_single_kernel<N, TW, PL><<<grid, SCfg<N, TW, false, PL>::NT, SCfg<N, TW, false, PL>::smem, st>>>(q, tm);
+            return cudaGetLastError();
+        }
+    }
     spass_kernel<N, TW, TC, PL><<<grid, SCfg<N, TW, TC, PL>::NT, SCfg<N, TW, TC, PL>::smem, st>>>(q, tm);
     return cudaGetLastError();
 }
@@ -265,6 +287,11 @@ static cudaError_t attr_s(int smem)
     if constexpr (LineCfg<N, TW, PL>::usable) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(spass_line_kernel<N, TW, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem);
+    }
+    if constexpr (SingleMinBlocks<N, TW, PL>::value > 1) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(spass_single_kernel<N, TW, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem);
     }
     return e;

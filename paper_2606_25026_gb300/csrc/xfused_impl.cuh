@@ -178,6 +178,16 @@ template <int N, bool DENS> struct XFMinBlocks {
     static constexpr int value = (DENS && N == 256 && fit > 3) ? 3 : (fit < 1 ? 1 : fit);
 };
 
+// v exp(-i (phi + kappa |v|^2) ks) = v + v (cos th - 1 - i sin th), cos th - 1 = -2 sin^2(th / 2)
+__device__ __forceinline__ float2 xf_kick(float2 v, float phi, float kap, float ks)
+{
+    const float a2 = v.x * v.x + v.y * v.y;
+    float sh, ch;
+    half_angle_sincos(0.5f * ((phi + kap * a2) * ks), sh, ch);
+    const float cm1 = -2.f * sh * sh, sn = 2.f * sh * ch;
+    return make_float2(fmaf(v.x, cm1, fmaf(v.y, sn, v.x)), fmaf(v.y, cm1, fmaf(-v.x, sn, v.y)));
+}
+
 template <int N> constexpr bool xfused_ok() { return N >= 32 && Length<typename Plan<N>::type>::value >= 2; }
 
 // ---------------------------------------------------------------- kick pass
@@ -261,59 +271,132 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
     // the inverse stages between the first and the last
     fft_stages<N, M, HP, NT, +1, R1>(aux, p.tw, typename MiddleOf<PP>::type{});
 
-    // last inverse stage of Phi (in place per butterfly) and the kick of psi at its points
-    {
+    if constexpr (RL <= 8) {
+        // last inverse stage of Phi, the kick of both psi rows at its points and psi's first forward
+        // stage in registers: the reversed plan starts with radix RL, so that stage's butterfly j reads
+        // the points j + r N/RL the Phi butterfly j produced.  Loads, one barrier, then the first
+        // stage's outputs (which land on points other threads read).
         constexpr int B = N / RL, TOTAL = B * M, PER = (TOTAL + NT - 1) / NT;
         const float ks = p.kick_scale, kap = p.kappa;
+        float2 f[PER][RL], va[PER][RL], vb[PER][RL];
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int idx = tid + q * NT;
             if (TOTAL % NT == 0 || idx < TOTAL) {
                 const int m = idx % M, j = idx / M;
-                float2 f[RL];
-#pragma unroll
-                for (int r = 0; r < RL; ++r) f[r] = aux[(j + r * B) * HP + m];
-                if (B > 1) {
-#pragma unroll
-                    for (int r = 1; r < RL; ++r) {
-                        const float4 w = __ldg(&p.tw[j * r]);
-                        f[r] = cmul_comp(f[r], make_float2(w.x, -w.y), make_float2(w.z, -w.w));
-                    }
-                }
-                Dft<RL, +1>::run(f);
-                // f[r] = Phi(row 2m, point j + r B) + i Phi(row 2m + 1, point j + r B)
 #pragma unroll
                 for (int r = 0; r < RL; ++r) {
                     const int n = j + r * B;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int t = 2 * m + h;
-                        const float phi = h ? f[r].y : f[r].x;
-                        float2 v = tile_s[n * TP + t];
-                        // v exp(-i ph) = v + v (cos ph - 1 - i sin ph), cos ph - 1 = -2 sin^2(ph / 2)
-                        const float a2 = v.x * v.x + v.y * v.y;
-                        float sh, ch;
-                        half_angle_sincos(0.5f * ((phi + kap * a2) * ks), sh, ch);
-                        const float cm1 = -2.f * sh * sh, sn = 2.f * sh * ch;
-                        v = make_float2(fmaf(v.x, cm1, fmaf(v.y, sn, v.x)), fmaf(v.y, cm1, fmaf(-v.x, sn, v.y)));
-                        tile_s[n * TP + t] = v;
-                        if (WPHI && row0 + t < p.rows) p.phi_out[(size_t)(row0 + t) * N + n] = phi;
-                    }
+                    f[q][r] = aux[n * HP + m];
+                    va[q][r] = tile_s[n * TP + 2 * m];
+                    vb[q][r] = tile_s[n * TP + 2 * m + 1];
                 }
             }
         }
         __syncthreads();
-    }
-
-    // forward transform of psi with the reversed plan; a last stage of radix 8 or less stores the rows
-    // itself (with lanes over the butterflies each lane loads its own twiddles, which costs more than
-    // the copy-out it saves once the stage has 15 of them)
-    if constexpr (SplitLast<PS>::last <= 8) {
-        fft_stages<N, T, TP, NT, -1, 1>(tile_s, p.tw, typename SplitLast<PS>::init{});
-        xf_last_stage_to_rows<N, T, TP, NT, -1, SplitLast<PS>::last>(tile_s, p.tw, p.psi, row0, p.rows);
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int idx = tid + q * NT;
+            if (TOTAL % NT == 0 || idx < TOTAL) {
+                const int m = idx % M, j = idx / M;
+                if (B > 1) {
+#pragma unroll
+                    for (int r = 1; r < RL; ++r) {
+                        const float4 w = __ldg(&p.tw[j * r]);
+                        f[q][r] = cmul_comp(f[q][r], make_float2(w.x, -w.y), make_float2(w.z, -w.w));
+                    }
+                }
+                Dft<RL, +1>::run(f[q]);
+                // f[r] = Phi(row 2m, point j + r B) + i Phi(row 2m + 1, point j + r B)
+#pragma unroll
+                for (int r = 0; r < RL; ++r) {
+                    va[q][r] = xf_kick(va[q][r], f[q][r].x, kap, ks);
+                    vb[q][r] = xf_kick(vb[q][r], f[q][r].y, kap, ks);
+                    if (WPHI) {
+                        const int n = j + r * B, ra = row0 + 2 * m;
+                        if (ra < p.rows) p.phi_out[(size_t)ra * N + n] = f[q][r].x;
+                        if (ra + 1 < p.rows) p.phi_out[(size_t)(ra + 1) * N + n] = f[q][r].y;
+                    }
+                }
+                Dft<RL, -1>::run(va[q]);
+                Dft<RL, -1>::run(vb[q]);
+                // outputs at points j RL + r; odd butterflies store their second row first, which puts
+                // a half-warp's two butterflies in opposite halves of the banks
+                const bool odd = j & 1;
+#pragma unroll
+                for (int r = 0; r < RL; ++r) {
+                    float2 *d = tile_s + (j * RL + r) * TP + 2 * m;
+                    d[odd ? 1 : 0] = odd ? vb[q][r] : va[q][r];
+                    d[odd ? 0 : 1] = odd ? va[q][r] : vb[q][r];
+                }
+            }
+        }
+        __syncthreads();
+        // the remaining forward stages of psi (from Ns = RL)
+        using Rest = typename SplitFirst<PS>::rest;
+        if constexpr (SplitLast<PS>::last <= 8) {
+            fft_stages<N, T, TP, NT, -1, RL>(tile_s, p.tw, typename SplitLast<Rest>::init{});
+            xf_last_stage_to_rows<N, T, TP, NT, -1, SplitLast<PS>::last>(tile_s, p.tw, p.psi, row0, p.rows);
+        } else {
+            xf_stages<N, T, TP, NT, -1, RL>(tile_s, p.tw, Rest{});
+            xf_rows_out<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
+        }
     } else {
-        xf_stages<N, T, TP, NT, -1, 1>(tile_s, p.tw, PS{});
-        xf_rows_out<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
+        // last inverse stage of Phi (in place per butterfly) and the kick of psi at its points
+        {
+            constexpr int B = N / RL, TOTAL = B * M, PER = (TOTAL + NT - 1) / NT;
+            const float ks = p.kick_scale, kap = p.kappa;
+    #pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int idx = tid + q * NT;
+                if (TOTAL % NT == 0 || idx < TOTAL) {
+                    const int m = idx % M, j = idx / M;
+                    float2 f[RL];
+    #pragma unroll
+                    for (int r = 0; r < RL; ++r) f[r] = aux[(j + r * B) * HP + m];
+                    if (B > 1) {
+    #pragma unroll
+                        for (int r = 1; r < RL; ++r) {
+                            const float4 w = __ldg(&p.tw[j * r]);
+                            f[r] = cmul_comp(f[r], make_float2(w.x, -w.y), make_float2(w.z, -w.w));
+                        }
+                    }
+                    Dft<RL, +1>::run(f);
+                    // f[r] = Phi(row 2m, point j + r B) + i Phi(row 2m + 1, point j + r B)
+    #pragma unroll
+                    for (int r = 0; r < RL; ++r) {
+                        const int n = j + r * B;
+    #pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int t = 2 * m + h;
+                            const float phi = h ? f[r].y : f[r].x;
+                            float2 v = tile_s[n * TP + t];
+                            // v exp(-i ph) = v + v (cos ph - 1 - i sin ph), cos ph - 1 = -2 sin^2(ph / 2)
+                            const float a2 = v.x * v.x + v.y * v.y;
+                            float sh, ch;
+                            half_angle_sincos(0.5f * ((phi + kap * a2) * ks), sh, ch);
+                            const float cm1 = -2.f * sh * sh, sn = 2.f * sh * ch;
+                            v = make_float2(fmaf(v.x, cm1, fmaf(v.y, sn, v.x)), fmaf(v.y, cm1, fmaf(-v.x, sn, v.y)));
+                            tile_s[n * TP + t] = v;
+                            if (WPHI && row0 + t < p.rows) p.phi_out[(size_t)(row0 + t) * N + n] = phi;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+
+        // forward transform of psi with the reversed plan; a last stage of radix 8 or less stores the rows
+        // itself (with lanes over the butterflies each lane loads its own twiddles, which costs more than
+        // the copy-out it saves once the stage has 15 of them)
+        if constexpr (SplitLast<PS>::last <= 8) {
+            fft_stages<N, T, TP, NT, -1, 1>(tile_s, p.tw, typename SplitLast<PS>::init{});
+            xf_last_stage_to_rows<N, T, TP, NT, -1, SplitLast<PS>::last>(tile_s, p.tw, p.psi, row0, p.rows);
+        } else {
+            xf_stages<N, T, TP, NT, -1, 1>(tile_s, p.tw, PS{});
+            xf_rows_out<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
+        }
+
     }
 }
 
