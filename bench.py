@@ -158,14 +158,23 @@ class ClockSampler:
         self.proc = None
         self.path = os.path.join("/tmp", f"spe_clocks_{os.getpid()}.csv")
 
-    def start(self):
+    def start(self, ready_s=10.0):
+        """Start sampling every 100 ms and return once the first sample is written, so that the
+        sampler is live when the timed region begins."""
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t_end = time.time() + ready_s
+        while time.time() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+        self.t0 = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -188,11 +197,12 @@ class ClockSampler:
         os.remove(self.path)
         if not rows:
             return None
+        window_ms = (time.time() - self.t0) * 1e3
         sm = sorted(r[0] for r in rows)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "interval_ms": 100, "window_ms": round(window_ms, 1)}
 
 
 def make_inputs(workload, grid=None):
