@@ -46,6 +46,7 @@ struct spe_fno {
     long long adam_t;
     float2 *Efwd, *Einv;
     uint4 *tcG, *tcF;
+    uint4 *tcFt, *tcGt;     // backward operand images
     void *act[16];
     float2 *xrow, *ym, *Ybuf, *Xbbuf, *Xsave[8];
     float *ubar, *partials;
@@ -124,11 +125,14 @@ int kmaj_host(int row, int k, int K) { return (row >> 3) * (K * 16) + (k >> 3) *
 
 // BF16 operand images of the x stages for the tensor-core row kernels:
 // G' [n][2M]: (Re Gx, -Im Gx) pairs; F' [2M][n]: rows (Re Fx), (Im Fx).
-void build_tc_images(int n, int M, std::vector<unsigned char> &g, std::vector<unsigned char> &fimg)
+void build_tc_images(int n, int M, std::vector<unsigned char> &g, std::vector<unsigned char> &fimg,
+                     std::vector<unsigned char> &ft, std::vector<unsigned char> &gt)
 {
     const int KM = 2 * M;
     g.assign((size_t)n * KM * 2, 0);
     fimg.assign((size_t)n * KM * 2, 0);
+    ft.assign((size_t)n * KM * 2, 0);
+    gt.assign((size_t)n * KM * 2, 0);
     for (int x = 0; x < n; ++x)
         for (int k = 0; k < M; ++k) {
             const double th = 2.0 * kPi * (double)((long long)k * x % n) / n;
@@ -143,6 +147,11 @@ void build_tc_images(int n, int M, std::vector<unsigned char> &g, std::vector<un
             put(g, kmaj_host(x, 2 * k + 1, KM), -gi);
             put(fimg, kmaj_host(2 * k, x, n), fr);
             put(fimg, kmaj_host(2 * k + 1, x, n), fi);
+            // backward: F'' [x][kk] (v bar = Re(Fx^H a bar)) and G'' [kk][x] (Bbar = Gx^H u bar)
+            put(ft, kmaj_host(x, 2 * k, KM), fr);
+            put(ft, kmaj_host(x, 2 * k + 1, KM), fi);
+            put(gt, kmaj_host(2 * k, x, n), gr);
+            put(gt, kmaj_host(2 * k + 1, x, n), -gi);
         }
 }
 
@@ -213,6 +222,8 @@ RowArgs base_args(spe_fno *f, int batch)
     a.status = f->status;
     a.tcG = f->tcG;
     a.tcF = f->tcF;
+    a.tcFt = f->tcFt;
+    a.tcGt = f->tcGt;
     return a;
 }
 
@@ -357,6 +368,8 @@ SPE_API int spe_fno_create(const spe_fno_config *cfg, spe_fno **out)
     ok(dalloc(f, &f->Efwd, M * n));
     ok(dalloc(f, &f->tcG, n * 2 * M * 2 / 16));
     ok(dalloc(f, &f->tcF, n * 2 * M * 2 / 16));
+    ok(dalloc(f, &f->tcFt, n * 2 * M * 2 / 16));
+    ok(dalloc(f, &f->tcGt, n * 2 * M * 2 / 16));
     ok(dalloc(f, &f->Einv, n * M));
     const int nact = f->train ? 2 * f->L : 2;
     for (int i = 0; i < nact; ++i) {
@@ -385,10 +398,12 @@ SPE_API int spe_fno_create(const spe_fno_config *cfg, spe_fno **out)
             }
         ok(cudaMemcpy(f->Efwd, Ef.data(), Ef.size() * sizeof(float2), cudaMemcpyHostToDevice));
         ok(cudaMemcpy(f->Einv, Ei.data(), Ei.size() * sizeof(float2), cudaMemcpyHostToDevice));
-        std::vector<unsigned char> gimg, fimg;
-        build_tc_images((int)n, (int)M, gimg, fimg);
+        std::vector<unsigned char> gimg, fimg, ftimg, gtimg;
+        build_tc_images((int)n, (int)M, gimg, fimg, ftimg, gtimg);
         ok(cudaMemcpy(f->tcG, gimg.data(), gimg.size(), cudaMemcpyHostToDevice));
         ok(cudaMemcpy(f->tcF, fimg.data(), fimg.size(), cudaMemcpyHostToDevice));
+        ok(cudaMemcpy(f->tcFt, ftimg.data(), ftimg.size(), cudaMemcpyHostToDevice));
+        ok(cudaMemcpy(f->tcGt, gtimg.data(), gtimg.size(), cudaMemcpyHostToDevice));
         ok(cudaMemset(f->master, 0, f->nparams * sizeof(float)));
         ok(cudaMemset(f->grad, 0, f->nparams * sizeof(float)));
         ok(cudaMemset(f->am, 0, f->nparams * sizeof(float)));
@@ -580,8 +595,13 @@ SPE_API int spe_fno_backward(spe_fno *f, const void *psi_target, double *loss_ou
     int rc = reduce_into(f, kTopSeg, grid, f->grad + f->off.Q1, kTopSeg - 1, f->dres);
     if (rc) return rc;
     a.vin = v_buf(f, L - 1);
-    SPE_TRY(FK_START_BWD, launch_grad_start(n, M, f->fp32, a, grid, f->st));
-    if ((rc = reduce_into(f, kLayerSeg, grid, f->grad + f->off.W[L - 1], kLayerSeg, nullptr))) return rc;
+    // BF16 activations: the row kernels below on the tensor cores, one partial per CTA of tgrid
+    const bool tc = !f->fp32;
+    const int tiles = rows / kTcTile, tgrid = tiles < kRowBlocks ? tiles : kRowBlocks;
+    const int pgrid = tc ? tgrid : grid;
+    if (tc) SPE_TRY(FK_START_BWD, launch_layer_bwd_tc(n, M, kTcBwdStart, a, tgrid, f->st));
+    else SPE_TRY(FK_START_BWD, launch_grad_start(n, M, f->fp32, a, grid, f->st));
+    if ((rc = reduce_into(f, kLayerSeg, pgrid, f->grad + f->off.W[L - 1], kLayerSeg, nullptr))) return rc;
     for (int l = L - 1; l >= 0; --l) {
         if ((rc = spectral_bwd(f, l, batch))) return rc;
         RowArgs b = base_args(f, batch);
@@ -591,11 +611,13 @@ SPE_API int spe_fno_backward(spe_fno *f, const void *psi_target, double *loss_ou
         if (l >= 1) {
             b.vin = v_buf(f, l - 1);
             b.upre = u_buf(f, l - 1);
-            SPE_TRY(FK_LAYER_BWD, launch_layer_bwd(n, M, f->fp32, b, grid, f->st));
-            if ((rc = reduce_into(f, kLayerSeg, grid, f->grad + f->off.W[l - 1], kLayerSeg, nullptr))) return rc;
+            if (tc) SPE_TRY(FK_LAYER_BWD, launch_layer_bwd_tc(n, M, kTcBwdLayer, b, tgrid, f->st));
+            else SPE_TRY(FK_LAYER_BWD, launch_layer_bwd(n, M, f->fp32, b, grid, f->st));
+            if ((rc = reduce_into(f, kLayerSeg, pgrid, f->grad + f->off.W[l - 1], kLayerSeg, nullptr))) return rc;
         } else {
-            SPE_TRY(FK_LIFT_BWD, launch_lift_bwd(n, M, f->fp32, b, grid, f->st));
-            if ((rc = reduce_into(f, kLiftSeg, grid, f->grad + f->off.P, kLiftSeg, nullptr))) return rc;
+            if (tc) SPE_TRY(FK_LIFT_BWD, launch_layer_bwd_tc(n, M, kTcBwdLift, b, tgrid, f->st));
+            else SPE_TRY(FK_LIFT_BWD, launch_lift_bwd(n, M, f->fp32, b, grid, f->st));
+            if ((rc = reduce_into(f, kLiftSeg, pgrid, f->grad + f->off.P, kLiftSeg, nullptr))) return rc;
         }
     }
     if (loss_out) {

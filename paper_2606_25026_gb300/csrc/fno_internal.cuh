@@ -61,6 +61,7 @@ struct RowArgs {
     float *partials;                // [gridDim.x][segment]
     int *status;                    // device status word (tensor-core wait timeouts)
     const uint4 *tcG, *tcF;         // BF16 operand images of G' [n][2M] and F' [2M][n] (K-major)
+    const uint4 *tcFt, *tcGt;       // backward images: F'' [n][2M] = (Re Fx, Im Fx) and G'' [2M][n] = (Re Gx, -Im Gx)
 };
 
 // forward row kernels (fno_fwd.cu)
@@ -82,6 +83,13 @@ constexpr int kTcBlocks = 456;      // 3 CTAs per SM (about 66 KB of shared memo
 constexpr int kProjBlocks = 1216;   // up to 8 CTAs per SM
 cudaError_t launch_layer_fwd_tc(int n, int M, int mode, const RowArgs &a, int grid, cudaStream_t st);
 cudaError_t launch_proj_tc(const RowArgs &a, int cells, int grid, cudaStream_t st);
+
+// tensor-core backward row kernels, BF16 activations (fno_tc_bwd.cu); grid <= rows / kTcTile CTAs,
+// each writing one partial segment (kLayerSeg, or kLiftSeg for the lift)
+constexpr int kTcBwdLayer = 0;      // v bar, u bar_{l-1}, Bbar_{l-1}, dL/dW_{l-1}, dL/db_{l-1}
+constexpr int kTcBwdStart = 1;      // Bbar_{L-1}, dL/dW_{L-1}, dL/db_{L-1} from the given u bar_{L-1}
+constexpr int kTcBwdLift = 2;       // v bar_0, dL/dP, dL/dp
+cudaError_t launch_layer_bwd_tc(int n, int M, int mode, const RowArgs &a, int grid, cudaStream_t st);
 
 // mode-space and elementwise kernels (fno_modes.cu)
 // out[o][m][i] = scale * sum_j Mat[m][j] in[o][j][i] with Mat = Efwd [M][n]

@@ -1,0 +1,333 @@
+// Tensor-core (tcgen05, BF16 operands, FP32 accumulation in TMEM) backward row kernels of the FNO
+// surrogate, used when activations are stored in BF16 (the FP32-activation network keeps the
+// CUDA-core kernels of fno_bwd.cu, whose gradients match the FP64 reference to 1e-4).
+//
+// Cotangents as in fno_bwd.cu: for a Fourier layer u_l = W_l v_{l-1} + b_l + Re(Fx-inverse of the
+// spectral path), v bar = W^T u bar + Re(Fx^H a bar) and the spectral path's x-stage cotangent is
+// Bbar = Gx^H u bar.  A tile is 4 rows; TMEM lane m = (r, c) = r * 32 + c (row r of the tile,
+// channel c), as in the forward kernels.  Per tile (all operands K-major, no swizzle):
+//   G1  D[(r,c)][x]   = sum_(r',j) blockdiag(W^T)[(r,c)][(r',j)] Ubar[r'][x][j]       (K = 128)
+//   G2  D[(r,c)][x]  += sum_kk Abar'[r][kk][c] F''[x][kk]                             (K = 2M)
+//       with Abar' = (Re, Im) of the row's x-stage cotangent and F''[x] = (Re Fx, Im Fx)[kk],
+//       so D = v bar of the row;
+//   epilogue: u bar_{l-1} = D GELU'(u_{l-1}) (stored in FP32, and in BF16 into the A operand of)
+//   G3  E[(r,c)][kk]  = sum_x Ubar'[r][x][c] G''[kk][x]                               (K = n)
+//       with G'' = (Re Gx, -Im Gx): the previous layer's x-stage cotangent Gx^H u bar;
+//   G4  S[(r,c)][(r',j)] += sum_x Ubar'[r][x][c] V[r'][x][j]                          (K = n)
+//       accumulated in TMEM over all tiles of the CTA; the blocks r = r' summed over r are the
+//       CTA's partial dL/dW (the off-diagonal blocks are computed and ignored).
+// Modes: layer (G1-G4), start (u bar of the last layer given: G3, G4), lift (G1, G2, then dL/dP
+// and dL/dp from the four input features on the CUDA cores).  Every CTA writes one partial segment
+// (W [C][C] | b [C], or P [C][4] | p [C]) in a fixed order, so the fixed-order reduction of the
+// partials is deterministic.
+//
+// One thread issues the MMAs; completion arrives on an mbarrier with a bounded wait (on timeout a
+// status bit is set and the kernel carries on).  TMEM (256 columns) is allocated once per CTA and
+// freed before exit.
+#include "fno_tccore.cuh"
+
+namespace spe {
+namespace fno {
+namespace {
+
+constexpr int kBwdLayer = kTcBwdLayer, kBwdStart = kTcBwdStart, kBwdLift = kTcBwdLift;
+
+constexpr int kColE = 64;    // TMEM column of E (D takes columns 0 .. n - 1)
+constexpr int kColS = 128;   // TMEM column of S (128 columns)
+
+template <int N, int M>
+struct BwdSmem {
+    static constexpr int KM = 2 * M;
+    static constexpr int A1 = 0;                       // blockdiag(W^T) [128][128]
+    static constexpr int B1 = A1 + 128 * 128 * 2;      // Ubar [N][128]
+    static constexpr int A2 = B1 + N * 128 * 2;        // Abar' [128][KM]
+    static constexpr int B2 = A2 + 128 * KM * 2;       // F'' [N][KM]
+    static constexpr int A3 = B2 + N * KM * 2;         // Ubar' [128][N]
+    static constexpr int B3 = A3 + 128 * N * 2;        // G'' [KM][N]
+    static constexpr int B4 = B3 + KM * N * 2;         // V as [(r',j)][x]: [128][N]
+    static constexpr int FS = B4;                      // lift: features [kTile][N][4] floats
+    static constexpr int CTL = B4 + 128 * N * 2;
+    static constexpr int BYTES = CTL + 64;
+    // after the tile loop A1 .. B1 hold the reduction scratch
+    static_assert(4 * 32 * 32 * 4 + kRowWarps * 32 * 5 * 4 <= B2, "reduction scratch");
+    static_assert(kTile * N * 4 * 4 <= 128 * N * 2, "lift features");
+};
+
+// 8 floats as 8 BF16 in one 16-byte word
+__device__ __forceinline__ uint4 pack8(const float4 &a, const float4 &b)
+{
+    return make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, b.w));
+}
+
+template <int N, int M, int MODE>
+__global__ void __launch_bounds__(kRowThreads) layer_bwd_tc_kernel(RowArgs a)
+{
+    constexpr bool START = MODE == kBwdStart, LIFT = MODE == kBwdLift;
+    using S = BwdSmem<N, M>;
+    constexpr int KM = S::KM;
+    constexpr int HW = N / 2;                          // epilogue columns per warp
+    extern __shared__ __align__(1024) unsigned char sm[];
+    TcCtl *ctl = reinterpret_cast<TcCtl *>(sm + S::CTL);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r_ep = warp & 3, half = warp >> 2;       // epilogue: tile row (TMEM quadrant), column half
+
+    // ---- per-CTA constants: blockdiag(W^T) (zero off the diagonal), F'', G''
+    if (!START) {
+        for (int e = tid; e < 128 * 128 * 2 / 16; e += kRowThreads)
+            reinterpret_cast<uint4 *>(sm + S::A1)[e] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        for (int e = tid; e < kTile * kC * 4; e += kRowThreads) {
+            const int r = e / (kC * 4), c = (e / 4) % kC, q = e % 4;
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const unsigned short lo = __bfloat16_as_ushort(a.w[a.oW + (size_t)(q * 8 + 2 * i) * kC + c]);
+                const unsigned short hi = __bfloat16_as_ushort(a.w[a.oW + (size_t)(q * 8 + 2 * i + 1) * kC + c]);
+                w[i] = (uint32_t)lo | ((uint32_t)hi << 16);
+            }
+            *reinterpret_cast<uint4 *>(sm + S::A1 + kmaj(r * 32 + c, r * 32 + q * 8, 128)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        for (int e = tid; e < N * KM * 2 / 16; e += kRowThreads)
+            reinterpret_cast<uint4 *>(sm + S::B2)[e] = a.tcFt[e];
+    }
+    if (!LIFT)
+        for (int e = tid; e < N * KM * 2 / 16; e += kRowThreads) reinterpret_cast<uint4 *>(sm + S::B3)[e] = a.tcGt[e];
+    ctl_setup<256>(ctl);
+    float Pr[kFin];                                    // lift: this lane's dL/dP row partial
+    float gacc = 0.f;                                  // dL/db or dL/dp partial of channel `lane`
+#pragma unroll
+    for (int f = 0; f < kFin; ++f) Pr[f] = 0.f;
+    float *fs = reinterpret_cast<float *>(sm + S::FS);
+    to_tensor_cores();
+    const uint32_t tbase = ctl->tmem_base;
+
+    const __nv_bfloat16 *vin = (const __nv_bfloat16 *)a.vin;
+    const __nv_bfloat16 *upre = (const __nv_bfloat16 *)a.upre;
+    const int tiles = a.rows / kTile;
+    int done = 0;
+
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++done) {
+        const int row0 = t * kTile;
+        const int row = row0 + r_ep;
+        if (!START) {
+            // Ubar (B1) and Abar' (A2)
+            for (int e = tid; e < kTile * N * 4; e += kRowThreads) {
+                const int r = e / (N * 4), x = (e / 4) % N, q = e % 4;
+                const float4 *u = reinterpret_cast<const float4 *>(a.ubar + ((size_t)(row0 + r) * N + x) * kC + q * 8);
+                *reinterpret_cast<uint4 *>(sm + S::B1 + kmaj(x, r * 32 + q * 8, 128)) = pack8(u[0], u[1]);
+            }
+            for (int e = tid; e < kTile * M * kC; e += kRowThreads) {
+                const int r = e / (M * kC), kx = (e / kC) % M, c = e % kC;
+                const float2 b = a.xrow[((size_t)(row0 + r) * M + kx) * kC + c];
+                *reinterpret_cast<uint32_t *>(sm + S::A2 + kmaj(r * 32 + c, 2 * kx, KM)) = pack_bf16(b.x, b.y);
+            }
+        }
+        if (!LIFT) {
+            // V as [(r',j)][x]: each lane takes two neighbouring x of 8 channels and stores the
+            // eight (x, x + 1) pairs of BF16 as 32-bit words
+            for (int it = warp; it < kTile * (N / 16); it += kRowWarps) {
+                const int rr = it / (N / 16), xb = (it % (N / 16)) * 16;
+                const int p = lane & 3, q = lane >> 2;
+                const int x = xb + (q & 1) * 8 + 2 * p, j0 = (q >> 1) * 8;
+                const __nv_bfloat16 *src = vin + ((size_t)(row0 + rr) * N + x) * kC + j0;
+                const uint4 v0 = *reinterpret_cast<const uint4 *>(src);
+                const uint4 v1 = *reinterpret_cast<const uint4 *>(src + kC);
+                const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w}, w1[4] = {v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj)
+                    *reinterpret_cast<uint32_t *>(sm + S::B4 + kmaj(rr * 32 + j0 + jj, x, N)) =
+                        __byte_perm(w0[jj >> 1], w1[jj >> 1], (jj & 1) ? 0x7632 : 0x5410);
+            }
+        }
+        if (LIFT) {
+            for (int e = tid; e < kTile * N; e += kRowThreads) {
+                const size_t c = (size_t)row0 * N + e;
+                const float2 u = a.psi[c], q = a.psib[c];
+                fs[e * 4 + 0] = u.x * a.inv_A;
+                fs[e * 4 + 1] = u.y * a.inv_A;
+                fs[e * 4 + 2] = q.x * a.inv_A;
+                fs[e * 4 + 3] = q.y * a.inv_A;
+            }
+        }
+        if (START) {
+            // the given u bar straight into the A operand of G3 / G4
+#pragma unroll
+            for (int i = 0; i < HW; i += 8) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) {
+                    const size_t e0 = ((size_t)row * N + half * HW + i + k) * kC + lane;
+                    const float u0 = a.ubar[e0], u1 = a.ubar[e0 + kC];
+                    gacc += u0;
+                    gacc += u1;
+                    pk[k / 2] = pack_bf16(u0, u1);
+                }
+                *reinterpret_cast<uint4 *>(sm + S::A3 + kmaj(r_ep * 32 + lane, half * HW + i, N)) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        to_tensor_cores();
+        if (!START) {
+            if (tid == 0) {
+                constexpr uint32_t id1 = idesc_bf16(N);
+#pragma unroll
+                for (int s = 0; s < 128 / 16; ++s)
+                    mma_bf16(tbase, desc_k(sm + S::A1 + s * 256, 128), desc_k(sm + S::B1 + s * 256, 128), id1,
+                             s > 0);
+#pragma unroll
+                for (int s = 0; s < KM / 16; ++s)
+                    mma_bf16(tbase, desc_k(sm + S::A2 + s * 256, KM), desc_k(sm + S::B2 + s * 256, KM), id1, 1);
+                tc_commit(&ctl->mbar);
+            }
+            wait_mma(ctl, a.status);
+            float d[HW];
+            tmem_ld<HW>(tbase + ((uint32_t)(r_ep * 32) << 16) + half * HW, d);
+            if (LIFT) {
+                // v bar of the lift: dL/dp += v bar, dL/dP[c][f] += v bar * feature f
+#pragma unroll
+                for (int i = 0; i < HW; ++i) {
+                    const float *f = fs + (r_ep * N + half * HW + i) * 4;
+                    gacc += d[i];
+#pragma unroll
+                    for (int q = 0; q < kFin; ++q) Pr[q] = fmaf(d[i], f[q], Pr[q]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < HW; i += 8) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int k = 0; k < 8; k += 2) {
+                        const size_t e0 = ((size_t)row * N + half * HW + i + k) * kC + lane;
+                        const float u0 = d[i + k] * gelu_grad(__bfloat162float(upre[e0]));
+                        const float u1 = d[i + k + 1] * gelu_grad(__bfloat162float(upre[e0 + kC]));
+                        a.ubar[e0] = u0;
+                        a.ubar[e0 + kC] = u1;
+                        gacc += u0;
+                        gacc += u1;
+                        pk[k / 2] = pack_bf16(u0, u1);
+                    }
+                    *reinterpret_cast<uint4 *>(sm + S::A3 + kmaj(r_ep * 32 + lane, half * HW + i, N)) =
+                        make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                }
+            }
+            end_phase(ctl);
+        }
+        if (!LIFT) {
+            to_tensor_cores();
+            if (tid == 0) {
+                constexpr uint32_t id3 = idesc_bf16(KM), id4 = idesc_bf16(128);
+#pragma unroll
+                for (int s = 0; s < N / 16; ++s)
+                    mma_bf16(tbase + kColE, desc_k(sm + S::A3 + s * 256, N), desc_k(sm + S::B3 + s * 256, N), id3,
+                             s > 0);
+#pragma unroll
+                for (int s = 0; s < N / 16; ++s)
+                    mma_bf16(tbase + kColS, desc_k(sm + S::A3 + s * 256, N), desc_k(sm + S::B4 + s * 256, N), id4,
+                             (s > 0 || done > 0) ? 1u : 0u);
+                tc_commit(&ctl->mbar);
+            }
+            wait_mma(ctl, a.status);
+            {
+                constexpr int EW = KM / 2;          // 8 or 16 columns per warp
+                // KM = 16: both halves read the same 16 columns and half 1 stores nothing
+                float d[16];
+                tmem_ld16(tbase + ((uint32_t)(r_ep * 32) << 16) + kColE + (EW == 16 ? half * 16 : 0), d);
+                if (EW == 16 || half == 0) {
+                    const int kx0 = (EW == 16) ? half * 8 : 0;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        a.xrow[((size_t)row * M + kx0 + k) * kC + lane] = make_float2(d[2 * k], d[2 * k + 1]);
+                }
+            }
+            end_phase(ctl);
+        }
+        __syncthreads();   // the next tile restages the operands
+    }
+
+    // ---- the CTA's partial segment, in a fixed order
+    float *red = reinterpret_cast<float *>(sm + S::A1);          // [4][32][32] diagonal blocks of S
+    float *gred = red + 4 * 32 * 32;                              // [8 warps][32][5]
+    const int seg = LIFT ? kLiftSeg : kLayerSeg;
+    float *out = a.partials + (size_t)blockIdx.x * seg;
+    if (!LIFT && done > 0) {
+        float sv[16];
+        tmem_ld16(tbase + ((uint32_t)(r_ep * 32) << 16) + kColS + r_ep * 32 + half * 16, sv);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) red[(r_ep * 32 + lane) * 32 + half * 16 + i] = sv[i];
+    }
+    gred[(warp * 32 + lane) * 5 + 0] = gacc;
+#pragma unroll
+    for (int f = 0; f < kFin; ++f) gred[(warp * 32 + lane) * 5 + 1 + f] = Pr[f];
+    __syncthreads();
+    if (LIFT) {
+        for (int e = tid; e < kC * kFin; e += kRowThreads) {
+            const int c = e / kFin, f = e % kFin;
+            float s = 0.f;
+            for (int w = 0; w < kRowWarps; ++w) s += gred[(w * 32 + c) * 5 + 1 + f];
+            out[c * kFin + f] = s;
+        }
+        for (int c = tid; c < kC; c += kRowThreads) {
+            float s = 0.f;
+            for (int w = 0; w < kRowWarps; ++w) s += gred[(w * 32 + c) * 5];
+            out[kC * kFin + c] = s;
+        }
+    } else {
+        for (int e = tid; e < kC * kC; e += kRowThreads) {
+            float s = 0.f;
+            if (done > 0)
+                for (int r = 0; r < 4; ++r) s += red[(r * 32 + e / kC) * 32 + e % kC];
+            out[e] = s;
+        }
+        for (int c = tid; c < kC; c += kRowThreads) {
+            float s = 0.f;
+            for (int w = 0; w < kRowWarps; ++w) s += gred[(w * 32 + c) * 5];
+            out[kC * kC + c] = s;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_free_n<256>(tbase);
+}
+
+template <int N, int M, int MODE>
+cudaError_t bwd_tc_run(const RowArgs &a, int grid, cudaStream_t st)
+{
+    constexpr int bytes = BwdSmem<N, M>::BYTES;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(layer_bwd_tc_kernel<N, M, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    layer_bwd_tc_kernel<N, M, MODE><<<grid, kRowThreads, bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int N, int M>
+cudaError_t bwd_tc_mode(int mode, const RowArgs &a, int grid, cudaStream_t st)
+{
+    if (mode == kBwdLift) return bwd_tc_run<N, M, kBwdLift>(a, grid, st);
+    if (mode == kBwdStart) return bwd_tc_run<N, M, kBwdStart>(a, grid, st);
+    return bwd_tc_run<N, M, kBwdLayer>(a, grid, st);
+}
+
+}  // namespace
+
+cudaError_t launch_layer_bwd_tc(int n, int M, int mode, const RowArgs &a, int grid, cudaStream_t st)
+{
+    if (a.rows % kTile || grid < 1 || grid > a.rows / kTile) return cudaErrorInvalidValue;
+#define SPE_FNO_TC_CASE(NN, MM) \
+    if (n == NN && M == MM) return bwd_tc_mode<NN, MM>(mode, a, grid, st);
+    SPE_FNO_TC_CASE(64, 16)
+    SPE_FNO_TC_CASE(64, 8)
+    SPE_FNO_TC_CASE(32, 16)
+    SPE_FNO_TC_CASE(32, 8)
+#undef SPE_FNO_TC_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace fno
+}  // namespace spe
