@@ -591,12 +591,14 @@ SPE_API int spe_fno_backward(spe_fno *f, const void *psi_target, double *loss_ou
     a.target = (const float2 *)psi_target;
     a.vin = v_buf(f, L);
     a.loss_scale = (float)(2.0 / (f->cfg.sigma * (double)batch * (double)n * n * n));
-    SPE_TRY(FK_TOP_BWD, launch_top_bwd(n, f->fp32, a, grid, f->st));
-    int rc = reduce_into(f, kTopSeg, grid, f->grad + f->off.Q1, kTopSeg - 1, f->dres);
+    // BF16 activations: the row kernels on the tensor cores, one partial per CTA of their grids
+    const bool tc = !f->fp32;
+    const int pcells = rows * n, ptiles = pcells / 128, pgrid_top = ptiles < kRowBlocks ? ptiles : kRowBlocks;
+    if (tc) SPE_TRY(FK_TOP_BWD, launch_proj_bwd_tc(a, pcells, pgrid_top, f->st));
+    else SPE_TRY(FK_TOP_BWD, launch_top_bwd(n, f->fp32, a, grid, f->st));
+    int rc = reduce_into(f, kTopSeg, tc ? pgrid_top : grid, f->grad + f->off.Q1, kTopSeg - 1, f->dres);
     if (rc) return rc;
     a.vin = v_buf(f, L - 1);
-    // BF16 activations: the row kernels below on the tensor cores, one partial per CTA of tgrid
-    const bool tc = !f->fp32;
     const int tiles = rows / kTcTile, tgrid = tiles < kRowBlocks ? tiles : kRowBlocks;
     const int pgrid = tc ? tgrid : grid;
     if (tc) SPE_TRY(FK_START_BWD, launch_layer_bwd_tc(n, M, kTcBwdStart, a, tgrid, f->st));

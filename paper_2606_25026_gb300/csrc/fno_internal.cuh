@@ -90,6 +90,9 @@ constexpr int kTcBwdLayer = 0;      // v bar, u bar_{l-1}, Bbar_{l-1}, dL/dW_{l-
 constexpr int kTcBwdStart = 1;      // Bbar_{L-1}, dL/dW_{L-1}, dL/db_{L-1} from the given u bar_{L-1}
 constexpr int kTcBwdLift = 2;       // v bar_0, dL/dP, dL/dp
 cudaError_t launch_layer_bwd_tc(int n, int M, int mode, const RowArgs &a, int grid, cudaStream_t st);
+// projection backward (top of the backward pass): u bar of the last layer, dL/dQ1, dL/dq1, dL/dQ2,
+// dL/dq2 and the loss; cells a multiple of 128, grid <= cells / 128, one kTopSeg partial per CTA
+cudaError_t launch_proj_bwd_tc(const RowArgs &a, int cells, int grid, cudaStream_t st);
 
 // mode-space and elementwise kernels (fno_modes.cu)
 // out[o][m][i] = scale * sum_j Mat[m][j] in[o][j][i] with Mat = Efwd [M][n]

@@ -314,6 +314,212 @@ cudaError_t bwd_tc_mode(int mode, const RowArgs &a, int grid, cudaStream_t st)
     return bwd_tc_run<N, M, kBwdLayer>(a, grid, st);
 }
 
+// Projection backward on the tensor cores: a tile of 128 cells, TMEM lane = cell.
+//   GA  H[cell][j]   = sum_c V[cell][c] Q1[j][c]                 (K = 32), h = H + q1
+//   epilogue: g = GELU(h), o = Q2 g + q2, the loss term, ob = dL/do, hb = (Q2^T ob) GELU'(h)
+//   GB  VB[cell][c]  = sum_j Hb[cell][j] Q1[j][c]                (K = 64): u bar of the last layer
+//   GW  W[m][k]     += sum_cell Aw[m][cell] Bw[k][cell]           (K = 128 cells, accumulated in
+//       TMEM over the CTA's tiles) with rows m < 64 = Hb^T and m >= 64 = G^T, columns k < 32 = V^T,
+//       k = 32, 33 the two ob and k = 34 ones: dL/dQ1[j][c] = W[j][c], dL/dq1[j] = W[j][34],
+//       dL/dQ2[o][j] = W[64 + j][32 + o].  dL/dq2 and the loss are summed on the CUDA cores.
+struct ProjBwdSmem {
+    static constexpr int AV = 0;                  // V [128][32]
+    static constexpr int BQ = AV + 128 * 32 * 2;  // Q1 [64][32]
+    static constexpr int AH = BQ + 64 * 32 * 2;   // Hb [128][64]
+    static constexpr int BQT = AH + 128 * 64 * 2; // Q1^T [32][64]
+    static constexpr int AW = BQT + 32 * 64 * 2;  // [Hb^T; G^T] [128][128]
+    static constexpr int BW = AW + 128 * 128 * 2; // [V^T; ob; 1; 0] [48][128]
+    static constexpr int PART = BW + 48 * 128 * 2;// [2 halves][128][2] partial o
+    static constexpr int PAR = PART + 2 * 128 * 2 * 4;   // q1 [64], Q2 [2][64], q2 [2]
+    static constexpr int RED = PAR + (64 + 128 + 2) * 4; // [128][3] loss and dL/dq2 partials
+    static constexpr int CTL = (RED + 128 * 3 * 4 + 63) & ~63;
+    static constexpr int BYTES = CTL + 64;
+};
+
+__device__ __forceinline__ void put_bf16(unsigned char *base, int off, float v)
+{
+    *reinterpret_cast<unsigned short *>(base + off) = bf16_bits(v);
+}
+
+__global__ void __launch_bounds__(kRowThreads) proj_bwd_tc_kernel(RowArgs a, int cells)
+{
+    using S = ProjBwdSmem;
+    constexpr int kColH = 0, kColVB = 64, kColW = 128;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    TcCtl *ctl = reinterpret_cast<TcCtl *>(sm + S::CTL);
+    float *part = reinterpret_cast<float *>(sm + S::PART);
+    float *q1 = reinterpret_cast<float *>(sm + S::PAR);
+    float *q2w = q1 + 64;
+    float *q2b = q2w + 128;
+    float *red = reinterpret_cast<float *>(sm + S::RED);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int qd = warp & 3, half = warp >> 2;
+    const int m = qd * 32 + lane;                 // this thread's cell (TMEM lane) in the tile
+
+    // ---- per-CTA constants: Q1, Q1^T, the ones row and zero rows of Bw, q1, Q2, q2
+    for (int e = tid; e < kH * 4; e += kRowThreads) {
+        const int j = e / 4, q = e % 4;
+        *reinterpret_cast<uint4 *>(sm + S::BQ + kmaj(j, q * 8, 32)) =
+            *reinterpret_cast<const uint4 *>(a.w + a.oQ1 + j * kC + q * 8);
+    }
+    for (int e = tid; e < kC * kH; e += kRowThreads) {
+        const int c = e / kH, j = e % kH;
+        *reinterpret_cast<unsigned short *>(sm + S::BQT + kmaj(c, j, 64)) =
+            __bfloat16_as_ushort(a.w[a.oQ1 + (size_t)j * kC + c]);
+    }
+    for (int e = tid; e < 16 * 128; e += kRowThreads) {
+        const int k = 32 + e / 128, cell = e % 128;
+        put_bf16(sm + S::BW, kmaj(k, cell, 128), k == 34 ? 1.f : 0.f);
+    }
+    for (int e = tid; e < kH; e += kRowThreads) q1[e] = wload(a.w, a.oq1 + e);
+    for (int e = tid; e < 2 * kH; e += kRowThreads) q2w[e] = wload(a.w, a.oQ2 + e);
+    if (tid < 2) q2b[tid] = wload(a.w, a.oq2 + tid);
+    ctl_setup<256>(ctl);
+    to_tensor_cores();
+    const uint32_t tbase = ctl->tmem_base;
+    const uint32_t lrow = (uint32_t)(qd * 32) << 16;
+    const __nv_bfloat16 *vin = (const __nv_bfloat16 *)a.vin;
+    const int tiles = cells / 128;
+    float loss = 0.f, gq2a = 0.f, gq2b = 0.f;
+    int done = 0;
+
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++done) {
+        const size_t cell0 = (size_t)t * 128;
+        const size_t cell = cell0 + m;
+        // V [cell][c] (A of GA) and V^T [c][cell] (rows 0..31 of Bw, pairs of cells per word)
+        for (int e = tid; e < 128 * 4; e += kRowThreads) {
+            const int mm = e / 4, q = e % 4;
+            *reinterpret_cast<uint4 *>(sm + S::AV + kmaj(mm, q * 8, 32)) =
+                *reinterpret_cast<const uint4 *>(vin + (cell0 + mm) * kC + q * 8);
+        }
+        {
+            const int p = lane & 3, q = lane >> 2;
+            // each warp takes 16 cells: lanes (p, q) hold cells mm, mm + 1 of channels j0 .. j0 + 7
+            const int mm = warp * 16 + (q & 1) * 8 + 2 * p, j0 = (q >> 1) * 8;
+            const __nv_bfloat16 *src = vin + (cell0 + mm) * kC + j0;
+            const uint4 v0 = *reinterpret_cast<const uint4 *>(src);
+            const uint4 v1 = *reinterpret_cast<const uint4 *>(src + kC);
+            const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w}, w1[4] = {v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                *reinterpret_cast<uint32_t *>(sm + S::BW + kmaj(j0 + jj, mm, 128)) =
+                    __byte_perm(w0[jj >> 1], w1[jj >> 1], (jj & 1) ? 0x7632 : 0x5410);
+        }
+        to_tensor_cores();
+        if (tid == 0) {
+            constexpr uint32_t id = idesc_bf16(64);
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+                mma_bf16(tbase + kColH, desc_k(sm + S::AV + s * 256, 32), desc_k(sm + S::BQ + s * 256, 32), id, s > 0);
+            tc_commit(&ctl->mbar);
+        }
+        wait_mma(ctl, a.status);
+        float h[32];
+        tmem_ld32(tbase + lrow + kColH + half * 32, h);
+        float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int j = half * 32 + i;
+            h[i] += q1[j];
+            const float g = gelu(h[i]);
+            o0 = fmaf(q2w[j], g, o0);
+            o1 = fmaf(q2w[kH + j], g, o1);
+            put_bf16(sm + S::AW, kmaj(64 + j, m, 128), g);
+        }
+        part[(half * 128 + m) * 2] = o0;
+        part[(half * 128 + m) * 2 + 1] = o1;
+        end_phase(ctl);      // also orders the partial sums of o before they are read
+        const float O0 = part[m * 2] + part[(128 + m) * 2] + q2b[0];
+        const float O1 = part[m * 2 + 1] + part[(128 + m) * 2 + 1] + q2b[1];
+        const float2 pb = a.psib[cell], tg = a.target[cell];
+        const float dx = pb.x + a.sigma * O0 - tg.x, dy = pb.y + a.sigma * O1 - tg.y;
+        const float ob0 = a.loss_scale * dx, ob1 = a.loss_scale * dy;
+        if (half == 0) {
+            loss = fmaf(dx, dx, loss);
+            loss = fmaf(dy, dy, loss);
+            gq2a += ob0;
+            gq2b += ob1;
+            put_bf16(sm + S::BW, kmaj(32, m, 128), ob0);
+            put_bf16(sm + S::BW, kmaj(33, m, 128), ob1);
+        }
+#pragma unroll
+        for (int i = 0; i < 32; i += 8) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                const int j = half * 32 + i + k;
+                const float hb0 = (q2w[j] * ob0 + q2w[kH + j] * ob1) * gelu_grad(h[i + k]);
+                const float hb1 = (q2w[j + 1] * ob0 + q2w[kH + j + 1] * ob1) * gelu_grad(h[i + k + 1]);
+                put_bf16(sm + S::AW, kmaj(j, m, 128), hb0);
+                put_bf16(sm + S::AW, kmaj(j + 1, m, 128), hb1);
+                pk[k / 2] = pack_bf16(hb0, hb1);
+            }
+            *reinterpret_cast<uint4 *>(sm + S::AH + kmaj(m, half * 32 + i, 64)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        to_tensor_cores();
+        if (tid == 0) {
+            constexpr uint32_t idb = idesc_bf16(32), idw = idesc_bf16(48);
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                mma_bf16(tbase + kColVB, desc_k(sm + S::AH + s * 256, 64), desc_k(sm + S::BQT + s * 256, 64), idb,
+                         s > 0);
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                mma_bf16(tbase + kColW, desc_k(sm + S::AW + s * 256, 128), desc_k(sm + S::BW + s * 256, 128), idw,
+                         (s > 0 || done > 0) ? 1u : 0u);
+            tc_commit(&ctl->mbar);
+        }
+        wait_mma(ctl, a.status);
+        {
+            float vb[16];
+            tmem_ld16(tbase + lrow + kColVB + half * 16, vb);
+            float4 *dst = reinterpret_cast<float4 *>(a.ubar + cell * kC + half * 16);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = make_float4(vb[4 * i], vb[4 * i + 1], vb[4 * i + 2], vb[4 * i + 3]);
+        }
+        end_phase(ctl);
+    }
+
+    // ---- the CTA's partial segment: Q1 [H][C] | q1 [H] | Q2 [2][H] | q2 [2] | loss
+    constexpr int q1o = kH * kC, q2o = kH * kC + kH;
+    float *out = a.partials + (size_t)blockIdx.x * kTopSeg;
+    if (done > 0) {
+        if (half == 0) {
+            float w[32];
+            tmem_ld32(tbase + lrow + kColW, w);
+            if (m < 64) {
+#pragma unroll
+                for (int c = 0; c < kC; ++c) out[m * kC + c] = w[c];
+            }
+        } else {
+            float w[16];
+            tmem_ld16(tbase + lrow + kColW + 32, w);
+            if (m < 64) out[q1o + m] = w[2];
+            else {
+                out[q2o + (m - 64)] = w[0];
+                out[q2o + kH + (m - 64)] = w[1];
+            }
+        }
+    } else {
+        for (int e = tid; e < q2o + 2 * kH; e += kRowThreads) out[e] = 0.f;
+    }
+    if (half == 0) {
+        red[m * 3 + 0] = gq2a;
+        red[m * 3 + 1] = gq2b;
+        red[m * 3 + 2] = loss;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        float s = 0.f;
+        for (int k = 0; k < 128; ++k) s += red[k * 3 + tid];
+        out[kTopSeg - 3 + tid] = s;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_free_n<256>(tbase);
+}
+
 }  // namespace
 
 cudaError_t launch_layer_bwd_tc(int n, int M, int mode, const RowArgs &a, int grid, cudaStream_t st)
@@ -327,6 +533,20 @@ cudaError_t launch_layer_bwd_tc(int n, int M, int mode, const RowArgs &a, int gr
     SPE_FNO_TC_CASE(32, 8)
 #undef SPE_FNO_TC_CASE
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_proj_bwd_tc(const RowArgs &a, int cells, int grid, cudaStream_t st)
+{
+    if (cells % 128 || grid < 1 || grid > cells / 128) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(proj_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             ProjBwdSmem::BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    proj_bwd_tc_kernel<<<grid, kRowThreads, ProjBwdSmem::BYTES, st>>>(a, cells);
+    return cudaGetLastError();
 }
 
 }  // namespace fno
