@@ -398,7 +398,35 @@ def surrogate_arm(args, r):
     t_train = time.perf_counter() - t0
     e_coarse, e_prop = sg.evaluate(net, test)
     params = net.get_params()
-    del train, net
+    # per-kernel breakdown of one training step (forward, backward, Adam) at batch 8: a profiled
+    # copy of the trained network on the first 8 pairs, 3 untimed and 20 timed steps
+    pnet = spe.Fno(n=n, layers=4, modes=16, max_batch=8, train=True, profile=True, inv_A=inv_A, sigma=sigma)
+    pnet.set_params(params)
+    xb, bb, tb = (train.psi[:8].contiguous(), train.psi_b[:8].contiguous(), train.target[:8].contiguous())
+    pout = torch.empty_like(xb)
+    for _ in range(3):
+        pnet.forward(xb, bb, out=pout)
+        pnet.backward(tb)
+        pnet.adam(lr=0.0)
+    torch.cuda.synchronize()
+    pnet.profile_read()
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record()
+    for _ in range(20):
+        pnet.forward(xb, bb, out=pout)
+        pnet.backward(tb)
+        pnet.adam(lr=0.0)
+    pe1.record()
+    pe1.synchronize()
+    tprof = pnet.profile_read()
+    ttot = sum(v[1] for v in tprof.values())
+    train_step = {"ms": pe0.elapsed_time(pe1) / 20, "batch": 8,
+                  "what": "forward, backward (tensor-core row kernels for BF16 activations) and Adam; "
+                          "per-kind device time from events around each kind's launches",
+                  "kernels": {k: {"launches_per_step": v[0] // 20, "ms_per_step": round(v[1] / 20, 4),
+                                  "share": round(v[1] / ttot, 4)}
+                              for k, v in sorted(tprof.items(), key=lambda kv: -kv[1][1])}}
+    del train, net, pnet
     torch.cuda.empty_cache()
 
     inf = spe.Fno(n=n, layers=4, modes=16, max_batch=1, inv_A=inv_A, sigma=sigma)
@@ -512,7 +540,7 @@ def surrogate_arm(args, r):
                   "mass_drift_max": float(max(v["mass_drift"] for v in verdicts)),
                   "energy_drift_max": float(max(v["energy_drift"] for v in verdicts))},
         "training": {"loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "seconds": t_train,
-                     "pair_generation_s": t_gen, "sigma": sigma},
+                     "pair_generation_s": t_gen, "sigma": sigma, "step": train_step},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": dom_bytes / dom_launch_s / 1e9, "peak": peak,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                      else "fallback 6800 GB/s", "unit": "GB/s",
