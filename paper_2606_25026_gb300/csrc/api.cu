@@ -178,6 +178,10 @@ struct spe_grid {
     int *status;      // device status word
     // CUDA graph of one full step (dt_k = dt), replayed on the caller's stream
     cudaStream_t cap_st;
+    // the stars' kick-drift-deposit runs on side_st while the y and z transforms of psi run on st
+    // (fork after the kick pass, join before the density pass); profile mode keeps them serial
+    cudaStream_t side_st;
+    cudaEvent_t fork_ev, join_ev;
     cudaGraphExec_t step_exec;
     double graph_dt;
     size_t graph_np;
@@ -506,6 +510,14 @@ int sort_particles(spe_grid *g)
     return cuerr(e);
 }
 
+int ensure_side_stream(spe_grid *g)
+{
+    if (!g->side_st && cudaStreamCreateWithFlags(&g->side_st, cudaStreamNonBlocking) != cudaSuccess) return SPE_ECUDA;
+    if (!g->fork_ev && cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming) != cudaSuccess) return SPE_ECUDA;
+    if (!g->join_ev && cudaEventCreateWithFlags(&g->join_ev, cudaEventDisableTiming) != cudaSuccess) return SPE_ECUDA;
+    return SPE_OK;
+}
+
 // One KDK step whose leading kick has size dtk (dt/2 for the first step of
 // a call, dt afterwards).
 // absorb_prev: apply the absorbing layer of the previous step (all steps of a
@@ -522,13 +534,29 @@ int step_body(spe_grid *g, double dtk, double dt, bool absorb_prev)
                static_flag(g) | ((absorb_prev && g->absorbing) ? X_ABSORB : 0);
     xp.kick_scale = (float)(dtk / g->cfg.hbar_over_m);
     if ((rc = run_x(g, KIND_X_KICK_FFT, xp))) return rc;
+    // The stars need only the kick pass (the real Phi it writes) and the density pass needs their
+    // deposit, so they run beside the y and z transforms of psi, which touch neither.
+    const bool side = parts && !g->profile;
     if (parts) {
         if (!g->capturing && (g->sort_due || g->steps_done % kSortEvery == 0) && (rc = sort_particles(g))) return rc;
         PParams pp = base_p(g);
         pp.flags = PK_DRIFT | (skick ? PK_KICK : 0) | (grav ? PK_DEPOSIT : 0);
         pp.kick = (float)dtk;
         pp.drift = (float)dt;
-        if ((rc = launch(g, KIND_PARTICLES, [&] { return launch_particles(pp, g->st); }))) return rc;
+        if (side) {
+            if ((rc = ensure_side_stream(g))) return rc;
+            if (cudaEventRecord(g->fork_ev, g->st) != cudaSuccess ||
+                cudaStreamWaitEvent(g->side_st, g->fork_ev, 0) != cudaSuccess)
+                return SPE_ECUDA;
+            rc = launch(g, KIND_PARTICLES, [&] { return launch_particles(pp, g->side_st); });
+            if (cudaEventRecord(g->join_ev, g->side_st) != cudaSuccess && !rc) rc = SPE_ECUDA;
+            if (rc) {
+                cudaStreamWaitEvent(g->st, g->join_ev, 0);   // rejoin the side stream before failing
+                return rc;
+            }
+        } else if ((rc = launch(g, KIND_PARTICLES, [&] { return launch_particles(pp, g->st); }))) {
+            return rc;
+        }
     }
     SParams y = base_y(g, g->psi, g->n[0], g->n[0]);
     y.flags = S_FWD;
@@ -538,6 +566,7 @@ int step_body(spe_grid *g, double dtk, double dt, bool absorb_prev)
     if ((rc = run_s(g, KIND_Z_DRIFT, g->n[2], z))) return rc;
     y.flags = S_INV;
     if ((rc = run_s(g, KIND_Y_PSI, g->n[1], y))) return rc;
+    if (side && cudaStreamWaitEvent(g->st, g->join_ev, 0) != cudaSuccess) return SPE_ECUDA;
     xp.flags = X_IFFT | X_MASS | (grav ? X_R2C : 0) | ((parts && grav) ? X_DEP : 0);
     if ((rc = run_x(g, KIND_X_IFFT_DENSITY, xp))) return rc;
     if (grav) {
@@ -953,6 +982,9 @@ int spe_destroy(spe_grid *g)
     for (auto e : g->evfree) cudaEventDestroy(e);
     if (g->step_exec) cudaGraphExecDestroy(g->step_exec);
     if (g->cap_st) cudaStreamDestroy(g->cap_st);
+    if (g->side_st) cudaStreamDestroy(g->side_st);
+    if (g->fork_ev) cudaEventDestroy(g->fork_ev);
+    if (g->join_ev) cudaEventDestroy(g->join_ev);
     if (g->h_stage) cudaFreeHost(g->h_stage);
     if (g->owns_ws) cudaFree(g->ws);
     delete g;

@@ -68,6 +68,9 @@ __device__ __forceinline__ void tile_reduce(double (&v)[K], int maxmask, double 
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    // the loads are independent of the running sums: unrolled, they are in flight together (the
+    // order of the additions, and so the result, is unchanged)
+#pragma unroll 8
     for (unsigned int b = threadIdx.x; b < nblocks; b += NT) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
