@@ -60,7 +60,7 @@ __device__ __forceinline__ uint4 pack8(const float4 &a, const float4 &b)
 }
 
 template <int N, int M, int MODE>
-__global__ void __launch_bounds__(kRowThreads) layer_bwd_tc_kernel(RowArgs a)
+__global__ void __launch_bounds__(kRowThreads, 2) layer_bwd_tc_kernel(RowArgs a)
 {
     constexpr bool START = MODE == kBwdStart, LIFT = MODE == kBwdLift;
     using S = BwdSmem<N, M>;
@@ -110,30 +110,68 @@ __global__ void __launch_bounds__(kRowThreads) layer_bwd_tc_kernel(RowArgs a)
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++done) {
         const int row0 = t * kTile;
         const int row = row0 + r_ep;
+        // the tile's global loads first, all in flight together, then their conversions and stores
+        constexpr int NB1 = kTile * N * 4 / kRowThreads, NA2 = kTile * M * kC / kRowThreads;
+        constexpr int NB4 = kTile * (N / 16) / kRowWarps;
+        static_assert(NB1 * kRowThreads == kTile * N * 4 && NA2 * kRowThreads == kTile * M * kC &&
+                          NB4 * kRowWarps == kTile * (N / 16),
+                      "staging loops divide evenly");
+        float4 ub[START ? 1 : NB1][2];
+        float2 ab[START ? 1 : NA2];
+        uint4 vv[LIFT ? 1 : NB4][2];
         if (!START) {
-            // Ubar (B1) and Abar' (A2)
-            for (int e = tid; e < kTile * N * 4; e += kRowThreads) {
-                const int r = e / (N * 4), x = (e / 4) % N, q = e % 4;
+#pragma unroll
+            for (int i = 0; i < NB1; ++i) {
+                const int e = tid + i * kRowThreads, r = e / (N * 4), x = (e / 4) % N, q = e % 4;
                 const float4 *u = reinterpret_cast<const float4 *>(a.ubar + ((size_t)(row0 + r) * N + x) * kC + q * 8);
-                *reinterpret_cast<uint4 *>(sm + S::B1 + kmaj(x, r * 32 + q * 8, 128)) = pack8(u[0], u[1]);
+                ub[i][0] = u[0];
+                ub[i][1] = u[1];
             }
-            for (int e = tid; e < kTile * M * kC; e += kRowThreads) {
-                const int r = e / (M * kC), kx = (e / kC) % M, c = e % kC;
-                const float2 b = a.xrow[((size_t)(row0 + r) * M + kx) * kC + c];
-                *reinterpret_cast<uint32_t *>(sm + S::A2 + kmaj(r * 32 + c, 2 * kx, KM)) = pack_bf16(b.x, b.y);
+#pragma unroll
+            for (int i = 0; i < NA2; ++i) {
+                const int e = tid + i * kRowThreads, r = e / (M * kC), kx = (e / kC) % M, c = e % kC;
+                ab[i] = a.xrow[((size_t)(row0 + r) * M + kx) * kC + c];
+            }
+        }
+        // V as [(r',j)][x]: each lane takes two neighbouring x of 8 channels and stores the eight
+        // (x, x + 1) pairs of BF16 as 32-bit words
+        const int vp = lane & 3, vq = lane >> 2;
+        if (!LIFT) {
+#pragma unroll
+            for (int i = 0; i < NB4; ++i) {
+                const int it = warp + i * kRowWarps, rr = it / (N / 16), xb = (it % (N / 16)) * 16;
+                const int x = xb + (vq & 1) * 8 + 2 * vp, j0 = (vq >> 1) * 8;
+                const __nv_bfloat16 *src = vin + ((size_t)(row0 + rr) * N + x) * kC + j0;
+                vv[i][0] = *reinterpret_cast<const uint4 *>(src);
+                vv[i][1] = *reinterpret_cast<const uint4 *>(src + kC);
+            }
+        }
+        // layer: the pre-activations the epilogue needs (this lane's channel, this warp's columns)
+        unsigned short up[LIFT || START ? 1 : HW];
+        if (!LIFT && !START) {
+            const unsigned short *ur = reinterpret_cast<const unsigned short *>(upre) + ((size_t)row * N + half * HW) * kC + lane;
+#pragma unroll
+            for (int i = 0; i < HW; ++i) up[i] = ur[(size_t)i * kC];
+        }
+        if (!START) {
+#pragma unroll
+            for (int i = 0; i < NB1; ++i) {
+                const int e = tid + i * kRowThreads, r = e / (N * 4), x = (e / 4) % N, q = e % 4;
+                *reinterpret_cast<uint4 *>(sm + S::B1 + kmaj(x, r * 32 + q * 8, 128)) = pack8(ub[i][0], ub[i][1]);
+            }
+#pragma unroll
+            for (int i = 0; i < NA2; ++i) {
+                const int e = tid + i * kRowThreads, r = e / (M * kC), kx = (e / kC) % M, c = e % kC;
+                *reinterpret_cast<uint32_t *>(sm + S::A2 + kmaj(r * 32 + c, 2 * kx, KM)) = pack_bf16(ab[i].x, ab[i].y);
             }
         }
         if (!LIFT) {
-            // V as [(r',j)][x]: each lane takes two neighbouring x of 8 channels and stores the
-            // eight (x, x + 1) pairs of BF16 as 32-bit words
-            for (int it = warp; it < kTile * (N / 16); it += kRowWarps) {
-                const int rr = it / (N / 16), xb = (it % (N / 16)) * 16;
-                const int p = lane & 3, q = lane >> 2;
-                const int x = xb + (q & 1) * 8 + 2 * p, j0 = (q >> 1) * 8;
-                const __nv_bfloat16 *src = vin + ((size_t)(row0 + rr) * N + x) * kC + j0;
-                const uint4 v0 = *reinterpret_cast<const uint4 *>(src);
-                const uint4 v1 = *reinterpret_cast<const uint4 *>(src + kC);
-                const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w}, w1[4] = {v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+            for (int i = 0; i < NB4; ++i) {
+                const int it = warp + i * kRowWarps, rr = it / (N / 16), xb = (it % (N / 16)) * 16;
+                const int x = xb + (vq & 1) * 8 + 2 * vp, j0 = (vq >> 1) * 8;
+                const uint32_t w0[4] = {vv[i][0].x, vv[i][0].y, vv[i][0].z, vv[i][0].w};
+                const uint32_t w1[4] = {vv[i][1].x, vv[i][1].y, vv[i][1].z, vv[i][1].w};
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj)
                     *reinterpret_cast<uint32_t *>(sm + S::B4 + kmaj(rr * 32 + j0 + jj, x, N)) =
@@ -199,8 +237,8 @@ __global__ void __launch_bounds__(kRowThreads) layer_bwd_tc_kernel(RowArgs a)
 #pragma unroll
                     for (int k = 0; k < 8; k += 2) {
                         const size_t e0 = ((size_t)row * N + half * HW + i + k) * kC + lane;
-                        const float u0 = d[i + k] * gelu_grad(__bfloat162float(upre[e0]));
-                        const float u1 = d[i + k + 1] * gelu_grad(__bfloat162float(upre[e0 + kC]));
+                        const float u0 = d[i + k] * gelu_grad(__bfloat162float(__ushort_as_bfloat16(up[i + k])));
+                        const float u1 = d[i + k + 1] * gelu_grad(__bfloat162float(__ushort_as_bfloat16(up[i + k + 1])));
                         a.ubar[e0] = u0;
                         a.ubar[e0 + kC] = u1;
                         gacc += u0;
@@ -327,8 +365,9 @@ struct ProjBwdSmem {
     static constexpr int BQ = AV + 128 * 32 * 2;  // Q1 [64][32]
     static constexpr int AH = BQ + 64 * 32 * 2;   // Hb [128][64]
     static constexpr int BQT = AH + 128 * 64 * 2; // Q1^T [32][64]
-    static constexpr int AW = BQT + 32 * 64 * 2;  // [Hb^T; G^T] [128][128]
-    static constexpr int BW = AW + 128 * 128 * 2; // [V^T; ob; 1; 0] [48][128]
+    static constexpr int AW = BQT + 32 * 64 * 2;  // [Hb^T; G^T] [128][128], 128-byte swizzle (column writes)
+    static constexpr int BW = AW + 128 * 128 * 2; // [V^T; ob; 1; 0] [48][128], 128-byte swizzle
+    static_assert(AW % 1024 == 0 && BW % 1024 == 0 && (48 * 128) % 1024 == 0, "swizzle atoms 1024-byte aligned");
     static constexpr int PART = BW + 48 * 128 * 2;// [2 halves][128][2] partial o
     static constexpr int PAR = PART + 2 * 128 * 2 * 4;   // q1 [64], Q2 [2][64], q2 [2]
     static constexpr int RED = PAR + (64 + 128 + 2) * 4; // [128][3] loss and dL/dq2 partials
@@ -341,7 +380,7 @@ __device__ __forceinline__ void put_bf16(unsigned char *base, int off, float v)
     *reinterpret_cast<unsigned short *>(base + off) = bf16_bits(v);
 }
 
-__global__ void __launch_bounds__(kRowThreads) proj_bwd_tc_kernel(RowArgs a, int cells)
+__global__ void __launch_bounds__(kRowThreads, 2) proj_bwd_tc_kernel(RowArgs a, int cells)
 {
     using S = ProjBwdSmem;
     constexpr int kColH = 0, kColVB = 64, kColW = 128;
@@ -369,7 +408,7 @@ __global__ void __launch_bounds__(kRowThreads) proj_bwd_tc_kernel(RowArgs a, int
     }
     for (int e = tid; e < 16 * 128; e += kRowThreads) {
         const int k = 32 + e / 128, cell = e % 128;
-        put_bf16(sm + S::BW, kmaj(k, cell, 128), k == 34 ? 1.f : 0.f);
+        put_bf16(sm + S::BW, sw128(k, cell, 48), k == 34 ? 1.f : 0.f);
     }
     for (int e = tid; e < kH; e += kRowThreads) q1[e] = wload(a.w, a.oq1 + e);
     for (int e = tid; e < 2 * kH; e += kRowThreads) q2w[e] = wload(a.w, a.oQ2 + e);
@@ -402,7 +441,7 @@ __global__ void __launch_bounds__(kRowThreads) proj_bwd_tc_kernel(RowArgs a, int
             const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w}, w1[4] = {v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj)
-                *reinterpret_cast<uint32_t *>(sm + S::BW + kmaj(j0 + jj, mm, 128)) =
+                *reinterpret_cast<uint32_t *>(sm + S::BW + sw128(j0 + jj, mm, 48)) =
                     __byte_perm(w0[jj >> 1], w1[jj >> 1], (jj & 1) ? 0x7632 : 0x5410);
         }
         to_tensor_cores();
@@ -419,12 +458,16 @@ __global__ void __launch_bounds__(kRowThreads) proj_bwd_tc_kernel(RowArgs a, int
         float o0 = 0.f, o1 = 0.f;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
+            // GELU(u) = u Phi(u) and GELU'(u) = Phi(u) + u phi(u) share the normal CDF Phi; h[i]
+            // keeps GELU'(u) for the cotangent below
             const int j = half * 32 + i;
-            h[i] += q1[j];
-            const float g = gelu(h[i]);
+            const float u = h[i] + q1[j];
+            const float cdf = 0.5f * (1.f + erff(u * kInvSqrt2));
+            const float g = u * cdf;
+            h[i] = fmaf(u * kInvSqrt2Pi, expf(-0.5f * u * u), cdf);
             o0 = fmaf(q2w[j], g, o0);
             o1 = fmaf(q2w[kH + j], g, o1);
-            put_bf16(sm + S::AW, kmaj(64 + j, m, 128), g);
+            put_bf16(sm + S::AW, sw128(64 + j, m, 128), g);
         }
         part[(half * 128 + m) * 2] = o0;
         part[(half * 128 + m) * 2 + 1] = o1;
@@ -439,8 +482,8 @@ __global__ void __launch_bounds__(kRowThreads) proj_bwd_tc_kernel(RowArgs a, int
             loss = fmaf(dy, dy, loss);
             gq2a += ob0;
             gq2b += ob1;
-            put_bf16(sm + S::BW, kmaj(32, m, 128), ob0);
-            put_bf16(sm + S::BW, kmaj(33, m, 128), ob1);
+            put_bf16(sm + S::BW, sw128(32, m, 48), ob0);
+            put_bf16(sm + S::BW, sw128(33, m, 48), ob1);
         }
 #pragma unroll
         for (int i = 0; i < 32; i += 8) {
@@ -448,10 +491,10 @@ __global__ void __launch_bounds__(kRowThreads) proj_bwd_tc_kernel(RowArgs a, int
 #pragma unroll
             for (int k = 0; k < 8; k += 2) {
                 const int j = half * 32 + i + k;
-                const float hb0 = (q2w[j] * ob0 + q2w[kH + j] * ob1) * gelu_grad(h[i + k]);
-                const float hb1 = (q2w[j + 1] * ob0 + q2w[kH + j + 1] * ob1) * gelu_grad(h[i + k + 1]);
-                put_bf16(sm + S::AW, kmaj(j, m, 128), hb0);
-                put_bf16(sm + S::AW, kmaj(j + 1, m, 128), hb1);
+                const float hb0 = (q2w[j] * ob0 + q2w[kH + j] * ob1) * h[i + k];
+                const float hb1 = (q2w[j + 1] * ob0 + q2w[kH + j + 1] * ob1) * h[i + k + 1];
+                put_bf16(sm + S::AW, sw128(j, m, 128), hb0);
+                put_bf16(sm + S::AW, sw128(j + 1, m, 128), hb1);
                 pk[k / 2] = pack_bf16(hb0, hb1);
             }
             *reinterpret_cast<uint4 *>(sm + S::AH + kmaj(m, half * 32 + i, 64)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -465,7 +508,7 @@ __global__ void __launch_bounds__(kRowThreads) proj_bwd_tc_kernel(RowArgs a, int
                          s > 0);
 #pragma unroll
             for (int s = 0; s < 8; ++s)
-                mma_bf16(tbase + kColW, desc_k(sm + S::AW + s * 256, 128), desc_k(sm + S::BW + s * 256, 128), idw,
+                mma_bf16(tbase + kColW, desc_sw128(sm + S::AW, s, 128), desc_sw128(sm + S::BW, s, 48), idw,
                          (s > 0 || done > 0) ? 1u : 0u);
             tc_commit(&ctl->mbar);
         }

@@ -35,6 +35,28 @@ __device__ __forceinline__ uint64_t desc_k(const void *p, int K)
     return d;
 }
 
+// 128-byte-swizzled K-major operand: atoms of 8 rows x 64 BF16 (1024 bytes, 1024-byte aligned),
+// the 16-byte chunk c of row r stored at chunk c ^ (r & 7); rows are 128 bytes apart and the K range
+// splits into atoms of 64, atom a of a [rows][K] operand at byte a * rows * 128.  A column of such an
+// operand (one k, consecutive rows) spreads over all banks, unlike the no-swizzle core-matrix layout.
+__device__ __forceinline__ int sw128(int row, int k, int rows)
+{
+    return (k >> 6) * rows * 128 + row * 128 + ((((k & 63) >> 3) ^ (row & 7)) << 4) + ((k & 7) << 1);
+}
+
+// descriptor of K step s (16 elements) of a 128-byte-swizzled K-major operand with `rows` rows
+__device__ __forceinline__ uint64_t desc_sw128(const void *base, int s, int rows)
+{
+    const uint64_t addr = smem_u32(base) + (uint32_t)((s >> 2) * rows * 128 + (s & 3) * 32);
+    uint64_t d = 0;
+    d |= (addr >> 4) & 0x3FFFull;
+    d |= (uint64_t)1 << 16;                          // leading offset: unused within a swizzle atom
+    d |= (uint64_t)(1024 >> 4) << 32;                // next 8-row group
+    d |= 1ull << 46;
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
