@@ -98,16 +98,33 @@ __global__ void __launch_bounds__(kRowThreads) layer_fwd_tc_kernel(RowArgs a)
             }
             __syncthreads();
         }
-        // ---- stage V (B1) and B' (A2)
-        for (int e = tid; !LIFT && e < kTile * N * 4; e += kRowThreads) {
-            const int r = e / (N * 4), x = (e / 4) % N, q = e % 4;
-            const uint4 v = *reinterpret_cast<const uint4 *>(vin + ((size_t)(row0 + r) * N + x) * kC + q * 8);
-            *reinterpret_cast<uint4 *>(sm + S::B1 + kmaj(x, r * 32 + q * 8, 128)) = v;
-        }
-        for (int e = tid; !LIFT && e < kTile * M * kC; e += kRowThreads) {
-            const int r = e / (M * kC), kx = (e / kC) % M, c = e % kC;
-            const float2 b = a.xrow[((size_t)(row0 + r) * M + kx) * kC + c];
-            *reinterpret_cast<uint32_t *>(sm + S::A2 + kmaj(r * 32 + c, 2 * kx, KM)) = pack_bf16(b.x, b.y);
+        // ---- stage V (B1) and B' (A2): every load of the tile in flight before the stores
+        if (!LIFT) {
+            constexpr int NV = kTile * N * 4 / kRowThreads, NB = kTile * M * kC / kRowThreads;
+            static_assert(NV * kRowThreads == kTile * N * 4 && NB * kRowThreads == kTile * M * kC,
+                          "staging loops divide evenly");
+            uint4 vv[NV];
+            float2 bb[NB];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const int e = tid + i * kRowThreads, r = e / (N * 4), x = (e / 4) % N, q = e % 4;
+                vv[i] = *reinterpret_cast<const uint4 *>(vin + ((size_t)(row0 + r) * N + x) * kC + q * 8);
+            }
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const int e = tid + i * kRowThreads, r = e / (M * kC), kx = (e / kC) % M, c = e % kC;
+                bb[i] = a.xrow[((size_t)(row0 + r) * M + kx) * kC + c];
+            }
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const int e = tid + i * kRowThreads, r = e / (N * 4), x = (e / 4) % N, q = e % 4;
+                *reinterpret_cast<uint4 *>(sm + S::B1 + kmaj(x, r * 32 + q * 8, 128)) = vv[i];
+            }
+#pragma unroll
+            for (int i = 0; i < NB; ++i) {
+                const int e = tid + i * kRowThreads, r = e / (M * kC), kx = (e / kC) % M, c = e % kC;
+                *reinterpret_cast<uint32_t *>(sm + S::A2 + kmaj(r * 32 + c, 2 * kx, KM)) = pack_bf16(bb[i].x, bb[i].y);
+            }
         }
         if (!LIFT) {
             to_tensor_cores();
