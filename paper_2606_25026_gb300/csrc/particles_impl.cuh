@@ -89,8 +89,9 @@ __device__ __forceinline__ void particles_body(const PParams &p, int block, unsi
     unsigned long long *sdep = reinterpret_cast<unsigned long long *>(box_raw);
     const int i = block * kPartThreads + threadIdx.x;
     const bool live = i < p.n;
-    float x = 0.f, y = 0.f, z = 0.f, vx = 0.f, vy = 0.f, vz = 0.f;
+    float x = 0.f, y = 0.f, z = 0.f, vx = 0.f, vy = 0.f, vz = 0.f, m = 0.f;
     if (live) {
+        if (p.flags & PK_DEPOSIT) m = p.m[i];   // with the other loads: the deposit would wait on it
         x = p.x[i];
         y = p.y[i];
         z = p.z[i];
@@ -109,11 +110,24 @@ __device__ __forceinline__ void particles_body(const PParams &p, int block, unsi
         const int ex = bb[3] - bb[0] + 4, ey = bb[4] - bb[1] + 4, ez = bb[5] - bb[2] + 4;
         const bool tiled = (long long)ex * ey * ez <= kBoxPhi;
         if (tiled) {
+            // four nodes per thread in flight before their stores: the box fill waits on L2 once per
+            // four nodes instead of once per node
             const unsigned mx = div_magic(ex), my = div_magic(ey);
-            for (int v = threadIdx.x; v < ex * ey * ez; v += kPartThreads) {
-                const int r = div_small(v, mx), c = div_small(r, my);
-                const int a = v - r * ex, b = r - c * ey;
-                sphi[v] = __ldg(&p.phi[((size_t)wrapi(oz + c, nz) * ny + wrapi(oy + b, ny)) * nx + wrapi(ox + a, nx)]);
+            const int vol = ex * ey * ez;
+            for (int v0 = threadIdx.x; v0 < vol; v0 += 4 * kPartThreads) {
+                float f[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int v = v0 + u * kPartThreads;
+                    if (v < vol) {
+                        const int r = div_small(v, mx), c = div_small(r, my);
+                        const int a = v - r * ex, b = r - c * ey;
+                        f[u] = __ldg(&p.phi[((size_t)wrapi(oz + c, nz) * ny + wrapi(oy + b, ny)) * nx + wrapi(ox + a, nx)]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (v0 + u * kPartThreads < vol) sphi[v0 + u * kPartThreads] = f[u];
             }
             __syncthreads();
         }
@@ -205,7 +219,7 @@ __device__ __forceinline__ void particles_body(const PParams &p, int block, unsi
         const int ex = bb[3] - bb[0] + 2, ey = bb[4] - bb[1] + 2, ez = bb[5] - bb[2] + 2;
         const int vol = ex * ey * ez;
         const bool tiled = (long long)ex * ey * ez <= kBoxDep;
-        const float mq = live ? p.m[i] * p.inv_quantum : 0.f;
+        const float mq = live ? m * p.inv_quantum : 0.f;
         // The block's box counts in two 32-bit halves, q = hi 2^21 + lo (lo < 2^21): while every
         // share q < 2^41 (a star below 2^-9 of the total star mass), 256 stars cannot carry either
         // half's sum past 2^29, and the flush joins them into the exact 64-bit sum.  32-bit shared
