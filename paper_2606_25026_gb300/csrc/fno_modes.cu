@@ -28,7 +28,8 @@ __global__ void __launch_bounds__(kAxisThreads) axis_kernel(const float2 *__rest
 #pragma unroll
     for (int t = 0; t < MT; ++t) acc[t] = make_float2(0.f, 0.f);
     const float2 *src = in + (size_t)o * NIN * I + i;
-#pragma unroll 4
+    // eight loads of the strided input in flight per thread (the contraction is short and latency-bound)
+#pragma unroll 8
     for (int j = 0; j < NIN; ++j) {
         const float2 x = src[(size_t)j * I];
 #pragma unroll
