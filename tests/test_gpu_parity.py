@@ -226,6 +226,37 @@ def test_fast_stars_sweeping_rows_parity(spe):
     assert periodic_err(gp, op, 1.0) <= POS_TOL
 
 
+def test_heavy_star_cluster_uses_the_64bit_deposit_box_parity(spe):
+    """64 equal stars in a compact cluster: each holds 1/64 of the star mass, so its CIC shares
+    (up to 2^44 quanta) exceed what the star block's 32-bit deposit halves hold, and the block
+    deposits through 64-bit shared counters instead; the cluster is small enough for the block's
+    shared-memory boxes.  Density, psi and the stars must match the oracle."""
+    n = 32
+    rng = np.random.default_rng(93)
+    psi = inputs.gaussian_packets(n, seed=94).astype(np.complex64)
+    dt = inputs.kinetic_dt(n)
+    m = 64
+    pos = rng.uniform(-0.05, 0.05, (m, 3)).astype(np.float32)
+    vel = rng.normal(0.0, 0.05 / n / dt, (m, 3)).astype(np.float32)
+    mass = np.full(m, 0.3 / m, np.float32)
+    g = spe.Grid(n, G=1.0, max_particles=m)
+    g.set_ic(psi)
+    g.add_particles(pos, vel, mass)
+    o = oracle.Oracle(n, n, n, 1.0, G=1.0)
+    o.set_ic(as_oracle(psi))
+    o.set_particles(as_oracle(pos), as_oracle(vel), as_oracle(mass))
+    rho_g, rho_o = g.density().astype(np.float64), o.density()
+    assert np.abs(rho_g - rho_o).max() <= 1e-5 * np.abs(rho_o).max()
+    g.step(8, dt)
+    o.step(8, dt)
+    rho_g, rho_o = g.density().astype(np.float64), o.density()
+    assert np.abs(rho_g - rho_o).max() <= 1e-5 * np.abs(rho_o).max()
+    assert rel_l2(g.get_psi(), o.get_psi()) <= PSI_TOL
+    gp, _ = g.get_particles()
+    op, _ = o.get_particles()
+    assert periodic_err(gp, op, 1.0) <= POS_TOL
+
+
 # --------------------------------------------------------------------------- properties at any size
 
 
