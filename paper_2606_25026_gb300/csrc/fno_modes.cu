@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(256) mix_bwd_kernel(const float2 *__restrict__
 // X[kz][c] = sum_z Efwd[kz][z] A[z][c], mixing Y[kz][o] = sum_i R[k][i][o]
 // X[kz][i] (k = kz M^2 + ky M + kx), z inverse Z[z][c] = (1/n) sum_kz
 // Einv[z][kz] Y[kz][c]; Z overwrites A in place (the block owns the column).
-// X is kept for the backward pass when Xsave is given.  Lane = channel.
+// X is kept for the backward pass when Xsave is given.  Lane = channel.  One block per
+// (column, batch entry): blockIdx.x the column, blockIdx.y the entry.
 template <int N, int M>
 __global__ void __launch_bounds__(256) zmix_fwd_kernel(float2 *__restrict__ A, float2 *__restrict__ Xsave,
                                                       const __nv_bfloat162 *__restrict__ R,
@@ -145,7 +146,9 @@ __global__ void __launch_bounds__(256) zmix_fwd_kernel(float2 *__restrict__ A, f
         ei[e / M][e % M] = Einv[e];
     }
     const float inv_n = 1.f / N;
-    for (int b = 0; b < B; ++b) {
+    const int b = blockIdx.y;
+    (void)B;
+    {
         __syncthreads();
         for (int e = threadIdx.x; e < N * kC; e += 256) {
             const int z = e / kC, c = e % kC;
@@ -190,17 +193,32 @@ __global__ void __launch_bounds__(256) zmix_fwd_kernel(float2 *__restrict__ A, f
     }
 }
 
-__global__ void reduce_partials_kernel(const float *__restrict__ part, int seg, int nblk, float *__restrict__ dst,
-                                       int ndst, double *__restrict__ extra)
+// Column sums of the per-block partials in FP64, in a fixed order: a block takes 32 consecutive
+// entries; its 8 warps each sum the partials b = w, w + 8, ... of those entries (lanes over the
+// entries, so every load is coalesced), and the 8 warp sums are added in warp order.
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const float *__restrict__ part, int seg, int nblk,
+                                                             float *__restrict__ dst, int ndst,
+                                                             double *__restrict__ extra)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= seg) return;
+    __shared__ double ws[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += (double)part[(size_t)b * seg + e];
-    if (e < ndst)
-        dst[e] = (float)s;
-    else
-        extra[e - ndst] = s;
+    if (e < seg) {
+#pragma unroll 4
+        for (int b = warp; b < nblk; b += 8) s += (double)part[(size_t)b * seg + e];
+    }
+    ws[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && e < seg) {
+        double t = ws[0][lane];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) t += ws[w][lane];
+        if (e < ndst)
+            dst[e] = (float)t;
+        else
+            extra[e - ndst] = t;
+    }
 }
 
 __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
@@ -286,10 +304,10 @@ cudaError_t launch_zmix_fwd(int n, int M, float2 *A, float2 *Xsave, const __nv_b
                             const float2 *Einv, int B, cudaStream_t st)
 {
     const __nv_bfloat162 *R2 = (const __nv_bfloat162 *)R;
-    if (n == 64 && M == 16) zmix_fwd_kernel<64, 16><<<M * M, 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
-    else if (n == 64 && M == 8) zmix_fwd_kernel<64, 8><<<M * M, 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
-    else if (n == 32 && M == 16) zmix_fwd_kernel<32, 16><<<M * M, 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
-    else if (n == 32 && M == 8) zmix_fwd_kernel<32, 8><<<M * M, 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
+    if (n == 64 && M == 16) zmix_fwd_kernel<64, 16><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
+    else if (n == 64 && M == 8) zmix_fwd_kernel<64, 8><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
+    else if (n == 32 && M == 16) zmix_fwd_kernel<32, 16><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
+    else if (n == 32 && M == 8) zmix_fwd_kernel<32, 8><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -312,7 +330,7 @@ cudaError_t launch_mix_bwd(int M, const float2 *Ybar, const float2 *X, float2 *X
 cudaError_t launch_reduce_partials(const float *partials, int seg, int nblk, float *dst, int ndst, double *extra,
                                    cudaStream_t st)
 {
-    reduce_partials_kernel<<<(seg + 255) / 256, 256, 0, st>>>(partials, seg, nblk, dst, ndst, extra);
+    reduce_partials_kernel<<<(seg + 31) / 32, 256, 0, st>>>(partials, seg, nblk, dst, ndst, extra);
     return cudaGetLastError();
 }
 
