@@ -130,8 +130,7 @@ __global__ void __launch_bounds__(256) mix_bwd_kernel(const float2 *__restrict__
 template <int N, int M>
 __global__ void __launch_bounds__(256) zmix_fwd_kernel(float2 *__restrict__ A, float2 *__restrict__ Xsave,
                                                       const __nv_bfloat162 *__restrict__ R,
-                                                      const float2 *__restrict__ Efwd, const float2 *__restrict__ Einv,
-                                                      int B)
+                                                      const float2 *__restrict__ Efwd, const float2 *__restrict__ Einv)
 {
     __shared__ float2 as[N][kC];
     __shared__ float2 xs[M][kC];
@@ -147,49 +146,46 @@ __global__ void __launch_bounds__(256) zmix_fwd_kernel(float2 *__restrict__ A, f
     }
     const float inv_n = 1.f / N;
     const int b = blockIdx.y;
-    (void)B;
-    {
-        __syncthreads();
-        for (int e = threadIdx.x; e < N * kC; e += 256) {
-            const int z = e / kC, c = e % kC;
-            as[z][c] = A[(((size_t)b * N + z) * COLS + col) * kC + c];
-        }
-        __syncthreads();
-        for (int kz = warp; kz < M; kz += 8) {
-            float2 acc = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int e = threadIdx.x; e < N * kC; e += 256) {
+        const int z = e / kC, c = e % kC;
+        as[z][c] = A[(((size_t)b * N + z) * COLS + col) * kC + c];
+    }
+    __syncthreads();
+    for (int kz = warp; kz < M; kz += 8) {
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 8
-            for (int z = 0; z < N; ++z) {
-                const float2 m = ef[kz][z], x = as[z][lane];
-                acc.x = fmaf(m.x, x.x, fmaf(-m.y, x.y, acc.x));
-                acc.y = fmaf(m.x, x.y, fmaf(m.y, x.x, acc.y));
-            }
-            xs[kz][lane] = acc;
-            if (Xsave) Xsave[((size_t)b * K + (size_t)kz * COLS + col) * kC + lane] = acc;
+        for (int z = 0; z < N; ++z) {
+            const float2 m = ef[kz][z], x = as[z][lane];
+            acc.x = fmaf(m.x, x.x, fmaf(-m.y, x.y, acc.x));
+            acc.y = fmaf(m.x, x.y, fmaf(m.y, x.x, acc.y));
         }
-        __syncthreads();
-        for (int kz = warp; kz < M; kz += 8) {
-            const __nv_bfloat162 *Rk = R + ((size_t)kz * COLS + col) * kC * kC;
-            float2 y = make_float2(0.f, 0.f);
+        xs[kz][lane] = acc;
+        if (Xsave) Xsave[((size_t)b * K + (size_t)kz * COLS + col) * kC + lane] = acc;
+    }
+    __syncthreads();
+    for (int kz = warp; kz < M; kz += 8) {
+        const __nv_bfloat162 *Rk = R + ((size_t)kz * COLS + col) * kC * kC;
+        float2 y = make_float2(0.f, 0.f);
 #pragma unroll 8
-            for (int i = 0; i < kC; ++i) {
-                const float2 r = __bfloat1622float2(Rk[i * kC + lane]);
-                const float2 x = xs[kz][i];
-                y.x = fmaf(r.x, x.x, fmaf(-r.y, x.y, y.x));
-                y.y = fmaf(r.x, x.y, fmaf(r.y, x.x, y.y));
-            }
-            ys[kz][lane] = y;
+        for (int i = 0; i < kC; ++i) {
+            const float2 r = __bfloat1622float2(Rk[i * kC + lane]);
+            const float2 x = xs[kz][i];
+            y.x = fmaf(r.x, x.x, fmaf(-r.y, x.y, y.x));
+            y.y = fmaf(r.x, x.y, fmaf(r.y, x.x, y.y));
         }
-        __syncthreads();
-        for (int z = warp; z < N; z += 8) {
-            float2 acc = make_float2(0.f, 0.f);
+        ys[kz][lane] = y;
+    }
+    __syncthreads();
+    for (int z = warp; z < N; z += 8) {
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int kz = 0; kz < M; ++kz) {
-                const float2 m = ei[z][kz], y = ys[kz][lane];
-                acc.x = fmaf(m.x, y.x, fmaf(-m.y, y.y, acc.x));
-                acc.y = fmaf(m.x, y.y, fmaf(m.y, y.x, acc.y));
-            }
-            A[(((size_t)b * N + z) * COLS + col) * kC + lane] = make_float2(acc.x * inv_n, acc.y * inv_n);
+        for (int kz = 0; kz < M; ++kz) {
+            const float2 m = ei[z][kz], y = ys[kz][lane];
+            acc.x = fmaf(m.x, y.x, fmaf(-m.y, y.y, acc.x));
+            acc.y = fmaf(m.x, y.y, fmaf(m.y, y.x, acc.y));
         }
+        A[(((size_t)b * N + z) * COLS + col) * kC + lane] = make_float2(acc.x * inv_n, acc.y * inv_n);
     }
 }
 
@@ -304,10 +300,10 @@ cudaError_t launch_zmix_fwd(int n, int M, float2 *A, float2 *Xsave, const __nv_b
                             const float2 *Einv, int B, cudaStream_t st)
 {
     const __nv_bfloat162 *R2 = (const __nv_bfloat162 *)R;
-    if (n == 64 && M == 16) zmix_fwd_kernel<64, 16><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
-    else if (n == 64 && M == 8) zmix_fwd_kernel<64, 8><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
-    else if (n == 32 && M == 16) zmix_fwd_kernel<32, 16><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
-    else if (n == 32 && M == 8) zmix_fwd_kernel<32, 8><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv, B);
+    if (n == 64 && M == 16) zmix_fwd_kernel<64, 16><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv);
+    else if (n == 64 && M == 8) zmix_fwd_kernel<64, 8><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv);
+    else if (n == 32 && M == 16) zmix_fwd_kernel<32, 16><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv);
+    else if (n == 32 && M == 8) zmix_fwd_kernel<32, 8><<<dim3(M * M, B), 256, 0, st>>>(A, Xsave, R2, Efwd, Einv);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
