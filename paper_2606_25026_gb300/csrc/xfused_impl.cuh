@@ -171,9 +171,14 @@ __device__ __forceinline__ void xf_rows_out(const float2 *tile, float2 *__restri
 // allows, up to 1024 threads per SM (64 registers a thread).  The 256-point density pass holds
 // 32 complex values across its fused radix-16 step and keeps three CTAs (85 registers) instead of
 // spilling at 64.
+// Threads of the density pass's CTA: 256 at 512 points (four butterflies per thread and up to 128
+// registers instead of two at 64: 762 -> 735 us per launch at 512^3, the same shared memory and
+// residency), else the x passes' XCfg count.
+template <int N> __host__ __device__ constexpr int xdens_nt() { return N == 512 ? 256 : XCfg<N>::NT; }
+
 template <int N, bool DENS> struct XFMinBlocks {
     static constexpr int by_smem = (int)((227 * 1024) / (XCfg<N>::smem + 1024));
-    static constexpr int by_threads = 1024 / XCfg<N>::NT;
+    static constexpr int by_threads = 1024 / (DENS ? xdens_nt<N>() : XCfg<N>::NT);
     static constexpr int fit = by_smem < by_threads ? by_smem : by_threads;
     static constexpr int value = (DENS && N == 256 && fit > 3) ? 3 : (fit < 1 ? 1 : fit);
 };
@@ -525,10 +530,10 @@ __device__ __forceinline__ void xdens_fused_body(const XParams &p, int tile, int
 }
 
 template <int N, bool DEP>
-__global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, true>::value) xdens_fused_kernel(XParams p)
+__global__ void __launch_bounds__(xdens_nt<N>(), XFMinBlocks<N, true>::value) xdens_fused_kernel(XParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    xdens_fused_body<N, XCfg<N>::NT, DEP>(p, blockIdx.x, gridDim.x, smem_raw);
+    xdens_fused_body<N, xdens_nt<N>(), DEP>(p, blockIdx.x, gridDim.x, smem_raw);
 }
 
 }  // namespace spe

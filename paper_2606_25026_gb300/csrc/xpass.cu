@@ -27,11 +27,11 @@ static cudaError_t launch_x_n(const XParams &p, cudaStream_t st, int *blocks_out
             return cudaGetLastError();
         }
         if (f == kDensFused) {
-            xdens_fused_kernel<N, false><<<blocks, NT, SM, st>>>(p);
+            xdens_fused_kernel<N, false><<<blocks, xdens_nt<N>(), SM, st>>>(p);
             return cudaGetLastError();
         }
         if (f == (kDensFused | X_DEP)) {
-            xdens_fused_kernel<N, true><<<blocks, NT, SM, st>>>(p);
+            xdens_fused_kernel<N, true><<<blocks, xdens_nt<N>(), SM, st>>>(p);
             return cudaGetLastError();
         }
     }
