@@ -27,10 +27,16 @@ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 // sin h and cos h of a kick half-angle.  A kick turns the phase by a small angle (|h| well below
 // 1/2 at any stable time step), where the Maclaurin series of sine to h^11 and of cosine to h^10
 // are exact to under 1e-12 relative (the first omitted terms are h^13/13! and h^12/12!), so the
-// only error is the FP32 rounding of the Horner evaluation; larger angles take sincosf.
+// only error is the FP32 rounding of the Horner evaluation; larger angles take sincosf.  For
+// |h| <= 2^-6 (the common case: about 1e-4 at a CFL-limited step of a 512^3 halo) the series to h^5
+// and h^4 already stay under 1e-12 relative (h^6/7! < 3e-15, h^6/6! < 2e-14).
 __device__ __forceinline__ void half_angle_sincos(float h, float &sh, float &ch)
 {
-    if (fabsf(h) <= 0.5f) {
+    if (fabsf(h) <= 0.015625f) {
+        const float s2 = h * h;
+        sh = fmaf(h * s2, fmaf(s2, 1.f / 120.f, -1.f / 6.f), h);
+        ch = fmaf(s2, fmaf(s2, 1.f / 24.f, -0.5f), 1.f);
+    } else if (fabsf(h) <= 0.5f) {
         const float s2 = h * h;
         float ps = -1.f / 39916800.f;
         ps = fmaf(ps, s2, 1.f / 362880.f);
