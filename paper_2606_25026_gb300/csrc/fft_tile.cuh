@@ -69,6 +69,28 @@ __device__ __forceinline__ float2 rot90(float2 a)
     return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
 }
 
+// ---- twiddle products.  A table pointer gives the compensated product with the entry's (hi, lo)
+// pair; PlainTw the plain FP32 product with hi alone, for the transforms of the potential (the
+// density's real transform and Phi's inverse): Phi is recomputed every step and reaches psi only
+// through the kick's phase, a small angle, so a fixed relative error of 1e-7 in Phi moves psi's
+// phase by about 1e-7 of that angle per step instead of compounding like an error in psi's own
+// transforms.
+struct PlainTw {
+    const float4 *p;
+};
+template <int DIR>
+__device__ __forceinline__ float2 tw_mul(float2 v, const float4 *__restrict__ tw, int i)
+{
+    const float4 w = __ldg(&tw[i]);
+    return cmul_comp(v, make_float2(w.x, DIR > 0 ? -w.y : w.y), make_float2(w.z, DIR > 0 ? -w.w : w.w));
+}
+template <int DIR>
+__device__ __forceinline__ float2 tw_mul(float2 v, PlainTw tw, int i)
+{
+    const float2 w = __ldg(reinterpret_cast<const float2 *>(tw.p + i));
+    return cmul(v, make_float2(w.x, DIR > 0 ? -w.y : w.y));
+}
+
 // ---- asynchronous global -> shared copies (all of a tile's loads in flight at once)
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -322,8 +344,8 @@ template <int N> constexpr bool has_alt_plan()
 }
 
 // One Stockham stage over all T lines of the tile, in place through registers.
-template <int N, int T, int TP, int NT, int DIR, int Ns, int R>
-__device__ __forceinline__ void fft_stage(float2 *s, const float4 *__restrict__ tw)
+template <int N, int T, int TP, int NT, int DIR, int Ns, int R, class TW>
+__device__ __forceinline__ void fft_stage(float2 *s, TW tw)
 {
     constexpr int B = N / R;
     constexpr int TOTAL = B * T;
@@ -348,12 +370,7 @@ __device__ __forceinline__ void fft_stage(float2 *s, const float4 *__restrict__ 
             const int k = j % Ns;
             if (Ns > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    const float4 w = __ldg(&tw[k * r * (N / (Ns * R))]);
-                    const float2 hi = make_float2(w.x, DIR > 0 ? -w.y : w.y);
-                    const float2 lo = make_float2(w.z, DIR > 0 ? -w.w : w.w);
-                    v[p][r] = cmul_comp(v[p][r], hi, lo);
-                }
+                for (int r = 1; r < R; ++r) v[p][r] = tw_mul<DIR>(v[p][r], tw, k * r * (N / (Ns * R)));
             }
             Dft<R, DIR>::run(v[p]);
             const int base = (j / Ns) * Ns * R + k;
@@ -364,11 +381,11 @@ __device__ __forceinline__ void fft_stage(float2 *s, const float4 *__restrict__ 
     __syncthreads();
 }
 
-template <int N, int T, int TP, int NT, int DIR, int Ns>
-__device__ __forceinline__ void fft_stages(float2 *, const float4 *, RList<>) {}
+template <int N, int T, int TP, int NT, int DIR, int Ns, class TW>
+__device__ __forceinline__ void fft_stages(float2 *, TW, RList<>) {}
 
-template <int N, int T, int TP, int NT, int DIR, int Ns, int R, int... Rest>
-__device__ __forceinline__ void fft_stages(float2 *s, const float4 *tw, RList<R, Rest...>)
+template <int N, int T, int TP, int NT, int DIR, int Ns, class TW, int R, int... Rest>
+__device__ __forceinline__ void fft_stages(float2 *s, TW tw, RList<R, Rest...>)
 {
     fft_stage<N, T, TP, NT, DIR, Ns, R>(s, tw);
     fft_stages<N, T, TP, NT, DIR, Ns * R>(s, tw, RList<Rest...>{});

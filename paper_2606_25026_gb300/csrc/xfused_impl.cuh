@@ -36,8 +36,8 @@ template <class L> struct MiddleOf {
 
 // The last stage of a transform (Ns = N / R): butterfly j of line t reads and writes the points
 // j + r N/R, so no barrier separates its loads from its stores.  Ends with a barrier.
-template <int N, int T, int TP, int NT, int DIR, int R>
-__device__ __forceinline__ void xf_last_stage(float2 *s, const float4 *__restrict__ tw)
+template <int N, int T, int TP, int NT, int DIR, int R, class TW>
+__device__ __forceinline__ void xf_last_stage(float2 *s, TW tw)
 {
     constexpr int B = N / R;
     constexpr int TOTAL = B * T;
@@ -52,11 +52,7 @@ __device__ __forceinline__ void xf_last_stage(float2 *s, const float4 *__restric
             for (int r = 0; r < R; ++r) v[r] = s[(j + r * B) * TP + t];
             if (B > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    const float4 w = __ldg(&tw[j * r]);
-                    v[r] = cmul_comp(v[r], make_float2(w.x, DIR > 0 ? -w.y : w.y),
-                                     make_float2(w.z, DIR > 0 ? -w.w : w.w));
-                }
+                for (int r = 1; r < R; ++r) v[r] = tw_mul<DIR>(v[r], tw, j * r);
             }
             Dft<R, DIR>::run(v);
 #pragma unroll
@@ -69,9 +65,9 @@ __device__ __forceinline__ void xf_last_stage(float2 *s, const float4 *__restric
 // The last stage of a transform straight to the global rows: lanes over the butterflies j of a
 // line (the tile reads stay conflict free at the odd pitch TP, and each warp stores whole row
 // segments), so the tile is not walked again for a separate copy-out.  No barrier at the end.
-template <int N, int T, int TP, int NT, int DIR, int R>
-__device__ __forceinline__ void xf_last_stage_to_rows(const float2 *s, const float4 *__restrict__ tw,
-                                                      float2 *__restrict__ dst, int row0, int rows)
+template <int N, int T, int TP, int NT, int DIR, int R, class TW>
+__device__ __forceinline__ void xf_last_stage_to_rows(const float2 *s, TW tw, float2 *__restrict__ dst, int row0,
+                                                      int rows)
 {
     constexpr int B = N / R;
     constexpr int TOTAL = B * T;
@@ -86,11 +82,7 @@ __device__ __forceinline__ void xf_last_stage_to_rows(const float2 *s, const flo
             for (int r = 0; r < R; ++r) v[r] = s[(j + r * B) * TP + t];
             if (B > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    const float4 w = __ldg(&tw[j * r]);
-                    v[r] = cmul_comp(v[r], make_float2(w.x, DIR > 0 ? -w.y : w.y),
-                                     make_float2(w.z, DIR > 0 ? -w.w : w.w));
-                }
+                for (int r = 1; r < R; ++r) v[r] = tw_mul<DIR>(v[r], tw, j * r);
             }
             Dft<R, DIR>::run(v);
             const int row = row0 + t;
@@ -105,14 +97,14 @@ __device__ __forceinline__ void xf_last_stage_to_rows(const float2 *s, const flo
 
 // The stages of a plan that ends the transform (Ns * R = N at its last radix): fft_stage for all
 // but the last, xf_last_stage for the last.
-template <int N, int T, int TP, int NT, int DIR, int Ns, int R>
-__device__ __forceinline__ void xf_stages(float2 *s, const float4 *tw, RList<R>)
+template <int N, int T, int TP, int NT, int DIR, int Ns, class TW, int R>
+__device__ __forceinline__ void xf_stages(float2 *s, TW tw, RList<R>)
 {
     static_assert(Ns * R == N, "plan does not cover the length");
     xf_last_stage<N, T, TP, NT, DIR, R>(s, tw);
 }
-template <int N, int T, int TP, int NT, int DIR, int Ns, int R0, int R1, int... Rs>
-__device__ __forceinline__ void xf_stages(float2 *s, const float4 *tw, RList<R0, R1, Rs...>)
+template <int N, int T, int TP, int NT, int DIR, int Ns, class TW, int R0, int R1, int... Rs>
+__device__ __forceinline__ void xf_stages(float2 *s, TW tw, RList<R0, R1, Rs...>)
 {
     fft_stage<N, T, TP, NT, DIR, Ns, R0>(s, tw);
     xf_stages<N, T, TP, NT, DIR, Ns * R0>(s, tw, RList<R1, Rs...>{});
@@ -274,7 +266,7 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
         __syncthreads();
     }
     // the inverse stages between the first and the last
-    fft_stages<N, M, HP, NT, +1, R1>(aux, p.tw, typename MiddleOf<PP>::type{});
+    fft_stages<N, M, HP, NT, +1, R1>(aux, PlainTw{p.tw}, typename MiddleOf<PP>::type{});
 
     if constexpr (RL <= 8) {
         // last inverse stage of Phi, the kick of both psi rows at its points and psi's first forward
@@ -306,10 +298,7 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
                 const int m = idx % M, j = idx / M;
                 if (B > 1) {
 #pragma unroll
-                    for (int r = 1; r < RL; ++r) {
-                        const float4 w = __ldg(&p.tw[j * r]);
-                        f[q][r] = cmul_comp(f[q][r], make_float2(w.x, -w.y), make_float2(w.z, -w.w));
-                    }
+                    for (int r = 1; r < RL; ++r) f[q][r] = tw_mul<+1>(f[q][r], PlainTw{p.tw}, j * r);
                 }
                 Dft<RL, +1>::run(f[q]);
                 // f[r] = Phi(row 2m, point j + r B) + i Phi(row 2m + 1, point j + r B)
@@ -361,10 +350,7 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
                     for (int r = 0; r < RL; ++r) f[r] = aux[(j + r * B) * HP + m];
                     if (B > 1) {
     #pragma unroll
-                        for (int r = 1; r < RL; ++r) {
-                            const float4 w = __ldg(&p.tw[j * r]);
-                            f[r] = cmul_comp(f[r], make_float2(w.x, -w.y), make_float2(w.z, -w.w));
-                        }
+                        for (int r = 1; r < RL; ++r) f[r] = tw_mul<+1>(f[r], PlainTw{p.tw}, j * r);
                     }
                     Dft<RL, +1>::run(f);
                     // f[r] = Phi(row 2m, point j + r B) + i Phi(row 2m + 1, point j + r B)
@@ -511,7 +497,7 @@ __device__ __forceinline__ void xdens_fused_body(const XParams &p, int tile, int
     }
     xf_rows_out<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
     // the remaining forward stages of the packed lines
-    xf_stages<N, M, HP, NT, -1, RL>(aux, p.tw, typename SplitFirst<PR>::rest{});
+    xf_stages<N, M, HP, NT, -1, RL>(aux, PlainTw{p.tw}, typename SplitFirst<PR>::rest{});
     // separate the two real rows: A_k = (Z_k + conj Z_{N-k}) / 2, B_k = (Z_k - conj Z_{N-k}) / (2i)
     for (int idx = tid; idx < M * (H + 1); idx += NT) {
         const int m = idx % M, k = idx / M;
