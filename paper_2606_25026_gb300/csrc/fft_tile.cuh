@@ -424,8 +424,8 @@ template <int R, int... Rs, int... As> struct Reverse<RList<R, Rs...>, RList<As.
 // first inverse stage of radix R_m (Ns = 1, no twiddles); the inverse then
 // continues with R_{m-1}..R_1.  op(v, n, t) gets the value of frequency n of
 // line t and returns it multiplied.
-template <int N, int T, int TP, int NT, class Op, int PL = 0>
-__device__ __forceinline__ void tile_fft_fwd_op_inv(float2 *s, const float4 *tw, const Op &op)
+template <int N, int T, int TP, int NT, class Op, int PL = 0, class TW = const float4 *>
+__device__ __forceinline__ void tile_fft_fwd_op_inv(float2 *s, TW tw, const Op &op)
 {
     using Full = typename PlanSel<N, PL>::type;
     constexpr int R = SplitLast<Full>::last;
@@ -452,10 +452,7 @@ __device__ __forceinline__ void tile_fft_fwd_op_inv(float2 *s, const float4 *tw,
             const int t = idx % T, j = idx / T;
             if (B > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    const float4 w = __ldg(&tw[j * r]);
-                    v[p][r] = cmul_comp(v[p][r], make_float2(w.x, w.y), make_float2(w.z, w.w));
-                }
+                for (int r = 1; r < R; ++r) v[p][r] = tw_mul<-1>(v[p][r], tw, j * r);
             }
             Dft<R, -1>::run(v[p]);
 #pragma unroll

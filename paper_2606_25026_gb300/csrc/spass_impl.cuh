@@ -143,7 +143,8 @@ __device__ __forceinline__ void spass_body(const SParams &p, const CUtensorMap *
         } else if constexpr (!SINGLE) {
             if (flags & S_DRIFT) tile_fft_fwd_op_inv<N, T, TP, NT, DriftOp, PL>(tile, p.tw, DriftOp{colfac, p.ez});
             else
-                tile_fft_fwd_op_inv<N, T, TP, NT, PoissonOp, PL>(tile, p.tw,
+                // the potential's transforms take plain FP32 twiddle products (fft_tile.cuh)
+                tile_fft_fwd_op_inv<N, T, TP, NT, PoissonOp, PL>(tile, PlainTw{p.tw},
                                                                  PoissonOp{colk2, p.linek2, p.poisson * p.norm});
         }
     } else if constexpr (TC) {
