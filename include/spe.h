@@ -146,7 +146,9 @@ SPE_API int spe_clear_particles(spe_grid *g);
  * first, so psi and the particles are always observed synchronised;
  * spe_last_mass needs no kick (the mass is measured inside the step).
  * Unless SPE_ASYNC is set, the call waits for the work and returns
- * SPE_ENONFINITE if the field's mass stopped being finite. */
+ * SPE_ETIMEOUT if a bounded device-side wait of a tile copy or a tensor-core
+ * stage gave up during the call (the state is then undefined and must be set
+ * again), else SPE_ENONFINITE if the field's mass stopped being finite. */
 SPE_API int spe_step(spe_grid *g, int nsteps, double dt);
 
 /* Apply a deferred closing half kick now (queued on the grid's stream, no

@@ -1115,22 +1115,18 @@ int spe_step(spe_grid *g, int nsteps, double dt)
     g->pending_dt = dt;
     if (g->cfg.flags & SPE_ASYNC) return SPE_OK;
     double mass = 0.0;
+    int st = 0;   // bounded mbarrier waits of the tile copies and tensor-core stages
     cudaError_t e = cudaMemcpyAsync(&mass, g->diag, sizeof(double), cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, g->status, sizeof(int), cudaMemcpyDeviceToHost, g->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     if (e != cudaSuccess) return SPE_ECUDA;
+    if (st) {
+        cudaMemsetAsync(g->status, 0, sizeof(int), g->st);
+        return SPE_ETIMEOUT;
+    }
     if (!isfinite(mass)) return SPE_ENONFINITE;
     g->host_mass = mass;          // spe_last_mass answers from here until the next step
     g->host_mass_valid = true;
-    if (g->tc) {
-        int st = 0;
-        e = cudaMemcpyAsync(&st, g->status, sizeof(int), cudaMemcpyDeviceToHost, g->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
-        if (e != cudaSuccess) return SPE_ECUDA;
-        if (st) {
-            cudaMemsetAsync(g->status, 0, sizeof(int), g->st);
-            return SPE_ETIMEOUT;
-        }
-    }
     return SPE_OK;
 }
 

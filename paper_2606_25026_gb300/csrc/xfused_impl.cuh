@@ -26,6 +26,7 @@
 // transform's last stage skips the barrier between its loads and stores, since
 // each thread writes back the points it read.
 #pragma once
+#include "tma.cuh"
 #include "xpass_impl.cuh"
 
 namespace spe {
@@ -187,12 +188,22 @@ __device__ __forceinline__ float2 xf_kick(float2 v, float phi, float kap, float 
 
 template <int N> constexpr bool xfused_ok() { return N >= 32 && Length<typename Plan<N>::type>::value >= 2; }
 
+// Row t of a tile staged row-major in the tile's space by bulk copies: t N + 2 (t / 2) complex (16-byte
+// aligned; rows 2m and 2m + 1 shifted by 2m, so that a half-warp reading point j, j + 1 of the eight
+// packed lines' rows hits sixteen different bank pairs when N is a multiple of 16).  The last row ends at
+// 16 N + 14 <= 17 N = the element-major tile.
+template <int N> __device__ __forceinline__ int xf_row_off(int t) { return t * N + 2 * (t >> 1); }
+
 // ---------------------------------------------------------------- kick pass
 // flags X_HAS_PHI | X_KICK | X_FFT, plus X_WRITE_PHI when WPHI (stars interpolate the real Phi).
 // The body works on tile `tile` (rows 16 tile .. 16 tile + 15) with NT threads and XCfg<N>::smem
 // bytes of shared memory at smem_raw; the kernel below runs one tile per block, a persistent kernel
 // any tile from any block.
-template <int N, int NT, bool WPHI>
+// BULK: the psi rows arrive by one bulk copy per row onto an mbarrier (thread 0 issues them; the wait is
+// bounded and a timeout sets the status bit), staged row-major at xf_row_off, instead of per-thread
+// 8-byte copies into the element-major tile.  Only the fused last-stage branch (last radix <= 8) reads
+// the staged rows; the persistent batch kernel, which runs many tiles per block, keeps the copies.
+template <int N, int NT, bool WPHI, bool BULK = false>
 __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, unsigned char *smem_raw)
 {
     using C = XCfg<N>;
@@ -204,7 +215,20 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
     float2 *aux = tile_s + N * TP;   // staged half-spectrum rows [t * SP + k], then packed lines [n * HP + m]
     const int row0 = tile * T, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    constexpr bool kBulk = BULK && RL <= 8;
+    __shared__ __align__(8) unsigned long long rows_bar;
 
+    if constexpr (kBulk) {
+        const int live = min(T, p.rows - row0);
+        if (tid == 0) {
+            mbar_init(&rows_bar, 1);
+            fence_mbar_init();
+            mbar_expect_tx(&rows_bar, (uint32_t)(live * N * sizeof(float2)));
+            for (int t = 0; t < live; ++t)
+                bulk_load(tile_s + xf_row_off<N>(t), p.psi + (size_t)(row0 + t) * N, N * sizeof(float2), &rows_bar);
+        }
+        for (int idx = live * N + tid; idx < T * N; idx += NT) tile_s[xf_row_off<N>(idx / N) + idx % N] = make_float2(0.f, 0.f);
+    }
     // half-spectrum rows of Phi first, then psi, all in flight at once
     for (int t = warp; t < T; t += NT / 32) {
         const int row = row0 + t;
@@ -216,7 +240,7 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
         }
     }
     cp_async_commit();
-    xf_rows_in<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
+    if constexpr (!kBulk) xf_rows_in<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
     cp_async_commit();
     cp_async_wait_group<1>();
     __syncthreads();
@@ -276,6 +300,9 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
         constexpr int B = N / RL, TOTAL = B * M, PER = (TOTAL + NT - 1) / NT;
         const float ks = p.kick_scale, kap = p.kappa;
         float2 f[PER][RL], va[PER][RL], vb[PER][RL];
+        if constexpr (kBulk) {
+            if (!mbar_wait(&rows_bar, 0) && lane == 0) atomicOr(p.status, kTcStatusTimeout);
+        }
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const int idx = tid + q * NT;
@@ -285,8 +312,13 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
                 for (int r = 0; r < RL; ++r) {
                     const int n = j + r * B;
                     f[q][r] = aux[n * HP + m];
-                    va[q][r] = tile_s[n * TP + 2 * m];
-                    vb[q][r] = tile_s[n * TP + 2 * m + 1];
+                    if constexpr (kBulk) {
+                        va[q][r] = tile_s[xf_row_off<N>(2 * m) + n];
+                        vb[q][r] = tile_s[xf_row_off<N>(2 * m + 1) + n];
+                    } else {
+                        va[q][r] = tile_s[n * TP + 2 * m];
+                        vb[q][r] = tile_s[n * TP + 2 * m + 1];
+                    }
                 }
             }
         }
@@ -395,7 +427,7 @@ template <int N, bool WPHI>
 __global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, false>::value) xkick_fused_kernel(XParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    xkick_fused_body<N, XCfg<N>::NT, WPHI>(p, blockIdx.x, smem_raw);
+    xkick_fused_body<N, XCfg<N>::NT, WPHI, true>(p, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------- density pass
