@@ -194,6 +194,53 @@ template <int N> constexpr bool xfused_ok() { return N >= 32 && Length<typename 
 // 16 N + 14 <= 17 N = the element-major tile.
 template <int N> __device__ __forceinline__ int xf_row_off(int t) { return t * N + 2 * (t >> 1); }
 
+// The kick pass's half-spectrum rows staged by bulk copies: H + 2 complex a row (a multiple of 16 bytes;
+// the element past H lies inside the row pitch P, a multiple of 4), row t at t SPB + 2 (t / 2) with SPB a
+// multiple of 16, so that the first stage's reads of rows 2m (and 2m + 1) for eight m and two
+// consecutive points hit sixteen different bank pairs.
+template <int N> __host__ __device__ constexpr int xf_spec_copy() { return N / 2 + 2; }
+template <int N> __host__ __device__ constexpr int xf_spec_pitch() { return (xf_spec_copy<N>() + 15) & ~15; }
+template <int N> __device__ __forceinline__ int xf_spec_off(int t) { return t * xf_spec_pitch<N>() + 2 * (t >> 1); }
+
+// The density pass's psi rows staged by bulk copies: row t at t (N + 16) + 2 (t mod 8), so that eight
+// consecutive rows at two consecutive points hit sixteen different bank pairs (N a multiple of 16); the
+// last row ends at 16 N + 254, inside the element-major tile for N >= 254.
+template <int N> __device__ __forceinline__ int xd_row_off(int t) { return t * (N + 16) + 2 * (t & 7); }
+
+// First stage (Ns = 1) of the density pass's inverse transform, reading the rows staged at xd_row_off and
+// writing the element-major tile over them: all loads, one barrier, then the radix-R DFTs and the stores
+// (the same outputs and positions as fft_stage at Ns = 1).  Lanes run over pairs of butterflies, then
+// the 16 lines: a half-warp reads 8 lines x 2 points and, for R <= 8, stores conflict free at pitch 17.
+template <int N, int T, int TP, int NT, int R>
+__device__ __forceinline__ void xd_first_stage_from_rows(float2 *s)
+{
+    constexpr int B = N / R, TOTAL = B * T, PER = (TOTAL + NT - 1) / NT;
+    static_assert(T == 16 && B % 2 == 0, "16 lines, an even number of butterflies");
+    float2 v[PER][R];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (TOTAL % NT == 0 || idx < TOTAL) {
+            const int t = (idx >> 1) & 15, j = ((idx >> 5) << 1) | (idx & 1);
+            const float2 *row = s + xd_row_off<N>(t);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[p][r] = row[j + r * B];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (TOTAL % NT == 0 || idx < TOTAL) {
+            const int t = (idx >> 1) & 15, j = ((idx >> 5) << 1) | (idx & 1);
+            Dft<R, +1>::run(v[p]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[(j * R + r) * TP + t] = v[p][r];
+        }
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- kick pass
 // flags X_HAS_PHI | X_KICK | X_FFT, plus X_WRITE_PHI when WPHI (stars interpolate the real Phi).
 // The body works on tile `tile` (rows 16 tile .. 16 tile + 15) with NT threads and XCfg<N>::smem
@@ -215,35 +262,67 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
     float2 *aux = tile_s + N * TP;   // staged half-spectrum rows [t * SP + k], then packed lines [n * HP + m]
     const int row0 = tile * T, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    // the staged psi rows end at 16 N + 14 <= 17 N; the staged half-spectrum rows must fit the aux area
+    // (N = 384, 512, 768), else only the psi rows go by bulk copies
     constexpr bool kBulk = BULK && RL <= 8;
-    __shared__ __align__(8) unsigned long long rows_bar;
+    constexpr bool kBulkPhi =
+        kBulk && (size_t)(15 * xf_spec_pitch<N>() + 14 + xf_spec_copy<N>()) * sizeof(float2) <= C::aux_bytes;
+    __shared__ __align__(8) unsigned long long phi_bar, rows_bar;
 
     if constexpr (kBulk) {
+        // half-spectrum rows of Phi first, then psi, all in flight at once (one thread issues them)
         const int live = min(T, p.rows - row0);
         if (tid == 0) {
+            if constexpr (kBulkPhi) mbar_init(&phi_bar, 1);
             mbar_init(&rows_bar, 1);
             fence_mbar_init();
+            if constexpr (kBulkPhi) {
+                mbar_expect_tx(&phi_bar, (uint32_t)(live * xf_spec_copy<N>() * sizeof(float2)));
+                for (int t = 0; t < live; ++t)
+                    bulk_load(aux + xf_spec_off<N>(t), p.phik + (size_t)(row0 + t) * p.P,
+                              xf_spec_copy<N>() * sizeof(float2), &phi_bar);
+            }
             mbar_expect_tx(&rows_bar, (uint32_t)(live * N * sizeof(float2)));
             for (int t = 0; t < live; ++t)
                 bulk_load(tile_s + xf_row_off<N>(t), p.psi + (size_t)(row0 + t) * N, N * sizeof(float2), &rows_bar);
         }
         for (int idx = live * N + tid; idx < T * N; idx += NT) tile_s[xf_row_off<N>(idx / N) + idx % N] = make_float2(0.f, 0.f);
-    }
-    // half-spectrum rows of Phi first, then psi, all in flight at once
-    for (int t = warp; t < T; t += NT / 32) {
-        const int row = row0 + t;
-        if (row < p.rows) {
-            const float2 *r = p.phik + (size_t)row * p.P;
-            for (int k = lane; k < SP; k += 32) cp_async8(&aux[t * SP + k], r + k);
+        if constexpr (kBulkPhi) {
+            for (int idx = live * SP + tid; idx < T * SP; idx += NT)
+                aux[xf_spec_off<N>(idx / SP) + idx % SP] = make_float2(0.f, 0.f);
         } else {
-            for (int k = lane; k < SP; k += 32) aux[t * SP + k] = make_float2(0.f, 0.f);
+            for (int t = warp; t < T; t += NT / 32) {
+                const int row = row0 + t;
+                if (row < p.rows) {
+                    const float2 *r = p.phik + (size_t)row * p.P;
+                    for (int k = lane; k < SP; k += 32) cp_async8(&aux[t * SP + k], r + k);
+                } else {
+                    for (int k = lane; k < SP; k += 32) aux[t * SP + k] = make_float2(0.f, 0.f);
+                }
+            }
+            cp_async_commit();
+            cp_async_wait_group<0>();
         }
+    } else {
+        // half-spectrum rows of Phi first, then psi, all in flight at once
+        for (int t = warp; t < T; t += NT / 32) {
+            const int row = row0 + t;
+            if (row < p.rows) {
+                const float2 *r = p.phik + (size_t)row * p.P;
+                for (int k = lane; k < SP; k += 32) cp_async8(&aux[t * SP + k], r + k);
+            } else {
+                for (int k = lane; k < SP; k += 32) aux[t * SP + k] = make_float2(0.f, 0.f);
+            }
+        }
+        cp_async_commit();
+        xf_rows_in<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
+        cp_async_commit();
+        cp_async_wait_group<1>();
     }
-    cp_async_commit();
-    if constexpr (!kBulk) xf_rows_in<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
-    cp_async_commit();
-    cp_async_wait_group<1>();
-    __syncthreads();
+    __syncthreads();   // also publishes thread 0's mbarrier initialisation: no thread waits on them before
+    if constexpr (kBulkPhi) {
+        if (!mbar_wait(&phi_bar, 0) && lane == 0) atomicOr(p.status, kTcStatusTimeout);
+    }
 
     // first inverse stage of the packed lines Z_m = A + i B (A, B the rows 2m, 2m + 1), with the
     // Hermitian extension A_{N-n} = conj A_n read straight from the staged rows
@@ -255,8 +334,8 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
             const int idx = tid + q * NT;
             if (TOTAL % NT == 0 || idx < TOTAL) {
                 const int m = idx % M, j = idx / M;
-                const float2 *ra = aux + (2 * m) * SP;
-                const float2 *rb = ra + SP;
+                const float2 *ra = kBulkPhi ? aux + xf_spec_off<N>(2 * m) : aux + (2 * m) * SP;
+                const float2 *rb = kBulkPhi ? aux + xf_spec_off<N>(2 * m + 1) : ra + SP;
 #pragma unroll
                 for (int r = 0; r < R1; ++r) {
                     const int n = j + r * B;
@@ -286,7 +365,7 @@ __device__ __forceinline__ void xkick_fused_body(const XParams &p, int tile, uns
                 xf_store_first_stage<R1, HP>(aux, v[q], j, m);
             }
         }
-        cp_async_wait_group<0>();
+        if constexpr (!kBulk) cp_async_wait_group<0>();
         __syncthreads();
     }
     // the inverse stages between the first and the last
@@ -433,7 +512,10 @@ __global__ void __launch_bounds__(XCfg<N>::NT, XFMinBlocks<N, false>::value) xki
 // ---------------------------------------------------------------- density pass
 // flags X_IFFT | X_MASS | X_R2C, plus X_DEP when DEP (the stars' fixed-point deposit).
 // The body works on tile `tile` of the ntiles tiles of the pass (the mass reduction counts them).
-template <int N, int NT, bool DEP>
+// BULK: the psi rows arrive by one bulk copy per row onto an mbarrier, staged at xd_row_off (bounded
+// wait, timeout status bit), and the first inverse stage reads them from there; the persistent batch
+// kernel keeps the per-thread copies.
+template <int N, int NT, bool DEP, bool BULK = false>
 __device__ __forceinline__ void xdens_fused_body(const XParams &p, int tile, int ntiles, unsigned char *smem_raw)
 {
     using C = XCfg<N>;
@@ -447,8 +529,24 @@ __device__ __forceinline__ void xdens_fused_body(const XParams &p, int tile, int
     float2 *aux = tile_s + N * TP;                // packed rho lines [n * HP + m]
     float *auxf = reinterpret_cast<float *>(aux);  // before them: deposit rows [t * DP + n]
     const int row0 = tile * T, tid = threadIdx.x;
+    using PInit = typename SplitLast<PI>::init;   // the inverse stages but the last
+    constexpr int R1 = SplitFirst<PI>::first;
+    constexpr bool kBulk = BULK && N % 16 == 0 && 16 * N + 254 <= N * TP && (N / R1) % 2 == 0;
+    __shared__ __align__(8) unsigned long long rows_bar;
 
-    xf_rows_in<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
+    if constexpr (kBulk) {
+        const int live = min(T, p.rows - row0);
+        if (tid == 0) {
+            mbar_init(&rows_bar, 1);
+            fence_mbar_init();
+            mbar_expect_tx(&rows_bar, (uint32_t)(live * N * sizeof(float2)));
+            for (int t = 0; t < live; ++t)
+                bulk_load(tile_s + xd_row_off<N>(t), p.psi + (size_t)(row0 + t) * N, N * sizeof(float2), &rows_bar);
+        }
+        for (int idx = live * N + tid; idx < T * N; idx += NT) tile_s[xd_row_off<N>(idx / N) + idx % N] = make_float2(0.f, 0.f);
+    } else {
+        xf_rows_in<N, T, TP, NT>(tile_s, p.psi, row0, p.rows);
+    }
     cp_async_commit();
     unsigned live_rows = 0;   // bit t: row row0 + t holds deposit (marked by the star kernel)
     if (DEP) {
@@ -467,7 +565,10 @@ __device__ __forceinline__ void xdens_fused_body(const XParams &p, int tile, int
         }
     }
     cp_async_wait_group<0>();
-    __syncthreads();
+    __syncthreads();   // also publishes thread 0's mbarrier initialisation: no thread waits on it before
+    if constexpr (kBulk) {
+        if (!mbar_wait(&rows_bar, 0) && (tid & 31) == 0) atomicOr(p.status, kTcStatusTimeout);
+    }
     if (DEP) {
         long long *__restrict__ dep = p.dep + (size_t)row0 * N;
         for (int idx = tid; idx < T * N; idx += NT)
@@ -476,7 +577,12 @@ __device__ __forceinline__ void xdens_fused_body(const XParams &p, int tile, int
     }
 
     // inverse stages of psi but the last
-    fft_stages<N, T, TP, NT, +1, 1>(tile_s, p.tw, typename SplitLast<PI>::init{});
+    if constexpr (kBulk) {
+        xd_first_stage_from_rows<N, T, TP, NT, R1>(tile_s);
+        fft_stages<N, T, TP, NT, +1, R1>(tile_s, p.tw, typename SplitFirst<PInit>::rest{});
+    } else {
+        fft_stages<N, T, TP, NT, +1, 1>(tile_s, p.tw, PInit{});
+    }
 
     // last inverse stage of psi (in place per butterfly) for the rows 2m, 2m + 1, rho at its points,
     // and the first forward stage of the packed line Z_m = rho_2m + i rho_2m+1
@@ -551,7 +657,7 @@ template <int N, bool DEP>
 __global__ void __launch_bounds__(xdens_nt<N>(), XFMinBlocks<N, true>::value) xdens_fused_kernel(XParams p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    xdens_fused_body<N, xdens_nt<N>(), DEP>(p, blockIdx.x, gridDim.x, smem_raw);
+    xdens_fused_body<N, xdens_nt<N>(), DEP, true>(p, blockIdx.x, gridDim.x, smem_raw);
 }
 
 }  // namespace spe
