@@ -190,8 +190,12 @@ __device__ __forceinline__ void spass_body(const SParams &p, const CUtensorMap *
     if constexpr (TC) tc_teardown(*tcs);
 }
 
+template <int N, int TW, bool TC, int PL> struct FusedMinBlocks {
+    static constexpr int value = (N == 512 && PL == 2 && TW == 8 && !TC) ? 5 : 1;
+};
 template <int N, int TW, bool TC = false, int PL = 0>
-__global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams p, const __grid_constant__ CUtensorMap tm)
+__global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT, FusedMinBlocks<N, TW, TC, PL>::value)
+    spass_kernel(SParams p, const __grid_constant__ CUtensorMap tm)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     spass_body<N, TW, SCfg<N, TW, TC, PL>::NT, TC, PL>(p, &tm, blockIdx.x, blockIdx.y, smem_dyn);
