@@ -190,15 +190,27 @@ __device__ __forceinline__ void spass_body(const SParams &p, const CUtensorMap *
     if constexpr (TC) tc_teardown(*tcs);
 }
 
-template <int N, int TW, bool TC, int PL> struct FusedMinBlocks {
-    static constexpr int value = (N == 512 && PL == 2 && TW == 8 && !TC) ? 5 : 1;
-};
 template <int N, int TW, bool TC = false, int PL = 0>
-__global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT, FusedMinBlocks<N, TW, TC, PL>::value)
-    spass_kernel(SParams p, const __grid_constant__ CUtensorMap tm)
+__global__ void __launch_bounds__(SCfg<N, TW, TC, PL>::NT) spass_kernel(SParams p, const __grid_constant__ CUtensorMap tm)
 {
     extern __shared__ __align__(128) unsigned char smem_dyn[];
     spass_body<N, TW, SCfg<N, TW, TC, PL>::NT, TC, PL>(p, &tm, blockIdx.x, blockIdx.y, smem_dyn);
+}
+
+// The fused passes (drift, Poisson) at 512 points with the [16, 32] plan and 8-column tiles, held to
+// five CTAs of 128 threads per SM (96 registers, no spills) instead of four at 106.  A kernel of its
+// own: a minimum-blocks bound of 1 on spass_kernel would lift the register cap of every other instance
+// (the 16-column one then takes 216 registers).
+template <int N, int TW, int PL> struct FusedMinBlocks {
+    static constexpr int value = (N == 512 && PL == 2 && TW == 8) ? 5 : 1;
+};
+
+template <int N, int TW, int PL>
+__global__ void __launch_bounds__(SCfg<N, TW, false, PL>::NT, FusedMinBlocks<N, TW, PL>::value)
+    spass_fused_mb_kernel(SParams p, const __grid_constant__ CUtensorMap tm)
+{
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    spass_body<N, TW, SCfg<N, TW, false, PL>::NT, false, PL>(p, &tm, blockIdx.x, blockIdx.y, smem_dyn);
 }
 
 // One forward or inverse transform alone, where spass_line_kernel does not apply: the same body
@@ -280,6 +292,10 @@ static cudaError_t launch_s_nt(const SParams &p, cudaStream_t st, int *blocks_ou
             return cudaGetLastError();
         }
     }
+    if constexpr (!TC && FusedMinBlocks<N, TW, PL>::value > 1) {
+        spass_fused_mb_kernel<N, TW, PL><<<grid, SCfg<N, TW, false, PL>::NT, SCfg<N, TW, false, PL>::smem, st>>>(q, tm);
+        return cudaGetLastError();
+    }
     spass_kernel<N, TW, TC, PL><<<grid, SCfg<N, TW, TC, PL>::NT, SCfg<N, TW, TC, PL>::smem, st>>>(q, tm);
     return cudaGetLastError();
 }
@@ -297,6 +313,11 @@ static cudaError_t attr_s(int smem)
     if constexpr (SingleMinBlocks<N, TW, PL>::value > 1) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(spass_single_kernel<N, TW, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem);
+    }
+    if constexpr (FusedMinBlocks<N, TW, PL>::value > 1) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(spass_fused_mb_kernel<N, TW, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      smem);
     }
     return e;
