@@ -745,6 +745,7 @@ def grid_line(args, r, workload, grid_spec=None, steps=None, warmup=None, e2e=Tr
     else:
         tiles = g.autotune() if not args.no_autotune else None
     schedule = g.schedule()
+    schedule_half = g.schedule_half()
     g.step(warmup, dt)
     g.sync()
     g.launch_count(reset=True)
@@ -808,6 +809,8 @@ def grid_line(args, r, workload, grid_spec=None, steps=None, warmup=None, e2e=Tr
                    "precision": args.prec, "tile_staging": "cp.async" if args.no_tma else "tma",
                    "strided_schedule_yz": {"tiles": list(schedule[0]),
                                                                    "alt_radix_plan": list(schedule[1]),
+                                                                   "half_spectrum_tiles": list(schedule_half[0]),
+                                                                   "half_spectrum_radix_plan": list(schedule_half[1]),
                                                                    "autotuned": tiles is not None and
                                                                    not (args.tiles or args.plans)},
                    "l2": f"working set {workspace_mib:.0f} MiB > 129 MB L2 (no flush needed)",

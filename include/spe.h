@@ -245,13 +245,16 @@ SPE_API int spe_field_energy_noalloc(const void *psi_c64, size_t n, double cell_
  * spe_autotune: time the strided (y, z) passes on a scratch field of the
  * grid's size (allocated and freed inside the call) over tile widths 8, 16
  * and 32 columns (32 where it fits in shared memory) and every radix schedule
- * of the length (see spe_set_schedule), and keep the fastest per axis;
- * choices are cached per (axis, length, nx) for the process.  tiles_out
- * (optional): the y and z widths chosen (spe_get_schedule also gives the
- * radix schedules). */
+ * of the length (see spe_set_schedule), and keep the fastest per axis, once
+ * for psi's passes and once for the half spectrum's (the density's forward
+ * transforms, the Poisson pass and the potential's inverse transforms, timed
+ * as the step runs them); choices are cached per (axis, length, nx, field) for
+ * the process.  tiles_out (optional): psi's y and z widths chosen
+ * (spe_get_schedule also gives the radix schedules, spe_get_schedule_half the
+ * half spectrum's). */
 SPE_API int spe_autotune(spe_grid *g, int *tiles_out);
 
-/* Pin the strided passes' schedule: tiles[0..1] = tile width of the y and z
+/* Pin the strided passes' schedule (psi's and the half spectrum's): tiles[0..1] = tile width of the y and z
  * passes (8, 16 or 32 columns; 0 = the default for the length) and plans[0..1]
  * = radix schedule (0 = default; 1 = the first alternative, for 32, 48, 64,
  * 96, 128, 192, 256, 384, 512, 768 and 1024; 2 = the two-stage [16, 32]
@@ -261,6 +264,9 @@ SPE_API int spe_autotune(spe_grid *g, int *tiles_out);
  * choice.  spe_get_schedule reports the schedule in use. */
 SPE_API int spe_set_schedule(spe_grid *g, const int *tiles, const int *plans);
 SPE_API int spe_get_schedule(spe_grid *g, int *tiles, int *plans);
+/* The schedule of the half spectrum's strided passes in use: psi's unless
+ * spe_autotune chose one of its own (spe_set_schedule pins both). */
+SPE_API int spe_get_schedule_half(spe_grid *g, int *tiles, int *plans);
 
 /* A batch of independent grids (sizes, parameters and particle counts may
  * all differ), stepped together on the batch stream cfgs[0].cuda_stream.

@@ -173,6 +173,8 @@ struct spe_grid {
     bool absorbing;
     int stile[3];     // strided-pass tile width per axis (0 = default; set by the autotuner)
     int splan[3];     // strided-pass radix schedule per axis (0 default, 1 alternative)
+    int htile[3];     // the half spectrum's strided passes (rho, Phi): 0 = as psi's, else set by the autotuner
+    int hplan[3];
     int tc;           // SPE_PREC_SPLIT16
     __half *tcw;      // 32 x 32 DFT operands for the tensor stages: [dir][hi, lo][core layout]
     int *status;      // device status word
@@ -287,8 +289,9 @@ SParams base_y(spe_grid *g, float2 *data, int W, int P)
     SParams p;
     memset(&p, 0, sizeof(p));
     p.data = data;
-    p.tile = g->stile[1];
-    p.plan = g->splan[1];
+    const bool half = W != g->n[0] && g->htile[1];   // the half spectrum, with a schedule of its own
+    p.tile = half ? g->htile[1] : g->stile[1];
+    p.plan = half ? g->hplan[1] : g->splan[1];
     p.tc = g->tc;
     p.tma = !g->tc && !(g->cfg.flags & SPE_NO_TMA);
     p.tcw = g->tcw;
@@ -311,8 +314,9 @@ SParams base_z(spe_grid *g, float2 *data, int W, int P)
     SParams p;
     memset(&p, 0, sizeof(p));
     p.data = data;
-    p.tile = g->stile[2];
-    p.plan = g->splan[2];
+    const bool half = W != g->n[0] && g->htile[2];
+    p.tile = half ? g->htile[2] : g->stile[2];
+    p.plan = half ? g->hplan[2] : g->splan[2];
     p.tc = g->tc;
     p.tma = !g->tc && !(g->cfg.flags & SPE_NO_TMA);
     p.tcw = g->tcw;
@@ -585,7 +589,11 @@ int step_body(spe_grid *g, double dtk, double dt, bool absorb_prev)
 // everything about the strided passes' launch shapes that a captured graph bakes in
 int schedule_key(const spe_grid *g)
 {
-    return ((g->stile[1] * 64 + g->stile[2]) * 4 + g->splan[1]) * 4 + g->splan[2];
+    auto t = [](int w) { return w == 8 ? 1 : (w == 16 ? 2 : (w == 32 ? 3 : 0)); };
+    int k = 0;
+    for (int a = 1; a <= 2; ++a)
+        k = (((k * 4 + t(g->stile[a])) * 4 + g->splan[a]) * 4 + t(g->htile[a])) * 4 + g->hplan[a];
+    return k;
 }
 
 bool graphs_enabled(spe_grid *g) { return !(g->cfg.flags & (SPE_NO_GRAPH | SPE_PROFILE)); }
@@ -1366,27 +1374,38 @@ int spe_profile_read(spe_grid *g, const char **names, unsigned long long *launch
 }  // extern "C"
 
 // ======================================================================== autotuning
-// The strided passes' tile width (16 or 32 columns per CTA) is picked per
-// (axis, transform length, row pitch) by timing a forward + inverse transform
-// of both widths on a scratch buffer the size of the field; choices are cached
-// for the process.
+// The strided passes' tile width (8, 16 or 32 columns per CTA) and radix schedule are picked per
+// (axis, transform length, row length nx, field) by timing every candidate on a scratch buffer the
+// size of psi; choices are cached for the process.  psi's passes are timed as a forward and an
+// inverse transform in one launch; the half spectrum's (rho forward, Poisson, Phi inverse) as the
+// step runs them: the y forward and inverse as single transforms, the z forward transform, Poisson
+// multiply and inverse transform in one launch.  Its 257 live columns at 512 points (against 512 for
+// psi) and the Poisson pass's own register use can favour a narrower tile than psi's.
 
 namespace {
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;  // (axis, n, nx) -> (tile, plan)
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tuned;  // (axis, n, nx, field) -> (tile, plan)
 
-int time_tile(spe_grid *g, int axis, int tile, int plan, float2 *scratch, float *ms_out)
+int time_tile(spe_grid *g, int axis, bool half, int tile, int plan, float2 *scratch, float *ms_out)
 {
-    SParams p = axis == 1 ? base_y(g, scratch, g->n[0], g->n[0]) : base_z(g, scratch, g->n[0], g->n[0]);
-    p.flags = S_FWD | S_INV;
+    const int W = half ? g->W : g->n[0], P = half ? g->P : g->n[0];
+    SParams p = axis == 1 ? base_y(g, scratch, W, P) : base_z(g, scratch, W, P);
     p.tile = tile;
     p.plan = plan;
+    const int flags[2] = {half ? (axis == 1 ? S_FWD : S_FWD | S_POISSON | S_INV) : S_FWD | S_INV,
+                          half && axis == 1 ? S_INV : 0};
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return SPE_ECUDA;
-    cudaError_t e = launch_spass(g->n[axis], p, g->st, nullptr);  // warm-up
-    if (e == cudaSuccess) e = cudaEventRecord(a, g->st);
-    for (int r = 0; r < 5 && e == cudaSuccess; ++r) e = launch_spass(g->n[axis], p, g->st, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < 6 && e == cudaSuccess; ++r) {   // one warm-up round, then five timed
+        if (r == 1) e = cudaEventRecord(a, g->st);
+        for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
+            if (!flags[f]) continue;
+            p.flags = flags[f];
+            e = launch_spass(g->n[axis], p, g->st, nullptr);
+        }
+    }
     if (e == cudaSuccess) e = cudaEventRecord(b, g->st);
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     if (e == cudaSuccess) e = cudaEventElapsedTime(ms_out, a, b);
@@ -1397,39 +1416,50 @@ int time_tile(spe_grid *g, int axis, int tile, int plan, float2 *scratch, float 
 
 int autotune_grid(spe_grid *g, float2 *scratch)
 {
-    for (int axis = 1; axis <= 2; ++axis) {
-        const auto key = std::make_tuple(axis, g->n[axis], g->n[0]);
-        {
-            std::lock_guard<std::mutex> lock(g_tune_mu);
-            auto it = g_tuned.find(key);
-            if (it != g_tuned.end()) {
-                g->stile[axis] = it->second.first;
-                g->splan[axis] = it->second.second;
+    // the half spectrum (rows of P complex) must fit the psi-sized scratch
+    const bool half_fits = (size_t)g->P * g->n[1] * g->n[2] <= g->ncells;
+    for (int field = 0; field < 2; ++field) {
+        int *tile_of = field ? g->htile : g->stile;
+        int *plan_of = field ? g->hplan : g->splan;
+        for (int axis = 1; axis <= 2; ++axis) {
+            if (field == 1 && !half_fits) {
+                tile_of[axis] = 0;   // as psi's
+                plan_of[axis] = 0;
                 continue;
             }
-        }
-        // candidates: tile widths 16, 8, 32 (32 only where it fits in shared memory) x the default
-        // and the alternative radix schedules (lengths that have them)
-        float best_ms = 0.f;
-        int best_tile = 16, best_plan = 0, rc;
-        bool first = true;
-        for (int plan = 0; plan < plan_count_n(g->n[axis]); ++plan) {
-            for (int tile : {16, 8, 32}) {
-                if (!spass_tile_ok(g->n[axis], tile)) continue;
-                float ms = 0.f;
-                if ((rc = time_tile(g, axis, tile, plan, scratch, &ms))) return rc;
-                if (first || ms < best_ms) {
-                    best_tile = tile;
-                    best_plan = plan;
-                    best_ms = ms;
-                    first = false;
+            const auto key = std::make_tuple(axis, g->n[axis], g->n[0], field);
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                auto it = g_tuned.find(key);
+                if (it != g_tuned.end()) {
+                    tile_of[axis] = it->second.first;
+                    plan_of[axis] = it->second.second;
+                    continue;
                 }
             }
+            // candidates: tile widths 16, 8, 32 (32 only where it fits in shared memory) x the default
+            // and the alternative radix schedules (lengths that have them)
+            float best_ms = 0.f;
+            int best_tile = 16, best_plan = 0, rc;
+            bool first = true;
+            for (int plan = 0; plan < plan_count_n(g->n[axis]); ++plan) {
+                for (int tile : {16, 8, 32}) {
+                    if (!spass_tile_ok(g->n[axis], tile)) continue;
+                    float ms = 0.f;
+                    if ((rc = time_tile(g, axis, field == 1, tile, plan, scratch, &ms))) return rc;
+                    if (first || ms < best_ms) {
+                        best_tile = tile;
+                        best_plan = plan;
+                        best_ms = ms;
+                        first = false;
+                    }
+                }
+            }
+            tile_of[axis] = best_tile;
+            plan_of[axis] = best_plan;
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tuned[key] = std::make_pair(best_tile, best_plan);
         }
-        g->stile[axis] = best_tile;
-        g->splan[axis] = best_plan;
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tuned[key] = std::make_pair(best_tile, best_plan);
     }
     return SPE_OK;
 }
@@ -1466,6 +1496,8 @@ extern "C" int spe_set_schedule(spe_grid *g, const int *tiles, const int *plans)
     for (int a = 0; a < 2; ++a) {
         g->stile[a + 1] = tiles[a];
         g->splan[a + 1] = plans[a];
+        g->htile[a + 1] = 0;   // the half spectrum's passes follow the pinned schedule
+        g->hplan[a + 1] = 0;
     }
     return SPE_OK;
 }
@@ -1476,6 +1508,18 @@ extern "C" int spe_get_schedule(spe_grid *g, int *tiles, int *plans)
     for (int a = 0; a < 2; ++a) {
         tiles[a] = g->stile[a + 1] ? g->stile[a + 1] : spass_default_tile(g->n[a + 1]);
         plans[a] = g->splan[a + 1];
+    }
+    return SPE_OK;
+}
+
+extern "C" int spe_get_schedule_half(spe_grid *g, int *tiles, int *plans)
+{
+    if (!g || !tiles || !plans) return SPE_EINVAL;
+    for (int a = 0; a < 2; ++a) {
+        const bool own = g->htile[a + 1] != 0;
+        const int t = own ? g->htile[a + 1] : g->stile[a + 1];
+        tiles[a] = t ? t : spass_default_tile(g->n[a + 1]);
+        plans[a] = own ? g->hplan[a + 1] : g->splan[a + 1];
     }
     return SPE_OK;
 }

@@ -35,6 +35,7 @@ EXPORTED = (
     "spe_last_mass", "spe_mass_async", "spe_get_psi", "spe_get_particles", "spe_particle_count", "spe_sync", "spe_settle",
     "spe_launch_count", "spe_profile_read", "spe_strerror", "spe_field_energy_noalloc",
     "spe_set_static_potential", "spe_virial", "spe_autotune", "spe_set_schedule", "spe_get_schedule",
+    "spe_get_schedule_half",
     "spe_batch_create", "spe_batch_grid",
     "spe_batch_autotune", "spe_batch_step", "spe_batch_settle", "spe_batch_launch_count", "spe_batch_destroy",
     "spe_batch_set_persistent", "spe_batch_get_persistent", "spe_pair_norms",
@@ -135,6 +136,7 @@ def load_library(path: str = LIB_PATH):
         "spe_autotune": (I, [P, ctypes.POINTER(I)]),
         "spe_set_schedule": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "spe_get_schedule": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "spe_get_schedule_half": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "spe_batch_create": (I, [ctypes.POINTER(spe_config), I, ctypes.POINTER(P)]),
         "spe_batch_grid": (I, [P, I, ctypes.POINTER(P)]),
         "spe_batch_autotune": (I, [P]),
@@ -351,6 +353,13 @@ class Grid:
         t = (ctypes.c_int * 2)()
         p = (ctypes.c_int * 2)()
         _check(self._lib.spe_get_schedule(self._h, t, p), "spe_get_schedule")
+        return (t[0], t[1]), (p[0], p[1])
+
+    def schedule_half(self):
+        """((y tile, z tile), (y plan, z plan)) of the half spectrum's passes (rho, Poisson, Phi)."""
+        t = (ctypes.c_int * 2)()
+        p = (ctypes.c_int * 2)()
+        _check(self._lib.spe_get_schedule_half(self._h, t, p), "spe_get_schedule_half")
         return (t[0], t[1]), (p[0], p[1])
 
     def virial(self) -> dict:

@@ -91,14 +91,17 @@ def test_graph_replay_equals_direct_launches(spe, members):
 
 
 def test_autotune_stays_within_parity(spe, members):
-    """Tile widths regroup independent lines; the radix schedule the tuner may pick changes only
-    the FP32 rounding: the tuned grid stays within 1e-6 of the default one."""
+    """Tile widths regroup independent lines; the radix schedule the tuner may pick (for psi's
+    passes and, separately, for the half spectrum's) changes only the FP32 rounding: the tuned grid
+    stays within 1e-6 of the default one, and pinning a schedule pins both fields' passes."""
     m = members[0]
     g = spe.Grid(m["n"], G=1.0)
     tiles = g.autotune()
     assert all(t in (8, 16, 32) for t in tiles)
     (ty, tz), (py, pz) = g.schedule()
     assert (ty, tz) == tuple(tiles) and py in (0, 1) and pz in (0, 1)
+    (hy, hz), (hpy, hpz) = g.schedule_half()
+    assert hy in (8, 16, 32) and hz in (8, 16, 32) and hpy in (0, 1) and hpz in (0, 1)
     g.set_ic(m["psi"])
     g.step(6, m["dt"])
     h = spe.Grid(m["n"], G=1.0)
@@ -106,8 +109,10 @@ def test_autotune_stays_within_parity(spe, members):
     h.step(6, m["dt"])
     a, b = g.get_psi(), h.get_psi()
     assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
-    if (py, pz) == (0, 0):
+    if (py, pz, hpy, hpz) == (0, 0, 0, 0):
         assert np.array_equal(a, b)
+    g.set_schedule((16, 8), (0, 0))
+    assert g.schedule_half() == g.schedule() == ((16, 8), (0, 0))
 
 
 @pytest.mark.parametrize("n", [64, 96, 128, 256, 512])
