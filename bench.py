@@ -746,6 +746,14 @@ def grid_line(args, r, workload, grid_spec=None, steps=None, warmup=None, e2e=Tr
         tiles = g.autotune() if not args.no_autotune else None
     schedule = g.schedule()
     schedule_half = g.schedule_half()
+
+    def same_schedule(other):
+        # the timed grid's schedule on another grid of the same shape: pinned as given, or the
+        # autotuner's cached choices (psi's and the half spectrum's), which re-applies them untimed
+        if args.tiles or args.plans:
+            other.set_schedule(pin_t, pin_p)
+        else:
+            other.autotune()
     g.step(warmup, dt)
     g.sync()
     g.launch_count(reset=True)
@@ -766,7 +774,7 @@ def grid_line(args, r, workload, grid_spec=None, steps=None, warmup=None, e2e=Tr
     # no graphs): per-kernel durations for the roofline and the kernel split
     gp = make_grid(spe.SPE_ASYNC | spe.SPE_PROFILE)
     if tiles is not None:
-        gp.set_schedule(*schedule)
+        same_schedule(gp)
     gp.step(warmup, dt)
     gp.sync()
     gp.profile_read()
@@ -854,7 +862,7 @@ def grid_line(args, r, workload, grid_spec=None, steps=None, warmup=None, e2e=Tr
         o_psi = torch.empty(psi.shape, dtype=torch.complex64).pin_memory()
         ge = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, flags=prec_flag | spe.SPE_ASYNC, stream=stream)
         if tiles is not None:
-            ge.set_schedule(*schedule)
+            same_schedule(ge)
         ke = max(1, min(steps, 200))
         h_mass_out = torch.zeros(ke, dtype=torch.float64).pin_memory()
         # warm the path once
@@ -904,7 +912,7 @@ def grid_line(args, r, workload, grid_spec=None, steps=None, warmup=None, e2e=Tr
                                           "Phi(0) solve untimed"}
         gc = spe.Grid(nx, ny, nz, L=1.0, G=1.0, max_particles=nstar, flags=prec_flag, stream=stream)
         if tiles is not None:
-            gc.set_schedule(*schedule)
+            same_schedule(gc)
         gc.set_ic(psi)
         if nstar:
             gc.add_particles(pos, vel, mass)
